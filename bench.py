@@ -1,0 +1,296 @@
+"""Benchmark: fermion-drift evaluations per second on an 8^3 x 4 lattice.
+
+One step = one drift evaluation of every replica of the batch: cl_factor
+(multifrontal LU of D(m;mu)), cl_selinv_blocks (selected inversion + block
+extraction) and cl_fermion_drift, links already resident in HBM.  The e2e
+figure repeats the step through the same C ABI with the links copied from
+pinned host memory and the drift copied back every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                    [--batch B] [--impl ours|reference]
+
+Multi-GPU: replicas only (independent lattices per rank, no data-path
+collective); value = evaluations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fermion-drift evals/sec on 8^3x4 (FP64 vs mixed, stated drift error); front TFLOP/s vs peak"
+NS, NT, M, MU = 8, 4, 0.05, 0.25
+# DRAM bytes per launch of the dominant kernel from an ncu capture of this
+# workload (profiles/gemm_fp64_8x4.md); None until captured for the current kernel.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of one 8^3 x 4 evaluation)
+# ---------------------------------------------------------------------------
+def oracle_sample(lu_steps=256, ncols=96):
+    """Time a bounded sample of the oracle's dense evaluation and scale it to
+    one full evaluation by exact operation counts: the dense D, the first
+    `lu_steps` of the N-step right-looking LU (step k costs (N-k)^2 updates)
+    and `ncols` of the N column solves (each column costs the same)."""
+    import oracle
+    from paper_1707_08874_gb300 import inputs
+    U = inputs.random_links(NS, NT, seed=inputs.BASE_SEED)
+    N = 3 * NS ** 3 * NT
+    t0 = time.perf_counter()
+    D = oracle.dirac_dense(NS, NT, U, M, MU)
+    t1 = time.perf_counter()
+    LU, piv, _ = oracle.lu_steps(D, lu_steps)
+    t2 = time.perf_counter()
+    # the column solves run on the partly factored matrix (pivots beyond the
+    # sample left in place): the same operations as on the finished factors
+    piv[lu_steps:] = np.arange(lu_steps, N, dtype=np.int32)
+    t3 = time.perf_counter()
+    oracle.solve_unit_columns(LU, piv, np.arange(ncols))
+    t4 = time.perf_counter()
+    k = np.arange(N, dtype=np.float64)
+    lu_scale = ((N - k) ** 2).sum() / ((N - k[:lu_steps]) ** 2).sum()
+    t_eval = (t1 - t0) + (t2 - t1) * lu_scale + (t4 - t3) * (N / ncols)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = ("8^3x4 oracle: dense D + first %d of %d LU steps (scaled by sum (N-k)^2) + %d of %d "
+              "column solves (scaled linearly); measured %.1f s" % (lu_steps, N, ncols, N, t4 - t0))
+    return 1.0 / t_eval, cores, sample, t_eval
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(lu_steps=64, ncols=24)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, sample, t_eval = oracle_sample(lu_steps=64, ncols=24)
+        vals.append(t_eval)
+    wall = time.perf_counter() - t0
+    t_eval = statistics.median(vals)
+    value = 1.0 / t_eval
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_eval, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "8^3x4 lattice, m=0.05, mu=0.25, batch 1, dense CPU oracle",
+                       "lattice": "8^3x4", "batch": 1, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample.split("; measured")[0] + "; %d samples in %.1f s" % (
+                                 args.steps, wall)},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1707_08874_gb300 import binding as B
+    from paper_1707_08874_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = B.CL_FP64 if args.precision == "fp64" else B.CL_MIXED_FP32
+    bsz = args.batch
+    plan = B.Plan.analyze(NS, NT, bsz, prec)
+    info = plan.info
+    U = inputs.random_links(NS, NT, seed=inputs.BASE_SEED + rank * bsz, batch=bsz)
+    links_host = torch.from_numpy(U).pin_memory()
+    links = links_host.to("cuda", non_blocking=True)
+    out = plan.alloc_outputs()
+    kf_host = torch.empty(out["Kf"].shape, dtype=torch.complex128).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.drift_eval(links, M, MU, 1.0, None, out["Gfwd"], out["Gbwd"], out["Kf"], stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    st, _ = plan.get_status()
+    if st != B.CL_OK:
+        raise RuntimeError("drift evaluation reported %s" % B.error_string(st))
+    peak_unit = 0 if prec == B.CL_FP64 else 2
+    peak_gflops = B.measure_peak(peak_unit)
+
+    clocks = Clocks(local)
+    plan.profile_enable(True)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = plan.profile_read()
+    plan.profile_enable(False)
+    st, _ = plan.get_status()
+    if st != B.CL_OK:
+        raise RuntimeError("drift evaluation reported %s" % B.error_string(st))
+
+    # end to end through the same ABI: H2D links, evaluation, D2H drift
+    h2d = links_host.numel() * 16
+    d2h = kf_host.numel() * 16
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        links.copy_(links_host, non_blocking=True)
+        step()
+        kf_host.copy_(out["Kf"], non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / args.steps
+
+    if dist:
+        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    value = world * bsz / (ms / 1e3)
+    g = prof.get("gemm", {})
+    gemm_ms = g.get("total_ms", 0.0) / max(1, g.get("launches", 1))
+    gemm_flops = g.get("flops", 0.0) / max(1, g.get("launches", 1))
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
+    peak = peak_gflops / 1e3
+    total_prof_ms = sum(v["total_ms"] for v in prof.values())
+    flops_eval = info["factor_flops"] + info["selinv_flops"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == B.CL_FP64 else "f32", "data": "synthetic",
+        "config": {"workload": "8^3x4 lattice, m=0.05, mu=0.25, links exp(i c.lambda), c ~ N(0,0.5)+iN(0,0.1)",
+                   "lattice": "8^3x4", "batch": bsz, "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set > L2 (front pool %.0f MB per replica)" % (info["front_bytes"] / bsz / 1e6)},
+        "e2e": {"value": world * bsz / (e2e_ms / 1e3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": info["launches_per_eval"] * args.steps,
+        "roofline": {"bound": "tensor" if prec == B.CL_FP64 else "alu", "kernel": "gemm",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None,
+                     "peak_source": ("FP64 MMA (mma.sync m8n8k4) throughput measured live on this GPU"
+                                     if prec == B.CL_FP64 else "FP32 FMA throughput measured live on this GPU"),
+                     "traffic": NCU_TRAFFIC.get((args.precision, bsz)),
+                     "gemm_share_of_kernel_time": g.get("total_ms", 0.0) / total_prof_ms if total_prof_ms else None},
+        "front_tflops": flops_eval * bsz / (ms / 1e3) / 1e12,
+        "flops_per_eval": flops_eval,
+        "kernel_ms_per_step": {k: v["total_ms"] / args.steps for k, v in prof.items()},
+        "clocks": ck,
+    }
+    if not args.no_cpu_baseline:
+        v, cores, sample, _ = oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * clselinv.h -- C ABI of the GB300 selected-inversion fermion drift library.
+ *
+ * Bloch & Schenk, "Selected inversion as key to a stable Langevin evolution
+ * across the QCD phase boundary" (arXiv:1707.08874).
+ *
+ * The library computes, for the staggered Dirac matrix D(m;mu) of Eq. 1 on an
+ * Ns^3 x Nt torus with SL(3,C) links, the 3x3 blocks of D^{-1} on the pattern
+ * of D (Sec. 3, the "selected inversion": a sparse LU followed by a backward
+ * sweep that never forms an inverse entry outside the filled pattern) and from
+ * them the fermion drift K^f of Eq. 6, written as Tr(P B) + Tr(Q F) (Eq. 8).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are interleaved (re, im) doubles ("complex128").
+ *  - Site index s = ((t*Ns + z)*Ns + y)*Ns + x, V = Ns^3 Nt; direction
+ *    nu = 0..3 is x, y, z, t; colour indices a, b = 0..2.
+ *  - links  [B][V][4][3][3]: U_{s,nu}, row a, column b.
+ *  - D_{s,s} = m; D_{s,s+nu} = +1/2 eta_nu(s) s_nu(s) e^{+mu d_{nu,t}} U_{s,nu};
+ *    D_{s+nu,s} = -1/2 eta_nu(s) s_nu(s) e^{-mu d_{nu,t}} U_{s,nu}^{-1}, with
+ *    eta_0 = 1, eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z) and
+ *    s_nu(s) = -1 on temporal hops between t = Nt-1 and t = 0 (antiperiodic),
+ *    else +1.  U^{-1} replaces U^dagger so that SL(3,C) links are allowed.
+ *  - Every pointer argument named as a device array is a caller-owned,
+ *    contiguous device pointer (cudaMalloc / torch tensor data_ptr()).  The
+ *    library never frees or retains caller memory.
+ *  - Every compute call is stream-ordered on the given stream (NULL = legacy
+ *    default stream), allocates nothing and does not synchronise the host.
+ *  - Return values are CL_* status codes.  Launch-time failures come back
+ *    directly; numerical failures (a tiny pivot, a non-finite result) are
+ *    recorded in a device status word and read with cl_get_status().
+ */
+#ifndef CLSELINV_H
+#define CLSELINV_H
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CL_OK 0
+#define CL_ERR_INVALID_ARG 1
+#define CL_ERR_OOM 2
+#define CL_ERR_CUDA 3
+#define CL_ERR_SINGULAR 4
+#define CL_ERR_NONFINITE 5
+#define CL_ERR_TIMEOUT 6
+#define CL_ERR_UNSUPPORTED 7
+
+/* arithmetic of the sparse factorisation and selected inversion */
+#define CL_FP64 0       /* all front arithmetic in FP64 (FP64 tensor-core MMA) */
+#define CL_MIXED_FP32 1 /* FP32 fronts, FP64 input/output and drift            */
+
+typedef struct cl_plan cl_plan;
+
+/* Summary of a plan (host values, no device access). */
+typedef struct cl_plan_info {
+  int Ns, Nt, V, N;          /* lattice and matrix order N = 3V                */
+  int batch;                 /* replicas per call                               */
+  int precision;             /* CL_FP64 or CL_MIXED_FP32                        */
+  int n_supernodes;          /* separators of the nested dissection            */
+  int n_levels;              /* height of the elimination tree + 1              */
+  int max_front;             /* largest front order (unknowns)                  */
+  int max_pivot_block;       /* largest supernode (pivot unknowns)              */
+  int panel;                 /* pivoting panel width (unknowns, multiple of 3)  */
+  double factor_flops;       /* real flops of one factorisation (per replica)   */
+  double selinv_flops;       /* real flops of one selected inversion            */
+  double front_bytes;        /* device bytes of the front pool (all replicas)   */
+  double device_bytes;       /* all device memory held by the plan              */
+  int launches_per_eval;     /* library kernel launches of one cl_drift_eval    */
+} cl_plan_info;
+
+/* Per-kernel timing record filled by cl_profile_read. */
+typedef struct cl_profile_entry {
+  char name[32];             /* kernel family: "gemm", "panel_inverse", ...     */
+  int launches;              /* launches recorded since cl_profile_enable       */
+  double total_ms;           /* sum of CUDA-event durations of those launches   */
+  double flops;              /* algorithmic real flops of those launches        */
+  double bytes;              /* algorithmic DRAM bytes of those launches        */
+} cl_profile_entry;
+
+/*
+ * cl_analyze -- symbolic analysis, done once per lattice shape (Sec. 3: the
+ * "sparse LU" needs an ordering; the paper's solver does not describe its
+ * own, this library uses geometric nested dissection of the 4D torus).
+ *   Ns, Nt     even extents >= 4 (even for the staggered phases, >= 4 so that
+ *              s+nu and s-nu are distinct sites)
+ *   batch      number of independent lattices (replicas) per call, >= 1
+ *   precision  CL_FP64 or CL_MIXED_FP32
+ *   plan       out: library-owned handle, release with cl_destroy_plan
+ * Builds the elimination tree, supernodes, front index maps and the launch
+ * schedule on the host, then allocates and uploads all device memory the
+ * later calls need on the current device.  Returns CL_ERR_INVALID_ARG for bad
+ * extents, CL_ERR_OOM / CL_ERR_CUDA on allocation or copy failure.
+ */
+int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan);
+
+/*
+ * cl_analyze_symbolic -- the host half of cl_analyze only (no device memory,
+ * usable without a GPU).  The plan supports cl_plan_get_info and
+ * cl_plan_get_node; compute calls on it return CL_ERR_INVALID_ARG.
+ */
+int cl_analyze_symbolic(int Ns, int Nt, int precision, cl_plan** plan);
+
+/*
+ * cl_factor -- numeric sparse LU of D(m;mu) (Sec. 3, first half of the
+ * selected inversion), multifrontal, for every replica.
+ *   links   device [B][V][4][3][3] complex128, read only
+ *   m, mu   quark mass and chemical potential
+ * Pivoting is partial pivoting restricted to diagonal panels of at most
+ * info.panel unknowns inside each supernode; a panel pivot below
+ * 1e-13 * max|panel| records CL_ERR_SINGULAR in the status word.
+ */
+int cl_factor(cl_plan* plan, const double* links, double m, double mu, cudaStream_t stream);
+
+/*
+ * cl_selinv_blocks -- backward (Takahashi) sweep of the selected inversion
+ * from the root to the leaves, then extraction of the blocks of G = D^{-1}
+ * where D is non-zero (Sec. 3, Eq. 8).  Requires a preceding cl_factor.
+ *   Gdiag  device out [B][V][3][3]     G_{s,s}
+ *   Gfwd   device out [B][V][4][3][3]  G_{s,s+nu}   (the block P of Eq. 8)
+ *   Gbwd   device out [B][V][4][3][3]  G_{s+nu,s}   (the block Q of Eq. 8)
+ * Any output pointer may be NULL to skip it.
+ */
+int cl_selinv_blocks(cl_plan* plan, double* Gdiag, double* Gfwd, double* Gbwd,
+                     cudaStream_t stream);
+
+/*
+ * cl_fermion_drift -- Eq. 6 through Eq. 8 for every link:
+ *   K^f_{a,s,nu} = nf * [Tr(G_{s,s+nu} B_a) + Tr(G_{s+nu,s} F_a)],
+ *   F_a = d_a D_{s,s+nu}, B_a = d_a D_{s+nu,s}, d_a U = i lambda_a U
+ *   (left Lie derivative, Gell-Mann lambda_a in the standard order).
+ *   links      device [B][V][4][3][3]
+ *   Gfwd/Gbwd  device [B][V][4][3][3] from cl_selinv_blocks
+ *   mu         chemical potential used in cl_factor
+ *   nf         overall factor (1.0 = the unrooted det D of Eq. 1)
+ *   Kf         device out [B][V][4][8] complex128
+ * Non-finite results record CL_ERR_NONFINITE in the status word.
+ */
+int cl_fermion_drift(cl_plan* plan, const double* links, const double* Gfwd, const double* Gbwd,
+                     double mu, double nf, double* Kf, cudaStream_t stream);
+
+/*
+ * cl_drift_eval -- cl_factor + cl_selinv_blocks + cl_fermion_drift in one
+ * call (one "fermion-drift evaluation").  Gdiag may be NULL; Gfwd, Gbwd and
+ * Kf are required.
+ */
+int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, double nf,
+                  double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
+
+/*
+ * cl_get_status -- synchronises `stream`, returns the first numerical error
+ * recorded since the last call (CL_OK if none) in *info and clears it.
+ * detail (may be NULL) receives the supernode and panel column of a
+ * singular pivot, or -1.
+ */
+int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail);
+
+/* cl_plan_get_info -- host summary of a plan. */
+int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info);
+
+/*
+ * cl_plan_get_node -- the structure of supernode i (0 <= i < n_supernodes,
+ * postorder: children before parents, the root last).
+ *   parent     out: parent supernode or -1
+ *   level      out: height above the leaves (0 = leaf)
+ *   n_sep      out: number of sites eliminated at this supernode
+ *   n_bnd      out: number of boundary sites (ancestor sites coupled to it)
+ *   sep, bnd   out (may be NULL): site lists in front order, capacities
+ *              given by the sizes returned by a first call with NULL
+ */
+int cl_plan_get_node(const cl_plan* plan, int i, int* parent, int* level, int* n_sep,
+                     int* n_bnd, int* sep, int* bnd);
+
+/*
+ * cl_profile_enable -- enable (1) or disable (0) per-launch timing: while
+ * enabled, every compute call records a CUDA event pair on its stream around
+ * each kernel launch (this adds event records between launches; use it to
+ * attribute time, not for the headline rate).  Enabling clears old records.
+ */
+int cl_profile_enable(cl_plan* plan, int enable);
+
+/*
+ * cl_profile_read -- synchronises on the recorded events and aggregates them
+ * per kernel family into out[0..cap-1]; *n receives the number of families.
+ */
+int cl_profile_read(cl_plan* plan, cl_profile_entry* out, int cap, int* n);
+
+/*
+ * cl_measure_peak -- measures an arithmetic peak of the current device with a
+ * throughput kernel (independent FMA / MMA chains on every SM, ~10 ms):
+ * unit 0 = FP64 tensor-core MMA (m8n8k4), 1 = FP64 FMA, 2 = FP32 FMA.
+ * *gflops receives GFLOP/s.  Allocates and frees a small device buffer.
+ */
+int cl_measure_peak(int unit, double* gflops);
+
+/* cl_destroy_plan -- frees the plan and all its device memory (NULL is a no-op). */
+void cl_destroy_plan(cl_plan* plan);
+
+/* cl_error_string -- static text for a status code. */
+const char* cl_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLSELINV_H */

@@ -49,6 +49,8 @@ def _load():
         _lib.or_dirac_dense.argtypes = [I, I, P, D, D, P]
         _lib.or_lu.argtypes = [I, P, P]
         _lib.or_lu.restype = I
+        _lib.or_lu_steps.argtypes = [I, P, P, I]
+        _lib.or_lu_steps.restype = I
         _lib.or_solve_unit_columns.argtypes = [I, P, P, I, P, P]
         _lib.or_inverse.argtypes = [I, P, P, P]
         _lib.or_logdet.argtypes = [I, P, P, P, P]
@@ -95,6 +97,15 @@ def lu(A: np.ndarray):
     N = LU.shape[0]
     piv = np.empty(N, np.int32)
     info = _load().or_lu(N, _ptr(LU), _ptr(piv))
+    return LU, piv, int(info)
+
+
+def lu_steps(A: np.ndarray, nsteps: int):
+    """Only the first ``nsteps`` elimination steps of ``lu`` (timing samples)."""
+    LU = np.array(A, dtype=np.complex128, order="C", copy=True)
+    N = LU.shape[0]
+    piv = np.empty(N, np.int32)
+    info = _load().or_lu_steps(N, _ptr(LU), _ptr(piv), int(nsteps))
     return LU, piv, int(info)
 
 

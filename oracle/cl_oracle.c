@@ -164,9 +164,14 @@ void or_dirac_dense(int Ns, int Nt, const cplx* U, double m, double mu, cplx* D)
 /* was swapped with row k at step k.  Returns 0, or k+1 if the pivot    */
 /* of column k is exactly zero.  Ties in |a_ik| keep the lowest row.    */
 /* ------------------------------------------------------------------ */
-int or_lu(int N, cplx* A, int* piv) {
+int or_lu_steps(int N, cplx* A, int* piv, int nsteps);
+int or_lu(int N, cplx* A, int* piv) { return or_lu_steps(N, A, piv, N); }
+
+/* The first nsteps elimination steps of the same factorisation (used only to
+   time a bounded sample of the dense reference). */
+int or_lu_steps(int N, cplx* A, int* piv, int nsteps) {
   int info = 0;
-  for (int k = 0; k < N; ++k) {
+  for (int k = 0; k < nsteps && k < N; ++k) {
     int p = k;
     double best = cabs(A[(size_t)k * N + k]);
     for (int i = k + 1; i < N; ++i) {

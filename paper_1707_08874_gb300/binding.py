@@ -1,0 +1,221 @@
+"""Thin ctypes binding of ``libclselinv.so`` (C ABI in ``include/clselinv.h``).
+
+Argument marshalling only: every step of the drift evaluation runs in the CUDA
+library.  Device arrays are torch tensors (complex128, CUDA, contiguous); the
+stream is torch's current stream unless one is given.  There is no CPU path:
+if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CL_OK = 0
+CL_ERR_INVALID_ARG = 1
+CL_ERR_OOM = 2
+CL_ERR_CUDA = 3
+CL_ERR_SINGULAR = 4
+CL_ERR_NONFINITE = 5
+CL_ERR_TIMEOUT = 6
+CL_ERR_UNSUPPORTED = 7
+CL_FP64 = 0
+CL_MIXED_FP32 = 1
+
+_lib = None
+
+
+class CLError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, error_string(code) if _lib else "?", code))
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("Ns", ctypes.c_int), ("Nt", ctypes.c_int), ("V", ctypes.c_int), ("N", ctypes.c_int),
+                ("batch", ctypes.c_int), ("precision", ctypes.c_int), ("n_supernodes", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("max_front", ctypes.c_int), ("max_pivot_block", ctypes.c_int),
+                ("panel", ctypes.c_int), ("factor_flops", ctypes.c_double), ("selinv_flops", ctypes.c_double),
+                ("front_bytes", ctypes.c_double), ("device_bytes", ctypes.c_double),
+                ("launches_per_eval", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
+           "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
+           "cl_profile_read", "cl_measure_peak", "cl_destroy_plan", "cl_error_string"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it in-tree if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError("libclselinv.so is not built: run paper_1707_08874_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.cl_analyze.argtypes = [I, I, I, I, ctypes.POINTER(P)]
+    L.cl_analyze_symbolic.argtypes = [I, I, I, ctypes.POINTER(P)]
+    L.cl_factor.argtypes = [P, P, D, D, P]
+    L.cl_selinv_blocks.argtypes = [P, P, P, P, P]
+    L.cl_fermion_drift.argtypes = [P, P, P, P, D, D, P, P]
+    L.cl_drift_eval.argtypes = [P, P, D, D, D, P, P, P, P, P]
+    L.cl_get_status.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.cl_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    L.cl_plan_get_node.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                   ctypes.POINTER(I), P, P]
+    L.cl_profile_enable.argtypes = [P, I]
+    L.cl_profile_read.argtypes = [P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(I)]
+    L.cl_measure_peak.argtypes = [I, ctypes.POINTER(D)]
+    L.cl_destroy_plan.argtypes = [P]
+    L.cl_destroy_plan.restype = None
+    L.cl_error_string.argtypes = [I]
+    L.cl_error_string.restype = ctypes.c_char_p
+    for f in EXPORTS:
+        if f not in ("cl_destroy_plan", "cl_error_string"):
+            getattr(L, f).restype = I
+    _lib = L
+    return L
+
+
+def error_string(code: int) -> str:
+    return load().cl_error_string(code).decode()
+
+
+def measure_peak(unit: int) -> float:
+    """GFLOP/s of the current device: 0 = FP64 MMA, 1 = FP64 FMA, 2 = FP32 FMA."""
+    g = ctypes.c_double()
+    _check(load().cl_measure_peak(unit, ctypes.byref(g)), "cl_measure_peak")
+    return g.value
+
+
+def _check(code: int, what: str):
+    if code != CL_OK:
+        raise CLError(code, what)
+
+
+def _dev(t, name, shape_tail=None):
+    """data_ptr of a contiguous complex128 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous complex128 CUDA tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A plan of cl_analyze: one lattice shape, `batch` replicas, one precision."""
+
+    def __init__(self, handle, symbolic: bool):
+        self._h = handle
+        self.symbolic = symbolic
+        self.info = self.get_info()
+
+    # -- construction ----------------------------------------------------
+    @classmethod
+    def analyze(cls, Ns: int, Nt: int, batch: int = 1, precision: int = CL_FP64) -> "Plan":
+        h = ctypes.c_void_p()
+        _check(load().cl_analyze(Ns, Nt, batch, precision, ctypes.byref(h)), "cl_analyze")
+        return cls(h, False)
+
+    @classmethod
+    def analyze_symbolic(cls, Ns: int, Nt: int, precision: int = CL_FP64) -> "Plan":
+        h = ctypes.c_void_p()
+        _check(load().cl_analyze_symbolic(Ns, Nt, precision, ctypes.byref(h)), "cl_analyze_symbolic")
+        return cls(h, True)
+
+    def close(self):
+        if self._h:
+            load().cl_destroy_plan(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- host queries ------------------------------------------------------
+    def get_info(self) -> dict:
+        inf = PlanInfo()
+        _check(load().cl_plan_get_info(self._h, ctypes.byref(inf)), "cl_plan_get_info")
+        return inf.as_dict()
+
+    def node(self, i: int) -> dict:
+        L = load()
+        par, lev, ns, nb = (ctypes.c_int() for _ in range(4))
+        _check(L.cl_plan_get_node(self._h, i, ctypes.byref(par), ctypes.byref(lev), ctypes.byref(ns),
+                                  ctypes.byref(nb), None, None), "cl_plan_get_node")
+        sep = np.empty(ns.value, np.int32)
+        bnd = np.empty(nb.value, np.int32)
+        _check(L.cl_plan_get_node(self._h, i, None, None, None, None, sep.ctypes.data_as(ctypes.c_void_p),
+                                  bnd.ctypes.data_as(ctypes.c_void_p)), "cl_plan_get_node")
+        return dict(parent=par.value, level=lev.value, sep=sep, bnd=bnd)
+
+    # -- compute calls (stream-ordered, no host sync) -----------------------
+    def factor(self, links, m: float, mu: float, stream=None):
+        _check(load().cl_factor(self._h, _dev(links, "links"), float(m), float(mu), _stream(stream)), "cl_factor")
+
+    def selinv_blocks(self, Gdiag, Gfwd, Gbwd, stream=None):
+        _check(load().cl_selinv_blocks(self._h, _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
+                                       _stream(stream)), "cl_selinv_blocks")
+
+    def fermion_drift(self, links, Gfwd, Gbwd, mu: float, nf: float, Kf, stream=None):
+        _check(load().cl_fermion_drift(self._h, _dev(links, "links"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
+                                       float(mu), float(nf), _dev(Kf, "Kf"), _stream(stream)),
+               "cl_fermion_drift")
+
+    def drift_eval(self, links, m: float, mu: float, nf: float, Gdiag, Gfwd, Gbwd, Kf, stream=None):
+        _check(load().cl_drift_eval(self._h, _dev(links, "links"), float(m), float(mu), float(nf),
+                                    _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
+                                    _dev(Kf, "Kf"), _stream(stream)), "cl_drift_eval")
+
+    def get_status(self, stream=None):
+        info = ctypes.c_int()
+        detail = (ctypes.c_int * 2)()
+        _check(load().cl_get_status(self._h, _stream(stream), ctypes.byref(info), detail), "cl_get_status")
+        return info.value, (detail[0], detail[1])
+
+    def profile_enable(self, on: bool = True):
+        _check(load().cl_profile_enable(self._h, 1 if on else 0), "cl_profile_enable")
+
+    def profile_read(self) -> dict:
+        buf = (ProfileEntry * 16)()
+        n = ctypes.c_int()
+        _check(load().cl_profile_read(self._h, buf, 16, ctypes.byref(n)), "cl_profile_read")
+        return {buf[i].name.decode(): dict(launches=buf[i].launches, total_ms=buf[i].total_ms,
+                                           flops=buf[i].flops, bytes=buf[i].bytes) for i in range(n.value)}
+
+    # -- convenience: allocate outputs and run one evaluation --------------
+    def alloc_outputs(self):
+        import torch
+        B, V = self.info["batch"], self.info["V"]
+        kw = dict(dtype=torch.complex128, device="cuda")
+        return dict(Gdiag=torch.empty((B, V, 3, 3), **kw), Gfwd=torch.empty((B, V, 4, 3, 3), **kw),
+                    Gbwd=torch.empty((B, V, 4, 3, 3), **kw), Kf=torch.empty((B, V, 4, 8), **kw))

@@ -1,0 +1,433 @@
+// Host symbolic analysis, done once per lattice shape: geometric nested
+// dissection of the Ns^3 x Nt torus, the supernodal elimination tree, the front
+// index maps and the fixed launch schedule of the factorisation and of the
+// selected-inversion sweep (Sec. 3: "sparse LU followed by a selected
+// inversion"; the paper's solver does not describe its ordering).
+#include <algorithm>
+#include <array>
+#include <functional>
+#include <stdexcept>
+
+#include "plan.hpp"
+
+namespace cl {
+namespace {
+
+struct Box {
+  std::array<int, 4> lo, n;
+  std::array<bool, 4> per;
+};
+
+struct Geo {
+  int Ns, Nt;
+  std::array<int, 4> L;
+  int site(const std::array<int, 4>& c) const { return ((c[3] * Ns + c[2]) * Ns + c[1]) * Ns + c[0]; }
+  std::array<int, 4> coords(int s) const {
+    std::array<int, 4> c;
+    c[0] = s % Ns; s /= Ns;
+    c[1] = s % Ns; s /= Ns;
+    c[2] = s % Ns; s /= Ns;
+    c[3] = s;
+    return c;
+  }
+  int nbr(int s, int nu, int dir) const {
+    auto c = coords(s);
+    c[nu] = (c[nu] + dir + L[nu]) % L[nu];
+    return site(c);
+  }
+  bool in_box(const Box& b, int s) const {
+    auto c = coords(s);
+    for (int d = 0; d < 4; ++d) {
+      if (b.per[d]) continue;
+      int rel = ((c[d] - b.lo[d]) % L[d] + L[d]) % L[d];
+      if (rel >= b.n[d]) return false;
+    }
+    return true;
+  }
+  std::vector<int> sites(const Box& b) const {
+    std::vector<int> out;
+    std::array<int, 4> c;
+    for (int t = 0; t < b.n[3]; ++t)
+      for (int z = 0; z < b.n[2]; ++z)
+        for (int y = 0; y < b.n[1]; ++y)
+          for (int x = 0; x < b.n[0]; ++x) {
+            c = {(b.lo[0] + x) % L[0], (b.lo[1] + y) % L[1], (b.lo[2] + z) % L[2], (b.lo[3] + t) % L[3]};
+            out.push_back(site(c));
+          }
+    std::sort(out.begin(), out.end());
+    return out;
+  }
+};
+
+// Recursive geometric nested dissection.  A periodic extent is cut by two
+// opposite hyperplanes, an open one by its middle hyperplane; the cut with the
+// smallest separator wins (ties: the longer extent, then the lower direction).
+// Nodes are appended in postorder; `boxes` keeps each node's subtree domain.
+int dissect(const Geo& g, const Box& b, std::vector<SNode>& nodes, std::vector<Box>& boxes) {
+  int64_t nsites = 1;
+  for (int d = 0; d < 4; ++d) nsites *= b.n[d];
+  int best = -1;
+  int64_t best_sz = 0;
+  for (int d = 0; d < 4; ++d) {
+    int64_t other = nsites / b.n[d], sz;
+    if (b.per[d]) {
+      if (b.n[d] < 4) continue;
+      sz = 2 * other;
+    } else {
+      if (b.n[d] < 2) continue;
+      sz = other;
+    }
+    if (best < 0 || sz < best_sz || (sz == best_sz && b.n[d] > b.n[best])) {
+      best = d;
+      best_sz = sz;
+    }
+  }
+  SNode nd;
+  if (nsites <= kLeafSites || best < 0) {
+    nd.sep = g.sites(b);
+    nodes.push_back(nd);
+    boxes.push_back(b);
+    return (int)nodes.size() - 1;
+  }
+  const int d = best, lo = b.lo[d], n = b.n[d];
+  std::vector<int> planes;
+  std::vector<std::pair<int, int>> pieces;
+  if (b.per[d]) {
+    planes = {lo, lo + n / 2};
+    pieces = {{lo + 1, n / 2 - 1}, {lo + n / 2 + 1, n - n / 2 - 1}};
+  } else {
+    int mid = lo + n / 2;
+    planes = {mid};
+    pieces = {{lo, n / 2}, {mid + 1, n - n / 2 - 1}};
+  }
+  std::vector<int> kids;
+  for (auto& pc : pieces) {
+    if (pc.second <= 0) continue;
+    Box c = b;
+    c.lo[d] = pc.first % g.L[d];
+    c.n[d] = pc.second;
+    c.per[d] = false;
+    kids.push_back(dissect(g, c, nodes, boxes));
+  }
+  for (int pl : planes) {
+    Box c = b;
+    c.lo[d] = pl % g.L[d];
+    c.n[d] = 1;
+    c.per[d] = false;
+    auto s = g.sites(c);
+    nd.sep.insert(nd.sep.end(), s.begin(), s.end());
+  }
+  std::sort(nd.sep.begin(), nd.sep.end());
+  nd.children = kids;
+  nodes.push_back(nd);
+  boxes.push_back(b);
+  int id = (int)nodes.size() - 1;
+  for (int c : kids) nodes[c].parent = id;
+  return id;
+}
+
+int64_t tiles(int M, int N) {
+  return (int64_t)((M + kTileM - 1) / kTileM) * ((N + kTileN - 1) / kTileN);
+}
+
+}  // namespace
+
+void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision) {
+  if (Ns < 4 || Nt < 4 || (Ns & 1) || (Nt & 1)) throw std::invalid_argument("Ns, Nt must be even and >= 4");
+  if (Ns > 64 || Nt > 128) throw std::invalid_argument("lattice too large");
+  if (precision != CL_FP64 && precision != CL_MIXED_FP32) throw std::invalid_argument("precision");
+  p.Ns = Ns;
+  p.Nt = Nt;
+  p.V = Ns * Ns * Ns * Nt;
+  p.N = 3 * p.V;
+  p.batch = batch;
+  p.precision = precision;
+  p.panel = precision == CL_FP64 ? kPanelFP64 : kPanelFP32;
+  Geo g{Ns, Nt, {Ns, Ns, Ns, Nt}};
+  const int V = p.V;
+
+  // ---- elimination tree -------------------------------------------------
+  std::vector<Box> boxes;
+  Box whole{{0, 0, 0, 0}, {Ns, Ns, Ns, Nt}, {true, true, true, true}};
+  p.nodes.clear();
+  dissect(g, whole, p.nodes, boxes);
+  auto& nodes = p.nodes;
+  const int nn = (int)nodes.size();
+  std::vector<int> sn(V, -1);
+  for (int i = 0; i < nn; ++i)
+    for (int s : nodes[i].sep) {
+      if (sn[s] != -1) throw std::logic_error("site in two supernodes");
+      sn[s] = i;
+    }
+  for (int s = 0; s < V; ++s)
+    if (sn[s] < 0) throw std::logic_error("site in no supernode");
+
+  // ---- boundaries, ordered by position in the parent's front (preorder) ----
+  std::vector<int> pos(V, -1);
+  for (int i = nn - 1; i >= 0; --i) {  // reverse postorder: parents before children
+    SNode& P = nodes[i];
+    std::vector<int> front = P.sep;
+    front.insert(front.end(), P.bnd.begin(), P.bnd.end());
+    for (size_t q = 0; q < front.size(); ++q) pos[front[q]] = (int)q;
+    for (int c : P.children) {
+      std::vector<int> b;
+      for (int s : g.sites(boxes[c]))
+        for (int nu = 0; nu < 4; ++nu)
+          for (int dir = -1; dir <= 1; dir += 2) {
+            int y = g.nbr(s, nu, dir);
+            if (!g.in_box(boxes[c], y)) b.push_back(y);
+          }
+      std::sort(b.begin(), b.end());
+      b.erase(std::unique(b.begin(), b.end()), b.end());
+      for (int s : b)
+        if (pos[s] < 0) throw std::logic_error("boundary outside the parent front");
+      std::sort(b.begin(), b.end(), [&](int a, int c2) { return pos[a] < pos[c2]; });
+      nodes[c].bnd = b;
+    }
+    for (int s : front) pos[s] = -1;
+  }
+
+  // ---- sizes, levels, front offsets ---------------------------------------
+  p.n_levels = 0;
+  int64_t off = 0;
+  for (int i = 0; i < nn; ++i) {
+    SNode& n = nodes[i];
+    n.k = 3 * (int)n.sep.size();
+    n.r = 3 * (int)n.bnd.size();
+    n.nf = n.k + n.r;
+    n.level = 0;
+    for (int c : n.children) n.level = std::max(n.level, nodes[c].level + 1);
+    p.n_levels = std::max(p.n_levels, n.level + 1);
+    n.off = off;
+    off += ((int64_t)n.nf * n.nf + 15) / 16 * 16;
+  }
+  p.pool_elems = off;
+
+  // per-node workspace inside its level (panel temps / selected-inversion temps)
+  const int b = p.panel;
+  std::vector<int64_t> level_tmp(p.n_levels, 0);
+  for (int i = 0; i < nn; ++i) {
+    SNode& n = nodes[i];
+    int64_t need = std::max<int64_t>(2LL * b * n.nf, 2LL * n.r * n.k);
+    need = (need + 15) / 16 * 16;
+    n.tmp = p.pool_elems + level_tmp[n.level];
+    level_tmp[n.level] += need;
+  }
+  p.tmp_elems = 0;
+  for (auto t : level_tmp) p.tmp_elems = std::max(p.tmp_elems, t);
+  p.arena_elems = (p.pool_elems + p.tmp_elems + 63) / 64 * 64;
+
+  // ---- flop counts (complex multiply-add = 8 real flops) ------------------
+  p.factor_flops = p.selinv_flops = 0;
+  for (auto& n : nodes) {
+    for (int c0 = 0; c0 < n.k; c0 += b) {
+      double bp = std::min(b, n.k - c0), nf = n.nf;
+      p.factor_flops += 8.0 * (bp * bp * bp + 2 * nf * bp * bp + nf * nf * bp);
+    }
+    double k = n.k, r = n.r;
+    p.selinv_flops += 8.0 * (2 * r * r * k + k * k * r);
+  }
+
+  // ---- assembly / extraction tables -----------------------------------------
+  // position of a site in a front: sep sites by their own index, boundary
+  // sites through a per-node table sorted by site
+  std::vector<int> sep_pos(V);
+  for (int i = 0; i < nn; ++i)
+    for (size_t q = 0; q < nodes[i].sep.size(); ++q) sep_pos[nodes[i].sep[q]] = (int)q;
+  std::vector<std::vector<std::pair<int, int>>> bnd_sorted(nn);
+  for (int i = 0; i < nn; ++i) {
+    auto& v = bnd_sorted[i];
+    for (size_t q = 0; q < nodes[i].bnd.size(); ++q) v.push_back({nodes[i].bnd[q], (int)q});
+    std::sort(v.begin(), v.end());
+  }
+  auto front_pos = [&](int node, int s) -> int {
+    if (sn[s] == node) return sep_pos[s];
+    const auto& v = bnd_sorted[node];
+    auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(s, -1));
+    if (it == v.end() || it->first != s) throw std::logic_error("site not in front");
+    return (int)nodes[node].sep.size() + it->second;
+  };
+  auto block_off = [&](int x, int y, int64_t& o, int& ld) {
+    int node = std::min(sn[x], sn[y]);  // the supernode eliminated first (postorder)
+    const SNode& n = nodes[node];
+    o = n.off + (int64_t)3 * front_pos(node, x) * n.nf + 3 * front_pos(node, y);
+    ld = n.nf;
+  };
+  p.off_diag.assign(V, 0);
+  p.ld_diag.assign(V, 0);
+  p.off_fwd.assign(4 * V, 0);
+  p.ld_fwd.assign(4 * V, 0);
+  p.off_bwd.assign(4 * V, 0);
+  p.ld_bwd.assign(4 * V, 0);
+  for (int s = 0; s < V; ++s) {
+    block_off(s, s, p.off_diag[s], p.ld_diag[s]);
+    for (int nu = 0; nu < 4; ++nu) {
+      int y = g.nbr(s, nu, +1);
+      block_off(s, y, p.off_fwd[4 * s + nu], p.ld_fwd[4 * s + nu]);
+      block_off(y, s, p.off_bwd[4 * s + nu], p.ld_bwd[4 * s + nu]);
+    }
+  }
+
+  // ---- schedule ----------------------------------------------------------
+  p.gemm.clear();
+  p.panels.clear();
+  p.copies.clear();
+  p.extadd.clear();
+  p.gather.clear();
+  p.maps.clear();
+  p.factor_ops.clear();
+  p.selinv_ops.clear();
+  std::vector<std::vector<int>> by_level(p.n_levels);
+  for (int i = 0; i < nn; ++i) by_level[nodes[i].level].push_back(i);
+
+  auto add_gemm = [&](int blk, int64_t a, int lda, int64_t bb, int ldb, int64_t c, int ldc, int M, int N,
+                      int K, int neg, int beta, int m0, int m1) {
+    GemmDesc d{a, bb, c, lda, ldb, ldc, M, N, K, neg, beta, m0, m1, blk, (N + kTileN - 1) / kTileN};
+    p.gemm.push_back(d);
+    return (int)tiles(M, N);
+  };
+  auto add_copy = [&](int blk, int64_t src, int lds, int64_t dst, int ldd, int rows, int cols, int rm0, int rm1,
+                      int cm0, int cm1) {
+    CopyDesc d{src, dst, lds, ldd, rows, cols, rm0, rm1, cm0, cm1, blk};
+    p.copies.push_back(d);
+    return (int)(((int64_t)rows * cols + 255) / 256);
+  };
+
+  p.factor_ops.push_back(Op{OP_ZERO, 0, 0, 0, -1});
+  p.factor_ops.push_back(Op{OP_ASSEMBLE, 0, 0, (4 * V + 127) / 128, -1});
+  for (int h = 0; h < p.n_levels; ++h) {
+    const auto& lv = by_level[h];
+    if (h > 0) {
+      Op op{OP_EXTADD, (int)p.extadd.size(), 0, 0, h};
+      int blk = 0;
+      for (int i : lv) {
+        const SNode& P = nodes[i];
+        if (P.children.empty()) continue;
+        ExtAddDesc d{};
+        d.parent = P.off;
+        d.nfp = P.nf;
+        d.nchild = (int)P.children.size();
+        if (d.nchild > 2) throw std::logic_error("more than two children");
+        std::vector<int> front(P.sep.size() + P.bnd.size());
+        for (int q = 0; q < d.nchild; ++q) {
+          const SNode& C = nodes[P.children[q]];
+          d.child[q] = C.off;
+          d.nfc[q] = C.nf;
+          d.kc[q] = C.k;
+          d.map[q] = (int)p.maps.size();
+          std::vector<int> inv(front.size(), -1);
+          for (size_t j = 0; j < C.bnd.size(); ++j) inv[front_pos(i, C.bnd[j])] = (int)j;
+          p.maps.insert(p.maps.end(), inv.begin(), inv.end());
+        }
+        d.blk0 = blk;
+        blk += (int)(((int64_t)P.nf * P.nf + 255) / 256);
+        p.extadd.push_back(d);
+      }
+      op.d1 = (int)p.extadd.size();
+      op.blocks = blk;
+      if (op.d1 > op.d0) p.factor_ops.push_back(op);
+    }
+    int maxk = 0;
+    for (int i : lv) maxk = std::max(maxk, nodes[i].k);
+    for (int c0 = 0; c0 < maxk; c0 += b) {
+      Op pinv{OP_PANEL, (int)p.panels.size(), 0, 0, h};
+      Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+      int blk1 = 0;
+      for (int i : lv) {
+        const SNode& n = nodes[i];
+        if (c0 >= n.k) continue;
+        int bp = std::min(b, n.k - c0);
+        p.panels.push_back(PanelDesc{n.off + (int64_t)c0 * n.nf + c0, n.nf, bp, i, c0});
+        if (n.nf == bp) continue;  // nothing outside the panel
+        int64_t tR = n.tmp, tC = n.tmp + (int64_t)b * n.nf;
+        // TR = Y * R_old  (bp x nf), TC = -C_old * Y (nf x bp)
+        blk1 += add_gemm(blk1, n.off + (int64_t)c0 * n.nf + c0, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, tR, n.nf,
+                         bp, n.nf, bp, 0, 0, 0, 0);
+        blk1 += add_gemm(blk1, n.off + c0, n.nf, n.off + (int64_t)c0 * n.nf + c0, n.nf, tC, bp, n.nf, bp, bp, 1,
+                         0, 0, 0);
+      }
+      pinv.d1 = (int)p.panels.size();
+      pinv.blocks = pinv.d1 - pinv.d0;
+      p.factor_ops.push_back(pinv);
+      g1.d1 = (int)p.gemm.size();
+      g1.blocks = blk1;
+      if (g1.d1 == g1.d0) continue;
+      p.factor_ops.push_back(g1);
+      Op g2{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+      Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
+      int blk2 = 0, blk3 = 0;
+      for (int i : lv) {
+        const SNode& n = nodes[i];
+        if (c0 >= n.k) continue;
+        int bp = std::min(b, n.k - c0);
+        if (n.nf == bp) continue;
+        int64_t tR = n.tmp, tC = n.tmp + (int64_t)b * n.nf;
+        // rest: A[r][c] -= C_old[r] * TR[c] for r, c outside the panel
+        blk2 += add_gemm(blk2, n.off + c0, n.nf, tR, n.nf, n.off, n.nf, n.nf, n.nf, bp, 1, 1, c0, c0 + bp);
+        blk3 += add_copy(blk3, tC, bp, n.off + c0, n.nf, n.nf, bp, c0, c0 + bp, 0, 0);
+        blk3 += add_copy(blk3, tR, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, bp, n.nf, 0, 0, c0, c0 + bp);
+      }
+      g2.d1 = (int)p.gemm.size();
+      g2.blocks = blk2;
+      cp.d1 = (int)p.copies.size();
+      cp.blocks = blk3;
+      p.factor_ops.push_back(g2);
+      p.factor_ops.push_back(cp);
+    }
+  }
+
+  // selected inversion: root to leaves
+  for (int h = p.n_levels - 1; h >= 0; --h) {
+    const auto& lv = by_level[h];
+    Op ga{OP_GATHER, (int)p.gather.size(), 0, 0, h};
+    int blk = 0;
+    for (int i : lv) {
+      const SNode& C = nodes[i];
+      if (C.parent < 0 || C.r == 0) continue;
+      const SNode& P = nodes[C.parent];
+      GatherDesc d{C.off, P.off, C.nf, C.k, P.nf, (int)C.bnd.size(), (int)p.maps.size(), blk};
+      for (int s : C.bnd) p.maps.push_back(front_pos(C.parent, s));
+      blk += (int)(((int64_t)C.r * C.r + 255) / 256);
+      p.gather.push_back(d);
+    }
+    ga.d1 = (int)p.gather.size();
+    ga.blocks = blk;
+    if (ga.d1 == ga.d0) continue;
+    p.selinv_ops.push_back(ga);
+    Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+    int blk1 = 0;
+    for (int i : lv) {
+      const SNode& n = nodes[i];
+      if (n.r == 0) continue;
+      int64_t tSJ = n.tmp, tJS = n.tmp + (int64_t)n.r * n.k;
+      int64_t SS = n.off + (int64_t)n.k * n.nf + n.k, SJ = n.off + (int64_t)n.k * n.nf, JS = n.off + n.k;
+      blk1 += add_gemm(blk1, SS, n.nf, SJ, n.nf, tSJ, n.k, n.r, n.k, n.r, 0, 0, 0, 0);   // G_SJ = G_SS (-Lhat)
+      blk1 += add_gemm(blk1, JS, n.nf, SS, n.nf, tJS, n.r, n.k, n.r, n.r, 1, 0, 0, 0);   // G_JS = -Uhat G_SS
+    }
+    g1.d1 = (int)p.gemm.size();
+    g1.blocks = blk1;
+    p.selinv_ops.push_back(g1);
+    Op g2{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+    Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
+    int blk2 = 0, blk3 = 0;
+    for (int i : lv) {
+      const SNode& n = nodes[i];
+      if (n.r == 0) continue;
+      int64_t tSJ = n.tmp, tJS = n.tmp + (int64_t)n.r * n.k;
+      int64_t SJ = n.off + (int64_t)n.k * n.nf, JS = n.off + n.k;
+      // G_JJ = Ainv - Uhat G_SJ = Ainv + G_JS (-Lhat)... written as Ainv + tJS * F_SJ
+      blk2 += add_gemm(blk2, tJS, n.r, SJ, n.nf, n.off, n.nf, n.k, n.k, n.r, 0, 1, 0, 0);
+      blk3 += add_copy(blk3, tSJ, n.k, SJ, n.nf, n.r, n.k, 0, 0, 0, 0);
+      blk3 += add_copy(blk3, tJS, n.r, JS, n.nf, n.k, n.r, 0, 0, 0, 0);
+    }
+    g2.d1 = (int)p.gemm.size();
+    g2.blocks = blk2;
+    cp.d1 = (int)p.copies.size();
+    cp.blocks = blk3;
+    p.selinv_ops.push_back(g2);
+    p.selinv_ops.push_back(cp);
+  }
+  p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, (4 * V + 127) / 128, -1});
+}
+
+}  // namespace cl

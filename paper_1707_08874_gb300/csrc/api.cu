@@ -1,0 +1,362 @@
+// C ABI of the library (declared in clselinv.h): plan creation, device memory
+// of the plan, and the stream-ordered compute calls.
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "kernels.cuh"
+
+using cl::Plan;
+
+struct cl_plan {
+  Plan p;
+};
+
+namespace {
+
+template <typename V>
+cudaError_t upload(V*& dst, const void* src, size_t bytes, size_t& total) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)&dst, bytes);
+  if (e != cudaSuccess) return e;
+  total += bytes;
+  return src ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaMemset(dst, 0, bytes);
+}
+
+void free_device(Plan& p) {
+  if (!p.has_device) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p.device);
+  cudaFree(p.d_arena);
+  cudaFree(p.d_status);
+  cudaFree(p.d_off);
+  cudaFree(p.d_ld);
+  cudaFree(p.d_maps);
+  cudaFree(p.d_gemm);
+  cudaFree(p.d_panels);
+  cudaFree(p.d_copies);
+  cudaFree(p.d_extadd);
+  cudaFree(p.d_gather);
+  cudaSetDevice(prev);
+  p.has_device = false;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CL_OK;
+  return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA;
+}
+
+size_t elem_bytes(const Plan& p) { return p.precision == CL_FP64 ? sizeof(double2) : sizeof(float2); }
+
+int setup_device(Plan& p) {
+  cudaGetDevice(&p.device);
+  size_t total = 0;
+  cudaError_t e;
+  const size_t arena = (size_t)p.arena_elems * p.batch * elem_bytes(p);
+  if ((e = cudaMalloc(&p.d_arena, arena)) != cudaSuccess) return cuda_status(e);
+  total += arena;
+  p.has_device = true;
+  std::vector<int64_t> off;
+  off.insert(off.end(), p.off_diag.begin(), p.off_diag.end());
+  off.insert(off.end(), p.off_fwd.begin(), p.off_fwd.end());
+  off.insert(off.end(), p.off_bwd.begin(), p.off_bwd.end());
+  std::vector<int> ld;
+  ld.insert(ld.end(), p.ld_diag.begin(), p.ld_diag.end());
+  ld.insert(ld.end(), p.ld_fwd.begin(), p.ld_fwd.end());
+  ld.insert(ld.end(), p.ld_bwd.begin(), p.ld_bwd.end());
+  if ((e = upload(p.d_status, nullptr, 4 * sizeof(int), total)) != cudaSuccess ||
+      (e = upload(p.d_off, off.data(), off.size() * sizeof(int64_t), total)) != cudaSuccess ||
+      (e = upload(p.d_ld, ld.data(), ld.size() * sizeof(int), total)) != cudaSuccess ||
+      (e = upload(p.d_maps, p.maps.data(), p.maps.size() * sizeof(int), total)) != cudaSuccess ||
+      (e = upload(p.d_gemm, p.gemm.data(), p.gemm.size() * sizeof(cl::GemmDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_panels, p.panels.data(), p.panels.size() * sizeof(cl::PanelDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_copies, p.copies.data(), p.copies.size() * sizeof(cl::CopyDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_extadd, p.extadd.data(), p.extadd.size() * sizeof(cl::ExtAddDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_gather, p.gather.data(), p.gather.size() * sizeof(cl::GatherDesc), total)) != cudaSuccess)
+    return cuda_status(e);
+  p.device_bytes = total;
+  return CL_OK;
+}
+
+bool compute_ready(const cl_plan* plan) { return plan && plan->p.has_device; }
+
+const char* kFamilyName[cl::F_COUNT] = {"zero",  "assemble", "extend_add", "panel_inverse", "gemm",
+                                         "copy",  "gather",   "extract",    "drift"};
+
+// algorithmic work of one scheduled op over all replicas: flops of the complex
+// products (8 real flops per complex multiply-add) and bytes that must cross
+// DRAM (reads + writes of the data the op touches once)
+void op_work(const Plan& p, const cl::Op& op, int& family, double& flops, double& bytes) {
+  const double es = p.precision == CL_FP64 ? 16.0 : 8.0, B = p.batch;
+  flops = bytes = 0;
+  switch (op.kind) {
+    case cl::OP_ZERO: family = cl::F_ZERO; bytes = es * p.pool_elems * B; break;
+    case cl::OP_ASSEMBLE: family = cl::F_ASSEMBLE; bytes = B * p.V * (4 * 144.0 + (8 * 9 + 9) * es); break;
+    case cl::OP_EXTADD:
+      family = cl::F_EXTADD;
+      for (int d = op.d0; d < op.d1; ++d) bytes += 3.0 * es * p.extadd[d].nfp * p.extadd[d].nfp * B;
+      break;
+    case cl::OP_PANEL:
+      family = cl::F_PANEL;
+      for (int d = op.d0; d < op.d1; ++d) {
+        double bp = p.panels[d].bp;
+        flops += 8.0 * bp * bp * bp * B;
+        bytes += 2.0 * es * bp * bp * B;
+      }
+      break;
+    case cl::OP_GEMM:
+      family = cl::F_GEMM;
+      for (int d = op.d0; d < op.d1; ++d) {
+        const cl::GemmDesc& g = p.gemm[d];
+        flops += 8.0 * g.M * g.N * g.K * B;
+        bytes += es * ((double)g.M * g.K + (double)g.K * g.N + (1.0 + g.beta) * g.M * g.N) * B;
+      }
+      break;
+    case cl::OP_COPY:
+      family = cl::F_COPY;
+      for (int d = op.d0; d < op.d1; ++d) bytes += 2.0 * es * p.copies[d].rows * p.copies[d].cols * B;
+      break;
+    case cl::OP_GATHER:
+      family = cl::F_GATHER;
+      for (int d = op.d0; d < op.d1; ++d) bytes += 2.0 * es * 9.0 * p.gather[d].rs * p.gather[d].rs * B;
+      break;
+    case cl::OP_EXTRACT: family = cl::F_EXTRACT; bytes = B * p.V * 9 * 9 * (es + 16.0); break;
+  }
+}
+
+void prof_begin(Plan& p, cudaStream_t st, cudaEvent_t& e0) {
+  e0 = nullptr;
+  if (!p.profiling) return;
+  cudaEventCreate(&e0);
+  cudaEventRecord(e0, st);
+}
+void prof_end(Plan& p, cudaStream_t st, cudaEvent_t e0, int family, double flops, double bytes) {
+  if (!p.profiling || !e0) return;
+  cudaEvent_t e1;
+  cudaEventCreate(&e1);
+  cudaEventRecord(e1, st);
+  p.prof.push_back(Plan::ProfRec{family, (void*)e0, (void*)e1, flops, bytes});
+}
+
+template <typename T, typename R>
+int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, double mu, double* Gd,
+            double* Gf, double* Gb, cudaStream_t st) {
+  T* arena = static_cast<T*>(p.d_arena);
+  for (const auto& op : ops) {
+    if (op.blocks == 0 && op.kind != cl::OP_ZERO) continue;
+    cudaEvent_t e0;
+    prof_begin(p, st, e0);
+    cudaError_t e = cl::launch_op<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (p.profiling) {
+      int fam;
+      double fl, by;
+      op_work(p, op, fam, fl, by);
+      prof_end(p, st, e0, fam, fl, by);
+    }
+  }
+  return CL_OK;
+}
+
+int run(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, double mu, double* Gd,
+        double* Gf, double* Gb, cudaStream_t st) {
+  if (p.precision == CL_FP64) return run_ops<double2, double>(p, ops, links, m, mu, Gd, Gf, Gb, st);
+  return run_ops<float2, float>(p, ops, links, m, mu, Gd, Gf, Gb, st);
+}
+
+int make_plan(int Ns, int Nt, int batch, int precision, cl_plan** out, bool device) {
+  if (!out) return CL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (device && batch < 1) return CL_ERR_INVALID_ARG;
+  cl_plan* plan = new (std::nothrow) cl_plan();
+  if (!plan) return CL_ERR_OOM;
+  try {
+    cl::analyze_host(plan->p, Ns, Nt, device ? batch : 1, precision);
+  } catch (const std::invalid_argument&) {
+    delete plan;
+    return CL_ERR_INVALID_ARG;
+  } catch (const std::bad_alloc&) {
+    delete plan;
+    return CL_ERR_OOM;
+  } catch (...) {
+    delete plan;
+    return CL_ERR_UNSUPPORTED;
+  }
+  if (device) {
+    int st = setup_device(plan->p);
+    if (st != CL_OK) {
+      free_device(plan->p);
+      delete plan;
+      return st;
+    }
+  }
+  *out = plan;
+  return CL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan) {
+  return make_plan(Ns, Nt, batch, precision, plan, true);
+}
+
+int cl_analyze_symbolic(int Ns, int Nt, int precision, cl_plan** plan) {
+  return make_plan(Ns, Nt, 1, precision, plan, false);
+}
+
+int cl_factor(cl_plan* plan, const double* links, double m, double mu, cudaStream_t stream) {
+  if (!compute_ready(plan) || !links) return CL_ERR_INVALID_ARG;
+  return run(plan->p, plan->p.factor_ops, links, m, mu, nullptr, nullptr, nullptr, stream);
+}
+
+int cl_selinv_blocks(cl_plan* plan, double* Gdiag, double* Gfwd, double* Gbwd, cudaStream_t stream) {
+  if (!compute_ready(plan)) return CL_ERR_INVALID_ARG;
+  return run(plan->p, plan->p.selinv_ops, nullptr, 0, 0, Gdiag, Gfwd, Gbwd, stream);
+}
+
+int cl_fermion_drift(cl_plan* plan, const double* links, const double* Gfwd, const double* Gbwd, double mu,
+                     double nf, double* Kf, cudaStream_t stream) {
+  if (!compute_ready(plan) || !links || !Gfwd || !Gbwd || !Kf) return CL_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  cudaEvent_t e0;
+  prof_begin(p, stream, e0);
+  int st = cuda_status(cl::launch_drift(p, links, Gfwd, Gbwd, mu, nf, Kf, stream));
+  prof_end(p, stream, e0, cl::F_DRIFT, 0.0, (double)p.batch * p.V * 4 * (3 * 144.0 + 128.0));
+  return st;
+}
+
+int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, double nf, double* Gdiag,
+                  double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream) {
+  if (!Gfwd || !Gbwd || !Kf) return CL_ERR_INVALID_ARG;
+  int st = cl_factor(plan, links, m, mu, stream);
+  if (st == CL_OK) st = cl_selinv_blocks(plan, Gdiag, Gfwd, Gbwd, stream);
+  if (st == CL_OK) st = cl_fermion_drift(plan, links, Gfwd, Gbwd, mu, nf, Kf, stream);
+  return st;
+}
+
+int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail) {
+  if (!compute_ready(plan) || !info) return CL_ERR_INVALID_ARG;
+  int h[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, plan->p.d_status, sizeof(h), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->p.d_status, 0, sizeof(h), stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  *info = h[0];
+  if (detail) {
+    detail[0] = h[0] ? h[1] : -1;
+    detail[1] = h[0] ? h[2] : -1;
+  }
+  return CL_OK;
+}
+
+int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info) {
+  if (!plan || !info) return CL_ERR_INVALID_ARG;
+  const Plan& p = plan->p;
+  std::memset(info, 0, sizeof(*info));
+  info->Ns = p.Ns;
+  info->Nt = p.Nt;
+  info->V = p.V;
+  info->N = p.N;
+  info->batch = p.batch;
+  info->precision = p.precision;
+  info->n_supernodes = (int)p.nodes.size();
+  info->n_levels = p.n_levels;
+  for (const auto& n : p.nodes) {
+    info->max_front = std::max(info->max_front, n.nf);
+    info->max_pivot_block = std::max(info->max_pivot_block, n.k);
+  }
+  info->panel = p.panel;
+  info->factor_flops = p.factor_flops;
+  info->selinv_flops = p.selinv_flops;
+  info->front_bytes = (double)p.pool_elems * p.batch * elem_bytes(p);
+  info->device_bytes = (double)p.device_bytes;
+  int launches = 1;  // drift
+  for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
+    for (const auto& op : *ops)
+      if (op.kind != cl::OP_ZERO && op.blocks > 0) ++launches;
+  info->launches_per_eval = launches;
+  return CL_OK;
+}
+
+int cl_plan_get_node(const cl_plan* plan, int i, int* parent, int* level, int* n_sep, int* n_bnd, int* sep,
+                     int* bnd) {
+  if (!plan || i < 0 || i >= (int)plan->p.nodes.size()) return CL_ERR_INVALID_ARG;
+  const cl::SNode& n = plan->p.nodes[i];
+  if (parent) *parent = n.parent;
+  if (level) *level = n.level;
+  if (n_sep) *n_sep = (int)n.sep.size();
+  if (n_bnd) *n_bnd = (int)n.bnd.size();
+  if (sep) std::memcpy(sep, n.sep.data(), n.sep.size() * sizeof(int));
+  if (bnd) std::memcpy(bnd, n.bnd.data(), n.bnd.size() * sizeof(int));
+  return CL_OK;
+}
+
+static void prof_clear(Plan& p) {
+  for (auto& r : p.prof) {
+    cudaEventDestroy((cudaEvent_t)r.ev0);
+    cudaEventDestroy((cudaEvent_t)r.ev1);
+  }
+  p.prof.clear();
+}
+
+int cl_profile_enable(cl_plan* plan, int enable) {
+  if (!compute_ready(plan)) return CL_ERR_INVALID_ARG;
+  prof_clear(plan->p);
+  plan->p.profiling = enable != 0;
+  return CL_OK;
+}
+
+int cl_profile_read(cl_plan* plan, cl_profile_entry* out, int cap, int* n) {
+  if (!compute_ready(plan) || !n || (cap > 0 && !out)) return CL_ERR_INVALID_ARG;
+  cl_profile_entry acc[cl::F_COUNT];
+  std::memset(acc, 0, sizeof(acc));
+  for (auto& r : plan->p.prof) {
+    cudaError_t e = cudaEventSynchronize((cudaEvent_t)r.ev1);
+    if (e != cudaSuccess) return cuda_status(e);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, (cudaEvent_t)r.ev0, (cudaEvent_t)r.ev1);
+    cl_profile_entry& a = acc[r.family];
+    a.launches += 1;
+    a.total_ms += ms;
+    a.flops += r.flops;
+    a.bytes += r.bytes;
+  }
+  int k = 0;
+  for (int f = 0; f < cl::F_COUNT; ++f) {
+    if (acc[f].launches == 0) continue;
+    if (k < cap) {
+      out[k] = acc[f];
+      std::strncpy(out[k].name, kFamilyName[f], sizeof(out[k].name) - 1);
+    }
+    ++k;
+  }
+  *n = k;
+  return CL_OK;
+}
+
+void cl_destroy_plan(cl_plan* plan) {
+  if (!plan) return;
+  prof_clear(plan->p);
+  free_device(plan->p);
+  delete plan;
+}
+
+const char* cl_error_string(int status) {
+  switch (status) {
+    case CL_OK: return "success";
+    case CL_ERR_INVALID_ARG: return "invalid argument";
+    case CL_ERR_OOM: return "out of device memory";
+    case CL_ERR_CUDA: return "CUDA error";
+    case CL_ERR_SINGULAR: return "singular or near-singular pivot block";
+    case CL_ERR_NONFINITE: return "non-finite result";
+    case CL_ERR_TIMEOUT: return "device wait timed out";
+    case CL_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,351 @@
+// Element-wise and small dense kernels of the selected-inversion path:
+// assembly of D into the fronts, extend-add, panel inverses, panel write-back,
+// the gather of G_SS, extraction of the selected blocks and the fermion drift.
+#include "kernels.cuh"
+
+namespace cl {
+
+// ---------------------------------------------------------------------------
+// D(m;mu) of Eq. 1 scattered into the fronts.  One thread per link (s, nu):
+// D_{s,s+nu} = +1/2 eta s_nu e^{+mu} U,  D_{s+nu,s} = -1/2 eta s_nu e^{-mu} U^{-1}
+// (e^{+-mu} on temporal hops only); the nu = 0 thread also writes D_{s,s} = m.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_assemble(const double* __restrict__ links, T* __restrict__ arena, int64_t stride,
+                           const int64_t* __restrict__ off, const int* __restrict__ ld, LatticeGeo g,
+                           double m, double mu) {
+  const int link = blockIdx.x * blockDim.x + threadIdx.x;
+  if (link >= 4 * g.V) return;
+  const int rep = blockIdx.y;
+  const int s = link >> 2, nu = link & 3;
+  T* A = arena + rep * stride;
+  const int V = g.V;
+  M3 u;
+  load_m3(links + ((int64_t)rep * 4 * V + link) * 18, u);
+  M3 ui = inv_m3(u);
+  const double ph = 0.5 * g.phase(s, nu);
+  const double ef = nu == 3 ? exp(mu) : 1.0, eb = nu == 3 ? exp(-mu) : 1.0;
+  const int64_t of = off[V + link], ob = off[5 * V + link];
+  const int lf = ld[V + link], lb = ld[5 * V + link];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      A[of + a * lf + b] = from_d2<T>(cscale(u.e[3 * a + b], ph * ef));
+      A[ob + a * lb + b] = from_d2<T>(cscale(ui.e[3 * a + b], -ph * eb));
+    }
+  if (nu == 0) {
+    const int64_t od = off[s];
+    const int l = ld[s];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) A[od + a * l + b] = from_d2<T>(make_double2(a == b ? m : 0.0, 0.0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Extend-add, pull form: every parent front entry adds the Schur-complement
+// entries of the children whose boundary contains both of its sites.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_extend_add(const ExtAddDesc* __restrict__ ds, int d0, int d1, const int* __restrict__ maps,
+                             T* __restrict__ arena, int64_t stride) {
+  const int di = find_desc(ds, d0, d1, blockIdx.x);
+  const ExtAddDesc d = ds[di];
+  const int64_t e = (int64_t)(blockIdx.x - d.blk0) * 256 + threadIdx.x;
+  if (e >= (int64_t)d.nfp * d.nfp) return;
+  const int i = (int)(e / d.nfp), j = (int)(e % d.nfp);
+  T* A = arena + blockIdx.y * stride;
+  double2 acc = make_double2(0, 0);
+  bool any = false;
+  for (int q = 0; q < d.nchild; ++q) {
+    const int ci = maps[d.map[q] + i / 3], cj = maps[d.map[q] + j / 3];
+    if (ci < 0 || cj < 0) continue;
+    const int kc = d.kc[q];
+    const T v = A[d.child[q] + (int64_t)(kc + 3 * ci + i % 3) * d.nfc[q] + kc + 3 * cj + j % 3];
+    acc = cadd(acc, to_d2(v));
+    any = true;
+  }
+  if (any) {
+    T* p = A + d.parent + e;
+    *p = from_d2<T>(cadd(to_d2(*p), acc));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Selected inversion, first step of a supernode: G_SS is read from the
+// parent's front, which holds G on the parent's whole front after its own step.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, const int* __restrict__ maps,
+                         T* __restrict__ arena, int64_t stride) {
+  const int di = find_desc(ds, d0, d1, blockIdx.x);
+  const GatherDesc d = ds[di];
+  const int r = 3 * d.rs;
+  const int64_t e = (int64_t)(blockIdx.x - d.blk0) * 256 + threadIdx.x;
+  if (e >= (int64_t)r * r) return;
+  const int i = (int)(e / r), j = (int)(e % r);
+  T* A = arena + blockIdx.y * stride;
+  const int pi = 3 * maps[d.map + i / 3] + i % 3, pj = 3 * maps[d.map + j / 3] + j % 3;
+  A[d.child + (int64_t)(d.kc + i) * d.nfc + d.kc + j] = A[d.parent + (int64_t)pi * d.nfp + pj];
+}
+
+// ---------------------------------------------------------------------------
+// In-place inverse of one diagonal panel block (bp <= kMaxPanel) by
+// Gauss-Jordan elimination with partial (row) pivoting inside the panel; the
+// row interchanges are undone on the columns at the end.  A pivot below
+// 1e-13 * max|block| records CL_ERR_SINGULAR (supernode, column).
+// ---------------------------------------------------------------------------
+constexpr int kMaxPanel = 48;
+
+template <typename T, typename R>
+__global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
+                                                       int64_t stride, int* __restrict__ status) {
+  const PanelDesc d = ds[d0 + blockIdx.x];
+  T* A = arena + blockIdx.y * stride + d.a;
+  const int bp = d.bp, tid = threadIdx.x;
+  __shared__ T S[kMaxPanel][kMaxPanel + 1];
+  __shared__ T fcol[kMaxPanel];
+  __shared__ int piv[kMaxPanel];
+  __shared__ R red[256];
+  __shared__ int sp;
+  R amax = 0;
+  for (int e = tid; e < bp * bp; e += blockDim.x) {
+    const int i = e / bp, j = e % bp;
+    T v = A[(int64_t)i * d.ld + j];
+    S[i][j] = v;
+    amax = fmax(amax, (R)hypot(v.x, v.y));
+  }
+  red[tid] = amax;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+    __syncthreads();
+  }
+  const R scale = red[0];
+  __syncthreads();
+  for (int c = 0; c < bp; ++c) {
+    if (tid < 32) {  // pivot search over rows c..bp-1, ties keep the lowest row
+      R best = -1;
+      int bi = c;
+      for (int i = c + tid; i < bp; i += 32) {
+        R v = hypot(S[i][c].x, S[i][c].y);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        R ob = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        sp = bi;
+        piv[c] = bi;
+        if (!(best >= (R)1e-13 * scale)) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
+      }
+    }
+    __syncthreads();
+    const int p = sp;
+    if (p != c)
+      for (int j = tid; j < bp; j += blockDim.x) {
+        T t = S[c][j];
+        S[c][j] = S[p][j];
+        S[p][j] = t;
+      }
+    __syncthreads();
+    const T pv = S[c][c];
+    const R n2 = pv.x * pv.x + pv.y * pv.y;
+    T inv;
+    inv.x = pv.x / n2;
+    inv.y = -pv.y / n2;
+    for (int i = tid; i < bp; i += blockDim.x) fcol[i] = S[i][c];
+    __syncthreads();
+    for (int j = tid; j < bp; j += blockDim.x) S[c][j] = (j == c) ? inv : cmul(S[c][j], inv);
+    __syncthreads();
+    for (int e = tid; e < bp * bp; e += blockDim.x) {
+      const int i = e / bp, j = e % bp;
+      if (i == c) continue;
+      const T f = fcol[i];
+      if (j == c) {
+        T v = cmul(f, inv);
+        v.x = -v.x;
+        v.y = -v.y;
+        S[i][c] = v;
+      } else {
+        T v = S[i][j];
+        T w = S[c][j];
+        v.x -= f.x * w.x - f.y * w.y;
+        v.y -= f.x * w.y + f.y * w.x;
+        S[i][j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = bp - 1; c >= 0; --c) {
+    const int p = piv[c];
+    if (p != c)
+      for (int i = tid; i < bp; i += blockDim.x) {
+        T t = S[i][c];
+        S[i][c] = S[i][p];
+        S[i][p] = t;
+      }
+    __syncthreads();
+  }
+  for (int e = tid; e < bp * bp; e += blockDim.x) {
+    const int i = e / bp, j = e % bp;
+    A[(int64_t)i * d.ld + j] = S[i][j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strided block copy with row / column exclusion ranges.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_copy(const CopyDesc* __restrict__ ds, int d0, int d1, T* __restrict__ arena, int64_t stride) {
+  const int di = find_desc(ds, d0, d1, blockIdx.x);
+  const CopyDesc d = ds[di];
+  const int64_t e = (int64_t)(blockIdx.x - d.blk0) * 256 + threadIdx.x;
+  if (e >= (int64_t)d.rows * d.cols) return;
+  const int i = (int)(e / d.cols), j = (int)(e % d.cols);
+  if ((i >= d.rm0 && i < d.rm1) || (j >= d.cm0 && j < d.cm1)) return;
+  T* A = arena + blockIdx.y * stride;
+  A[d.dst + (int64_t)i * d.ldd + j] = A[d.src + (int64_t)i * d.lds + j];
+}
+
+// ---------------------------------------------------------------------------
+// Extraction of G_{s,s}, G_{s,s+nu}, G_{s+nu,s} from the fronts (same offsets
+// as the assembly of the corresponding D blocks).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_extract(const T* __restrict__ arena, int64_t stride, const int64_t* __restrict__ off,
+                          const int* __restrict__ ld, int V, double* __restrict__ Gdiag, double* __restrict__ Gfwd,
+                          double* __restrict__ Gbwd) {
+  const int link = blockIdx.x * blockDim.x + threadIdx.x;
+  if (link >= 4 * V) return;
+  const int rep = blockIdx.y;
+  const T* A = arena + rep * stride;
+  const int64_t of = off[V + link], ob = off[5 * V + link];
+  const int lf = ld[V + link], lb = ld[5 * V + link];
+  const int64_t o = (int64_t)rep * 4 * V + link;
+  double2* F = Gfwd ? reinterpret_cast<double2*>(Gfwd) + o * 9 : nullptr;
+  double2* B = Gbwd ? reinterpret_cast<double2*>(Gbwd) + o * 9 : nullptr;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (F) F[3 * a + b] = to_d2(A[of + a * lf + b]);
+      if (B) B[3 * a + b] = to_d2(A[ob + a * lb + b]);
+    }
+  if ((link & 3) == 0 && Gdiag) {
+    const int s = link >> 2;
+    const int64_t od = off[s];
+    const int l = ld[s];
+    double2* Dg = reinterpret_cast<double2*>(Gdiag) + ((int64_t)rep * V + s) * 9;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Dg[3 * a + b] = to_d2(A[od + a * l + b]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fermion drift, Eq. 6 via Eq. 8.  With P = G_{s,s+nu}, Q = G_{s+nu,s} and
+// d_a U = i lambda_a U, d_a U^{-1} = -i U^{-1} lambda_a:
+//   Tr(P B_a) + Tr(Q F_a) = Tr(lambda_a M),
+//   M = (i/2) eta s_nu [e^{-mu} P U^{-1} + e^{+mu} U Q],
+// and Tr(lambda_a M) is read off the entries of M for the eight Gell-Mann
+// matrices.  Non-finite drift records CL_ERR_NONFINITE.
+// ---------------------------------------------------------------------------
+__global__ void k_drift(const double* __restrict__ links, const double* __restrict__ Gfwd,
+                        const double* __restrict__ Gbwd, LatticeGeo g, double mu, double nf,
+                        double* __restrict__ Kf, int* __restrict__ status) {
+  const int link = blockIdx.x * blockDim.x + threadIdx.x;
+  if (link >= 4 * g.V) return;
+  const int64_t o = (int64_t)blockIdx.y * 4 * g.V + link;
+  const int s = link >> 2, nu = link & 3;
+  M3 u, P, Q;
+  load_m3(links + o * 18, u);
+  load_m3(Gfwd + o * 18, P);
+  load_m3(Gbwd + o * 18, Q);
+  const M3 ui = inv_m3(u);
+  const M3 a = mul_m3(P, ui), b = mul_m3(u, Q);
+  const double ef = nu == 3 ? exp(mu) : 1.0, eb = nu == 3 ? exp(-mu) : 1.0;
+  const double ph = 0.5 * g.phase(s, nu) * nf;
+  M3 M;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    double2 v = cadd(cscale(a.e[i], eb), cscale(b.e[i], ef));
+    M.e[i] = make_double2(-ph * v.y, ph * v.x);  // multiply by i * ph
+  }
+  const double2* m = M.e;
+  const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
+  double2 K[8];
+  K[0] = cadd(m[3], m[1]);                                      // lambda_1
+  K[1] = make_double2(-(m[1].y - m[3].y), m[1].x - m[3].x);      // lambda_2: i (M01 - M10)
+  K[2] = csub(m[0], m[4]);                                      // lambda_3
+  K[3] = cadd(m[6], m[2]);                                      // lambda_4
+  K[4] = make_double2(-(m[2].y - m[6].y), m[2].x - m[6].x);      // lambda_5: i (M02 - M20)
+  K[5] = cadd(m[7], m[5]);                                      // lambda_6
+  K[6] = make_double2(-(m[5].y - m[7].y), m[5].x - m[7].x);      // lambda_7: i (M12 - M21)
+  K[7] = cscale(csub(cadd(m[0], m[4]), cscale(m[8], 2.0)), r3);  // lambda_8
+  double2* out = reinterpret_cast<double2*>(Kf) + o * 8;
+  bool finite = true;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    out[q] = K[q];
+    finite = finite && isfinite(K[q].x) && isfinite(K[q].y);
+  }
+  if (!finite) set_status(status, CL_ERR_NONFINITE, s, nu);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename T, typename R>
+cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links, double m, double mu,
+                      double* Gdiag, double* Gfwd, double* Gbwd, cudaStream_t st) {
+  const int64_t stride = p.arena_elems;
+  const dim3 grid1((unsigned)op.blocks, (unsigned)p.batch);
+  const LatticeGeo g{p.Ns, p.Nt, p.V};
+  switch (op.kind) {
+    case OP_ZERO:
+      return cudaMemset2DAsync(arena, (size_t)stride * sizeof(T), 0, (size_t)p.pool_elems * sizeof(T),
+                               (size_t)p.batch, st);
+    case OP_ASSEMBLE:
+      k_assemble<T><<<grid1, 128, 0, st>>>(links, arena, stride, p.d_off, p.d_ld, g, m, mu);
+      break;
+    case OP_EXTADD:
+      k_extend_add<T><<<grid1, 256, 0, st>>>(p.d_extadd, op.d0, op.d1, p.d_maps, arena, stride);
+      break;
+    case OP_PANEL:
+      k_panel_inverse<T, R><<<grid1, 256, 0, st>>>(p.d_panels, op.d0, arena, stride, p.d_status);
+      break;
+    case OP_GEMM:
+      return launch_gemm(p, op, arena, st);
+    case OP_COPY:
+      k_copy<T><<<grid1, 256, 0, st>>>(p.d_copies, op.d0, op.d1, arena, stride);
+      break;
+    case OP_GATHER:
+      k_gather<T><<<grid1, 256, 0, st>>>(p.d_gather, op.d0, op.d1, p.d_maps, arena, stride);
+      break;
+    case OP_EXTRACT:
+      k_extract<T><<<grid1, 128, 0, st>>>(arena, stride, p.d_off, p.d_ld, p.V, Gdiag, Gfwd, Gbwd);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_op<double2, double>(const Plan&, const Op&, double2*, const double*, double, double,
+                                                double*, double*, double*, cudaStream_t);
+template cudaError_t launch_op<float2, float>(const Plan&, const Op&, float2*, const double*, double, double,
+                                              double*, double*, double*, cudaStream_t);
+
+cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,
+                         double nf, double* Kf, cudaStream_t st) {
+  const LatticeGeo g{p.Ns, p.Nt, p.V};
+  const dim3 grid((unsigned)((4 * p.V + 127) / 128), (unsigned)p.batch);
+  k_drift<<<grid, 128, 0, st>>>(links, Gfwd, Gbwd, g, mu, nf, Kf, p.d_status);
+  return cudaGetLastError();
+}
+
+}  // namespace cl

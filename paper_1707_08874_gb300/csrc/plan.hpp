@@ -1,0 +1,140 @@
+// Internal plan of the selected-inversion library: the nested-dissection
+// elimination tree, the front layout in device memory and the fixed launch
+// schedule (built once per lattice shape by the host analysis).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "clselinv.h"
+
+namespace cl {
+
+// GEMM tile in complex elements (rows x cols); shared by host schedule and kernels.
+constexpr int kTileM = 64;
+constexpr int kTileN = 32;
+// Sites per leaf of the nested dissection and pivoting panel (unknowns) by precision.
+constexpr int kLeafSites = 8;
+constexpr int kPanelFP64 = 48;
+constexpr int kPanelFP32 = 48;
+
+struct SNode {
+  std::vector<int> sep;       // sites eliminated at this supernode (front order)
+  std::vector<int> bnd;       // boundary sites, ordered by position in the parent's front
+  std::vector<int> children;
+  int parent = -1;
+  int level = 0;              // height above the leaves
+  int k = 0, r = 0, nf = 0;   // pivot unknowns, boundary unknowns, front order
+  int64_t off = 0;            // front offset (elements) in the arena of one replica
+  int64_t tmp = 0;            // offset of this front's workspace (elements)
+};
+
+// C = beta*C + (neg ? -1 : +1) * A * B on one front; offsets are elements of the
+// replica arena; rows and columns inside [mask0, mask1) of C are left untouched.
+struct GemmDesc {
+  int64_t a, b, c;
+  int lda, ldb, ldc;
+  int M, N, K;
+  int neg, beta;
+  int mask0, mask1;
+  int blk0, tilesN;  // first CTA of this problem inside its launch; tiles along N
+};
+
+// In-place inverse of the diagonal panel block A[pp] (bp x bp, leading dim ld).
+struct PanelDesc {
+  int64_t a;
+  int ld, bp;
+  int node, col0;
+};
+
+// dst[i][j] = src[i][j] for i < rows, j < cols, skipping rows in [rm0,rm1) and
+// columns in [cm0,cm1).
+struct CopyDesc {
+  int64_t src, dst;
+  int lds, ldd;
+  int rows, cols;
+  int rm0, rm1, cm0, cm1;
+  int blk0;
+};
+
+// Extend-add (pull form): parent[i][j] += sum_c child_c[kc + 3*map_c[i/3] + i%3][...]
+// for both children whose boundary contains the parent sites i/3 and j/3.
+struct ExtAddDesc {
+  int64_t parent;
+  int nfp;
+  int nchild;
+  int64_t child[2];
+  int nfc[2], kc[2];
+  int map[2];  // offset into the int map table: parent front site -> child boundary index or -1
+  int blk0;
+};
+
+// Gather of G_SS (selected inversion): child[kc+i][kc+j] = parent[pos(i)][pos(j)].
+struct GatherDesc {
+  int64_t child, parent;
+  int nfc, kc, nfp, rs;  // rs = boundary sites of the child
+  int map;               // offset into the int map table: child boundary index -> parent front site
+  int blk0;
+};
+
+enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT };
+
+struct Op {
+  OpKind kind;
+  int d0, d1;     // descriptor range in the table of this kind
+  int blocks;     // CTAs per replica
+  int level;
+};
+
+struct Plan {
+  int Ns = 0, Nt = 0, V = 0, N = 0, batch = 0, precision = CL_FP64;
+  int panel = kPanelFP64;
+  bool has_device = false;
+  int device = 0;
+  std::vector<SNode> nodes;   // postorder, root last
+  int n_levels = 0;
+  double factor_flops = 0, selinv_flops = 0;
+  int64_t pool_elems = 0;     // fronts, per replica
+  int64_t tmp_elems = 0;      // workspace, per replica
+  int64_t arena_elems = 0;    // per replica (pool + workspace, padded)
+  // host tables
+  std::vector<int64_t> off_diag, off_fwd, off_bwd;  // assembly / extraction offsets
+  std::vector<int> ld_diag, ld_fwd, ld_bwd;
+  std::vector<int> maps;                            // int maps of extend-add and gather
+  std::vector<GemmDesc> gemm;
+  std::vector<PanelDesc> panels;
+  std::vector<CopyDesc> copies;
+  std::vector<ExtAddDesc> extadd;
+  std::vector<GatherDesc> gather;
+  std::vector<Op> factor_ops, selinv_ops;
+  // device memory
+  void* d_arena = nullptr;       // batch * arena_elems complex (precision-dependent)
+  int* d_status = nullptr;       // [4]: code, node, column, spare
+  int64_t* d_off = nullptr;      // off_diag | off_fwd | off_bwd
+  int* d_ld = nullptr;           // ld_diag | ld_fwd | ld_bwd
+  int* d_maps = nullptr;
+  GemmDesc* d_gemm = nullptr;
+  PanelDesc* d_panels = nullptr;
+  CopyDesc* d_copies = nullptr;
+  ExtAddDesc* d_extadd = nullptr;
+  GatherDesc* d_gather = nullptr;
+  size_t device_bytes = 0;
+  int launches_per_eval = 0;
+  // per-launch timing (cl_profile_enable)
+  struct ProfRec {
+    int family;
+    void* ev0;
+    void* ev1;
+    double flops, bytes;
+  };
+  bool profiling = false;
+  std::vector<ProfRec> prof;
+};
+
+// kernel families for profiling records
+enum Family { F_ZERO, F_ASSEMBLE, F_EXTADD, F_PANEL, F_GEMM, F_COPY, F_GATHER, F_EXTRACT, F_DRIFT, F_COUNT };
+
+// host analysis (analyze.cpp); throws std::runtime_error on invalid input
+void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision);
+
+}  // namespace cl
