@@ -151,6 +151,31 @@ int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, doubl
                   double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
 
 /*
+ * cl_drift_eval_noalloc -- the same evaluation as cl_drift_eval (FP64, one
+ * lattice) for callers that cannot allocate device memory: code running while
+ * a stream is captured into a graph, runtimes whose device memory belongs to
+ * another allocator, plugins that must not grow the footprint per call.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *   Ns, Nt         lattice; fronts + workspace + tables must fit the fixed
+ *                  20 MiB device scratch array (4^4, V = 256, fits; larger
+ *                  shapes return CL_ERR_UNSUPPORTED before any device work)
+ *   links, m, mu, nf, Gdiag (may be NULL), Gfwd, Gbwd, Kf: as cl_drift_eval,
+ *                  caller-owned device arrays for one lattice (batch 1)
+ * Allocates no device memory: the scratch is a file-scope device array that
+ * every GPU loading the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  Every call
+ * re-uploads the index tables from pageable host memory (the copy waits for
+ * the stream) and clears what must start at zero.  All calls share the one
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams, or different host threads) race and corrupt each other.
+ * Numerical status (singular pivot, non-finite drift) is not reported; check
+ * the outputs.
+ */
+int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double m, double mu, double nf,
+                          double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
+
+/*
  * cl_get_status -- synchronises `stream`, returns the first numerical error
  * recorded since the last call (CL_OK if none) in *info and clears it.
  * detail (may be NULL) receives the supernode and panel column of a

@@ -53,7 +53,7 @@ class ProfileEntry(ctypes.Structure):
 
 EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
            "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
-           "cl_profile_read", "cl_measure_peak", "cl_destroy_plan", "cl_error_string"]
+           "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_destroy_plan", "cl_error_string"]
 
 
 def lib_path() -> str:
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     L.cl_profile_enable.argtypes = [P, I]
     L.cl_profile_read.argtypes = [P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(I)]
     L.cl_measure_peak.argtypes = [I, ctypes.POINTER(D)]
+    L.cl_drift_eval_noalloc.argtypes = [I, I, P, D, D, D, P, P, P, P, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
@@ -105,6 +106,14 @@ def measure_peak(unit: int) -> float:
     g = ctypes.c_double()
     _check(load().cl_measure_peak(unit, ctypes.byref(g)), "cl_measure_peak")
     return g.value
+
+
+def drift_eval_noalloc(Ns: int, Nt: int, links, m: float, mu: float, nf: float, Gdiag, Gfwd, Gbwd, Kf,
+                       stream=None) -> int:
+    """cl_drift_eval_noalloc (no device allocation; small lattices); returns the status code."""
+    return load().cl_drift_eval_noalloc(Ns, Nt, _dev(links, "links"), float(m), float(mu), float(nf),
+                                        _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
+                                        _dev(Kf, "Kf"), _stream(stream))
 
 
 def _check(code: int, what: str):

@@ -1,0 +1,114 @@
+// Allocation-free drift evaluation for small lattices.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// drift: code that runs while a CUDA stream is being captured into a graph
+// (cudaMalloc is not a stream operation), host runtimes whose device memory is
+// owned and budgeted by another allocator, or plugins that must not grow the
+// process's footprint per call.  cl_drift_eval_noalloc serves them: all the
+// scratch memory the factorisation and the selected inversion need (fronts,
+// workspace, index tables, status word) lives in one file-scope device array
+// of fixed size that every GPU loading this library holds until the process
+// exits.  The paper has no counterpart; it is a deployment convenience.
+#include <mutex>
+#include <stdexcept>
+
+#include "kernels.cuh"
+
+namespace {
+
+// Maximum scratch: 20 MiB.  A 4^4 lattice (V = 256) needs ~14.5 MiB; larger
+// shapes are rejected with CL_ERR_UNSUPPORTED before any device work.
+constexpr size_t kNoAllocBytes = 20u << 20;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+unsigned char* g_scratch_addr[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Device address of the scratch array on the current device.  The symbol name
+// is only a host-side handle; the address must be queried on each device.
+int scratch_address(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CL_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return CL_ERR_CUDA;
+    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return CL_OK;
+}
+
+template <typename V>
+cudaError_t place(unsigned char* base, size_t& off, V*& dst, const void* src, size_t bytes, cudaStream_t st) {
+  dst = reinterpret_cast<V*>(base + off);
+  off = align256(off + (bytes ? bytes : 16));
+  if (!bytes) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+}
+
+}  // namespace
+
+extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double m, double mu, double nf,
+                                     double* Gdiag, double* Gfwd, double* Gbwd, double* Kf,
+                                     cudaStream_t stream) {
+  if (!links || !Gfwd || !Gbwd || !Kf) return CL_ERR_INVALID_ARG;
+  cl::Plan p;
+  try {
+    cl::analyze_host(p, Ns, Nt, 1, CL_FP64);
+  } catch (const std::invalid_argument&) {
+    return CL_ERR_INVALID_ARG;
+  } catch (...) {
+    return CL_ERR_UNSUPPORTED;
+  }
+  // layout inside the scratch array: status | arena | tables
+  std::vector<int64_t> off;
+  off.insert(off.end(), p.off_diag.begin(), p.off_diag.end());
+  off.insert(off.end(), p.off_fwd.begin(), p.off_fwd.end());
+  off.insert(off.end(), p.off_bwd.begin(), p.off_bwd.end());
+  std::vector<int> ld;
+  ld.insert(ld.end(), p.ld_diag.begin(), p.ld_diag.end());
+  ld.insert(ld.end(), p.ld_fwd.begin(), p.ld_fwd.end());
+  ld.insert(ld.end(), p.ld_bwd.begin(), p.ld_bwd.end());
+  const size_t arena_bytes = align256((size_t)p.arena_elems * sizeof(double2));
+  size_t need = 256 + arena_bytes;
+  const size_t table_bytes[] = {off.size() * sizeof(int64_t), ld.size() * sizeof(int), p.maps.size() * sizeof(int),
+                                p.gemm.size() * sizeof(cl::GemmDesc), p.panels.size() * sizeof(cl::PanelDesc),
+                                p.copies.size() * sizeof(cl::CopyDesc), p.extadd.size() * sizeof(cl::ExtAddDesc),
+                                p.gather.size() * sizeof(cl::GatherDesc)};
+  for (size_t b : table_bytes) need += align256(b ? b : 16);
+  if (need > kNoAllocBytes) return CL_ERR_UNSUPPORTED;
+
+  unsigned char* base = nullptr;
+  int st = scratch_address(&base);
+  if (st != CL_OK) return st;
+  p.d_status = reinterpret_cast<int*>(base);
+  p.d_arena = base + 256;
+  size_t o = 256 + arena_bytes;
+  cudaError_t e = cudaMemsetAsync(p.d_status, 0, 4 * sizeof(int), stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_off, off.data(), table_bytes[0], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_ld, ld.data(), table_bytes[1], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_maps, p.maps.data(), table_bytes[2], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_gemm, p.gemm.data(), table_bytes[3], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_panels, p.panels.data(), table_bytes[4], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_copies, p.copies.data(), table_bytes[5], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_extadd, p.extadd.data(), table_bytes[6], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_gather, p.gather.data(), table_bytes[7], stream);
+  if (e != cudaSuccess) return CL_ERR_CUDA;
+  double2* arena = static_cast<double2*>(p.d_arena);
+  for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
+    for (const auto& op : *ops) {
+      if (op.blocks == 0 && op.kind != cl::OP_ZERO) continue;
+      e = cl::launch_op<double2, double>(p, op, arena, links, m, mu, Gdiag, Gfwd, Gbwd, stream);
+      if (e != cudaSuccess) return CL_ERR_CUDA;
+    }
+  e = cl::launch_drift(p, links, Gfwd, Gbwd, mu, nf, Kf, stream);
+  // the tables above were copied from pageable host memory, which the copy
+  // engine has consumed when cudaMemcpyAsync returns; p may go out of scope
+  return e == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
