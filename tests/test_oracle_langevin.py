@@ -1,0 +1,144 @@
+"""Pins of the oracle's Langevin pieces (Eq. 3-5, Sec. 4.1): counter-based
+noise against published known-answer vectors and its moments, the gauge drift
+against finite differences of the Wilson action, exactness of the SL(3,C)
+update, gauge cooling (invariants, monotone unitarity norm) and observables."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from oracle import langevin as L
+from paper_1707_08874_gb300 import inputs
+
+NS, NT = 4, 4
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+
+
+def test_philox_known_answers():
+    n = 0
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = L.philox4x32_10(np.array([w[:4]], np.uint64), (w[4], w[5]))[0]
+        assert [int(x) for x in out] == w[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_noise_moments():
+    """<eta_a> = 0 and <eta_a eta_b> = 2 delta_ab (standard CL normalisation)."""
+    V = 8 ** 3 * 4
+    eta = np.concatenate([L.noise(1234, s, V).reshape(-1, 8) for s in range(4)])
+    n = eta.shape[0]
+    assert np.abs(eta.mean(0)).max() < 5 * np.sqrt(2.0 / n)
+    C = eta.T @ eta / n
+    np.testing.assert_allclose(np.diag(C), 2.0, atol=5 * 2 * np.sqrt(2.0 / n))
+    off = C - np.diag(np.diag(C))
+    assert np.abs(off).max() < 5 * 2 / np.sqrt(n)
+    # distinct steps, replicas and seeds give distinct streams
+    a = L.noise(1, 0, 16)
+    assert not np.allclose(a, L.noise(1, 1, 16))
+    assert not np.allclose(a, L.noise(1, 0, 16, replica=1))
+    assert not np.allclose(a, L.noise(2, 0, 16))
+
+
+@pytest.fixture(scope="module")
+def links():
+    return inputs.random_links(NS, NT, seed=31)
+
+
+def test_gauge_drift_finite_differences(links):
+    """K^g_a = -d/dh S_g(e^{i h lambda_a} U_{x,nu}) at h = 0."""
+    U = links
+    beta = 5.0
+    K = L.gauge_drift(U, beta, NS, NT)
+    lam = inputs._GM
+    h = 1e-5
+    kmax = np.abs(K).max()
+    for (s, nu) in ((0, 0), (45, 3), (130, 1), (255, 2)):
+        for a in range(8):
+            Up = U.copy()
+            Um = U.copy()
+            Up[s, nu] = scipy.linalg.expm(1j * h * lam[a]) @ U[s, nu]
+            Um[s, nu] = scipy.linalg.expm(-1j * h * lam[a]) @ U[s, nu]
+            fd = -(L.gauge_action(Up, beta, NS, NT) - L.gauge_action(Um, beta, NS, NT)) / (2 * h)
+            assert abs(fd - K[s, nu, a]) < 1e-7 * kmax, (s, nu, a)
+
+
+def test_gauge_drift_real_for_su3():
+    U = inputs.random_links(NS, NT, seed=8, sigma_im=0.0)
+    K = L.gauge_drift(U, 5.0, NS, NT)
+    assert np.abs(K.imag).max() < 1e-12 * np.abs(K).max()
+    # unit links: every plaquette is 1, the drift vanishes
+    assert np.abs(L.gauge_drift(inputs.unit_links(NS, NT), 5.0, NS, NT)).max() < 1e-14
+
+
+def test_link_update_exact(links):
+    U = links
+    V = U.shape[0]
+    rng = np.random.default_rng(0)
+    K = rng.normal(size=(V, 4, 8)) + 1j * rng.normal(size=(V, 4, 8))
+    eta = L.noise(5, 0, V)
+    U2 = L.link_update(U, K, 1e-3, eta)
+    R = U2 @ np.linalg.inv(U)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-13)
+    # real drift + real noise keep SU(3) links unitary (Eq. 4 with real K)
+    Us = inputs.random_links(NS, NT, seed=2, sigma_im=0.0)
+    U3 = L.link_update(Us, K.real, 1e-3, eta)
+    I3 = np.conj(np.swapaxes(U3, -1, -2)) @ U3
+    np.testing.assert_allclose(I3, np.broadcast_to(np.eye(3), I3.shape), atol=1e-13)
+    # R = exp(X) against a high-order Taylor series
+    X = L.algebra(1e-3 * K[0, 0] + np.sqrt(1e-3) * eta[0, 0])
+    T = np.eye(3, dtype=complex)
+    term = np.eye(3, dtype=complex)
+    for n in range(1, 30):
+        term = term @ X / n
+        T = T + term
+    np.testing.assert_allclose(L.expm_batch(X[None])[0], T, atol=1e-15)
+
+
+def test_step_size_rule():
+    K = np.zeros((4, 4, 8), complex)
+    K[1, 2, 3] = 3 + 4j
+    eps, km = L.step_size(K, 1e-3, 1e-3)
+    assert km == 5.0 and eps == pytest.approx(2e-4)
+    eps, km = L.step_size(K, 1e-3, 0.0)
+    assert eps == 1e-3
+
+
+def test_cooling_invariants(links):
+    U = links
+    n0 = L.unitarity_norm(U)
+    o0 = L.observables(U, NS, NT)
+    prev = n0
+    Uc = U
+    for _ in range(3):
+        Uc = L.gauge_cool(Uc, 1, 0.05, NS, NT)
+        n = L.unitarity_norm(Uc)
+        assert n <= prev + 1e-12
+        prev = n
+    assert prev < n0
+    o1 = L.observables(Uc, NS, NT)
+    for k in ("plaq_s", "plaq_t", "poly", "poly_inv"):
+        assert abs(o1[k] - o0[k]) < 1e-12, k
+    np.testing.assert_allclose(np.linalg.det(Uc), 1.0, atol=1e-12)
+    # det D and hence the physics are unchanged by the gauge transformation
+    a = oracle.drift_eval(NS, NT, U, 0.05, 0.25)["logdet"]
+    b = oracle.drift_eval(NS, NT, Uc, 0.05, 0.25)["logdet"]
+    assert abs(a.real - b.real) < 1e-10 * abs(a.real)
+
+
+def test_observables_unit_and_gauge_invariant(links):
+    o = L.observables(inputs.unit_links(NS, NT), NS, NT)
+    for k in ("plaq_s", "plaq_t", "poly", "poly_inv"):
+        assert abs(o[k] - 1) < 1e-15
+    assert abs(o["unitarity"]) < 1e-15
+    Om = inputs.random_gauge(NS, NT, seed=9)
+    U2 = inputs.gauge_transform(links, Om, NS, NT)
+    a = L.observables(links, NS, NT)
+    b = L.observables(U2, NS, NT)
+    for k in ("plaq_s", "plaq_t", "poly", "poly_inv"):
+        assert abs(a[k] - b[k]) < 1e-12, k
