@@ -81,6 +81,31 @@ typedef struct cl_profile_entry {
   double bytes;              /* algorithmic DRAM bytes of those launches        */
 } cl_profile_entry;
 
+/* Parameters of one complex-Langevin step (cl_langevin_step). */
+typedef struct cl_langevin_params {
+  double beta;               /* Wilson coupling: S_g = beta sum_P [1 - (Tr U_P + Tr U_P^{-1})/6] */
+  double m, mu;              /* quark mass and chemical potential of D(m;mu)   */
+  double nf;                 /* factor of the fermion drift (1 = unrooted det D) */
+  double eps_max;            /* largest Langevin step                           */
+  double kappa;              /* adaptive step eps = min(eps_max, kappa/K_max);
+                                kappa <= 0 keeps eps = eps_max                  */
+  double alpha_cool;         /* gauge-cooling step alpha0 (alpha = alpha0 / max_x |f_x|) */
+  unsigned long long seed;   /* key of the Philox4x32-10 noise stream           */
+  int n_cool;                /* gauge-cooling iterations after each update     */
+  int fermions;              /* 1: K = K^g + K^f (selected inversion); 0: K^g only */
+} cl_langevin_params;
+
+/*
+ * Record layouts used by the Langevin calls (device arrays of doubles):
+ *   state [B][4]:  t (Langevin time) | step count | eps of the last step | spare
+ *                  (caller zero-initialises; the step count keys the noise)
+ *   obs   [B][16]: plaq_s re,im | plaq_t re,im | P re,im | P' re,im |
+ *                  condensate re,im | unitarity norm | K_max | eps | t | step | spare
+ *   plaquettes (1/3) Tr U_P averaged over the 3V spatial / 3V temporal
+ *   plaquettes; P, P' = (1/(3 Ns^3)) sum Tr prod_t U_{x,t}^{+1 / -1};
+ *   condensate = (nf/V) sum_x Tr G_xx; unitarity = (1/4V) sum Tr(U U^dag) - 3.
+ */
+
 /*
  * cl_analyze -- symbolic analysis, done once per lattice shape (Sec. 3: the
  * "sparse LU" needs an ordering; the paper's solver does not describe its
@@ -149,6 +174,54 @@ int cl_fermion_drift(cl_plan* plan, const double* links, const double* Gfwd, con
  */
 int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, double nf,
                   double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
+
+/*
+ * cl_gauge_drift -- gauge part of Eq. 5 for the Wilson action:
+ *   K^g_{a,s,nu} = (i beta/6) sum_{6 staples A} Tr[lambda_a (U A - A^{-1} U^{-1})]
+ *   (A the staple with Tr U_P = Tr(U_{s,nu} A)), i.e. K^g = -d_a S_g.
+ *   links device [B][V][4][3][3]; Kg device out [B][V][4][8].
+ */
+int cl_gauge_drift(cl_plan* plan, const double* links, double beta, double* Kg, cudaStream_t stream);
+
+/*
+ * cl_link_update -- Eq. 3-4 with a fixed step: U <- R U,
+ *   R = exp(i sum_a lambda_a (eps K_a + sqrt(eps) eta_a)),
+ * eta_a real Gaussian, <eta_a eta_b> = 2 delta_ab, from Philox4x32-10 with
+ * counter (4 s + nu, half, step, replica) and key = seed, Box-Muller on
+ * u = (x + 1/2) 2^-32 (half 0 gives eta_1..4, half 1 eta_5..8).
+ *   links device in/out [B][V][4][3][3]; K device [B][V][4][8]; eps > 0.
+ */
+int cl_link_update(cl_plan* plan, double* links, const double* K, double eps, unsigned long long seed,
+                   long long step, cudaStream_t stream);
+
+/*
+ * cl_gauge_cool -- n_cool steepest-descent steps of gauge cooling (Sec. 4.1
+ * names it; the form follows the unitarity-norm gradient):
+ *   f_x = sum_nu [U_{x,nu} U_{x,nu}^dag - U_{x-nu,nu}^dag U_{x-nu,nu}] (traceless),
+ *   alpha = alpha0 / max_x |f_x|_F, Omega_x = exp(-alpha f_x),
+ *   U_{x,nu} <- Omega_x U_{x,nu} Omega_{x+nu}^{-1}.
+ */
+int cl_gauge_cool(cl_plan* plan, double* links, int n_cool, double alpha0, cudaStream_t stream);
+
+/*
+ * cl_observables -- plaquettes, Polyakov loops, unitarity norm and (when
+ * Gdiag != NULL) the chiral condensate of the current links into obs [B][16]
+ * (layout above; eps, t, step fields are zero).
+ */
+int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, double nf, double* obs,
+                   cudaStream_t stream);
+
+/*
+ * cl_langevin_step -- one stochastic Euler step of Eq. 3-5 for every replica:
+ * drift K = K^g + K^f (K^f by the selected inversion of D(m;mu)), adaptive
+ * step eps = min(eps_max, kappa / K_max), observables of the configuration
+ * before the update (condensate from this step's G_xx), the update with noise
+ * keyed by (seed, state.step), n_cool gauge-cooling steps, then
+ * state.t += eps, state.step += 1.
+ *   links device in/out; prm host struct; state device [B][4]; obs device [B][16].
+ */
+int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm, double* state, double* obs,
+                     cudaStream_t stream);
 
 /*
  * cl_drift_eval_noalloc -- the same evaluation as cl_drift_eval (FP64, one

@@ -213,3 +213,26 @@ def observables(U, Ns, Nt, Gdiag=None, nf=1.0):
     if Gdiag is not None:
         out["condensate"] = complex(nf * np.trace(Gdiag, axis1=1, axis2=2).sum() / V)
     return out
+
+
+def langevin_step(U, prm: dict, step: int, Ns: int, Nt: int, replica: int = 0):
+    """One stochastic Euler step (Eq. 3-5) in the order of the library's step:
+    K = K^g (+ K^f), eps from K_max, observables of the configuration before the
+    update, update with noise(seed, step), cooling.  Returns (U', obs, eps)."""
+    from . import drift_eval
+    V = U.shape[0]
+    K = gauge_drift(U, prm["beta"], Ns, Nt)
+    Gd = None
+    if prm.get("fermions", 1):
+        r = drift_eval(Ns, Nt, U, prm["m"], prm["mu"], prm.get("nf", 1.0))
+        K = K + r["Kf"]
+        Gd = r["Gdiag"]
+    eps, km = step_size(K, prm["eps_max"], prm.get("kappa", 0.0))
+    obs = observables(U, Ns, Nt, Gd, prm.get("nf", 1.0))
+    obs["kmax"] = km
+    obs["eps"] = eps
+    eta = noise(prm["seed"], step, V, replica)
+    U2 = link_update(U, K, eps, eta)
+    if prm.get("n_cool", 0) > 0:
+        U2 = gauge_cool(U2, prm["n_cool"], prm["alpha_cool"], Ns, Nt)
+    return U2, obs, eps

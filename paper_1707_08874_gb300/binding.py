@@ -51,9 +51,28 @@ class ProfileEntry(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class LangevinParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("m", ctypes.c_double), ("mu", ctypes.c_double), ("nf", ctypes.c_double),
+                ("eps_max", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha_cool", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("n_cool", ctypes.c_int), ("fermions", ctypes.c_int)]
+
+
+OBS_FIELDS = ["plaq_s_re", "plaq_s_im", "plaq_t_re", "plaq_t_im", "poly_re", "poly_im", "poly_inv_re",
+              "poly_inv_im", "cond_re", "cond_im", "unitarity", "kmax", "eps", "t", "step", "spare"]
+
+
+def obs_dict(row) -> dict:
+    """One replica's observables record (16 doubles) as a dict of complex / float values."""
+    r = [float(x) for x in row]
+    return dict(plaq_s=complex(r[0], r[1]), plaq_t=complex(r[2], r[3]), poly=complex(r[4], r[5]),
+                poly_inv=complex(r[6], r[7]), condensate=complex(r[8], r[9]), unitarity=r[10], kmax=r[11],
+                eps=r[12], t=r[13], step=r[14])
+
+
 EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
            "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
-           "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_destroy_plan", "cl_error_string"]
+           "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
+           "cl_observables", "cl_langevin_step", "cl_destroy_plan", "cl_error_string"]
 
 
 def lib_path() -> str:
@@ -86,6 +105,11 @@ def load(build_if_missing: bool = True):
     L.cl_profile_read.argtypes = [P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(I)]
     L.cl_measure_peak.argtypes = [I, ctypes.POINTER(D)]
     L.cl_drift_eval_noalloc.argtypes = [I, I, P, D, D, D, P, P, P, P, P]
+    L.cl_gauge_drift.argtypes = [P, P, D, P, P]
+    L.cl_link_update.argtypes = [P, P, P, D, ctypes.c_ulonglong, ctypes.c_longlong, P]
+    L.cl_gauge_cool.argtypes = [P, P, I, D, P]
+    L.cl_observables.argtypes = [P, P, P, D, P, P]
+    L.cl_langevin_step.argtypes = [P, P, ctypes.POINTER(LangevinParams), P, P, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
@@ -210,6 +234,36 @@ class Plan:
         detail = (ctypes.c_int * 2)()
         _check(load().cl_get_status(self._h, _stream(stream), ctypes.byref(info), detail), "cl_get_status")
         return info.value, (detail[0], detail[1])
+
+    # -- Langevin pieces ---------------------------------------------------
+    def _dbl(self, t, name):
+        import torch
+        if t is None:
+            return None
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+        return ctypes.c_void_p(t.data_ptr())
+
+    def gauge_drift(self, links, beta: float, Kg, stream=None):
+        _check(load().cl_gauge_drift(self._h, _dev(links, "links"), float(beta), _dev(Kg, "Kg"), _stream(stream)),
+               "cl_gauge_drift")
+
+    def link_update(self, links, K, eps: float, seed: int, step: int, stream=None):
+        _check(load().cl_link_update(self._h, _dev(links, "links"), _dev(K, "K"), float(eps), int(seed), int(step),
+                                     _stream(stream)), "cl_link_update")
+
+    def gauge_cool(self, links, n_cool: int, alpha0: float, stream=None):
+        _check(load().cl_gauge_cool(self._h, _dev(links, "links"), int(n_cool), float(alpha0), _stream(stream)),
+               "cl_gauge_cool")
+
+    def observables(self, links, Gdiag, nf: float, obs, stream=None):
+        _check(load().cl_observables(self._h, _dev(links, "links"), _dev(Gdiag, "Gdiag"), float(nf),
+                                     self._dbl(obs, "obs"), _stream(stream)), "cl_observables")
+
+    def langevin_step(self, links, params: dict, state, obs, stream=None):
+        prm = LangevinParams(**params)
+        _check(load().cl_langevin_step(self._h, _dev(links, "links"), ctypes.byref(prm), self._dbl(state, "state"),
+                                       self._dbl(obs, "obs"), _stream(stream)), "cl_langevin_step")
 
     def profile_enable(self, on: bool = True):
         _check(load().cl_profile_enable(self._h, 1 if on else 0), "cl_profile_enable")

@@ -38,6 +38,8 @@ void free_device(Plan& p) {
   cudaFree(p.d_copies);
   cudaFree(p.d_extadd);
   cudaFree(p.d_gather);
+  for (double* q : {p.d_Gdiag, p.d_Gfwd, p.d_Gbwd, p.d_K, p.d_Ui, p.d_F, p.d_Om, p.d_Omi, p.d_part}) cudaFree(q);
+  cudaFree(p.d_slots);
   cudaSetDevice(prev);
   p.has_device = false;
 }
@@ -74,6 +76,18 @@ int setup_device(Plan& p) {
       (e = upload(p.d_copies, p.copies.data(), p.copies.size() * sizeof(cl::CopyDesc), total)) != cudaSuccess ||
       (e = upload(p.d_extadd, p.extadd.data(), p.extadd.size() * sizeof(cl::ExtAddDesc), total)) != cudaSuccess ||
       (e = upload(p.d_gather, p.gather.data(), p.gather.size() * sizeof(cl::GatherDesc), total)) != cudaSuccess)
+    return cuda_status(e);
+  const size_t B = p.batch, V = p.V;
+  if ((e = upload(p.d_Gdiag, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_Gfwd, nullptr, B * V * 72 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_Gbwd, nullptr, B * V * 72 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_K, nullptr, B * V * 64 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_Ui, nullptr, B * V * 72 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_F, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_Om, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_Omi, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_part, nullptr, B * cl::obs_partial_doubles(p) * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_slots, nullptr, B * 4 * sizeof(unsigned long long), total)) != cudaSuccess)
     return cuda_status(e);
   p.device_bytes = total;
   return CL_OK;
@@ -235,6 +249,57 @@ int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, doubl
   if (st == CL_OK) st = cl_selinv_blocks(plan, Gdiag, Gfwd, Gbwd, stream);
   if (st == CL_OK) st = cl_fermion_drift(plan, links, Gfwd, Gbwd, mu, nf, Kf, stream);
   return st;
+}
+
+int cl_gauge_drift(cl_plan* plan, const double* links, double beta, double* Kg, cudaStream_t stream) {
+  if (!compute_ready(plan) || !links || !Kg) return CL_ERR_INVALID_ARG;
+  return cuda_status(cl::launch_gauge_drift(plan->p, links, plan->p.d_Ui, beta, Kg, 0, stream));
+}
+
+int cl_gauge_cool(cl_plan* plan, double* links, int n_cool, double alpha0, cudaStream_t stream) {
+  if (!compute_ready(plan) || !links || n_cool < 0) return CL_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  return cuda_status(cl::launch_cool(p, links, n_cool, alpha0, p.d_F, p.d_Om, p.d_Omi, p.d_slots, stream));
+}
+
+int cl_link_update(cl_plan* plan, double* links, const double* K, double eps, unsigned long long seed, long long step,
+                   cudaStream_t stream) {
+  if (!compute_ready(plan) || !links || !K || !(eps > 0)) return CL_ERR_INVALID_ARG;
+  cl::LangevinArgs a{eps, 0.0, eps, seed, step};
+  return cuda_status(cl::launch_update(plan->p, links, K, a, plan->p.d_slots, nullptr, stream));
+}
+
+int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, double nf, double* obs,
+                   cudaStream_t stream) {
+  if (!compute_ready(plan) || !links || !obs) return CL_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  cl::LangevinArgs a{0.0, 0.0, 0.0, 0ull, 0};
+  cudaError_t e = cl::launch_obs_partial(p, links, p.d_Ui, Gdiag, p.d_part, true, stream);
+  if (e == cudaSuccess)
+    e = cl::launch_obs_final(p, p.d_part, Gdiag != nullptr, nf, p.d_slots, a, nullptr, obs, 0, stream);
+  return cuda_status(e);
+}
+
+int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm, double* state, double* obs,
+                     cudaStream_t stream) {
+  if (!compute_ready(plan) || !links || !prm || !state || !obs) return CL_ERR_INVALID_ARG;
+  if (!(prm->eps_max > 0) || prm->n_cool < 0) return CL_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  int st = CL_OK;
+  const bool ferm = prm->fermions != 0;
+  if (ferm) {
+    st = cl_drift_eval(plan, links, prm->m, prm->mu, prm->nf, p.d_Gdiag, p.d_Gfwd, p.d_Gbwd, p.d_K, stream);
+    if (st != CL_OK) return st;
+  }
+  cl::LangevinArgs a{prm->eps_max, prm->kappa, 0.0, prm->seed, 0};
+  cudaError_t e = cl::launch_gauge_drift(p, links, p.d_Ui, prm->beta, p.d_K, ferm ? 1 : 0, stream);
+  if (e == cudaSuccess) e = cl::launch_kmax(p, p.d_K, p.d_slots, stream);
+  if (e == cudaSuccess) e = cl::launch_obs_partial(p, links, p.d_Ui, ferm ? p.d_Gdiag : nullptr, p.d_part, false, stream);
+  if (e == cudaSuccess) e = cl::launch_update(p, links, p.d_K, a, p.d_slots, state, stream);
+  if (e == cudaSuccess && prm->n_cool > 0)
+    e = cl::launch_cool(p, links, prm->n_cool, prm->alpha_cool, p.d_F, p.d_Om, p.d_Omi, p.d_slots, stream);
+  if (e == cudaSuccess) e = cl::launch_obs_final(p, p.d_part, ferm, prm->nf, p.d_slots, a, state, obs, 1, stream);
+  return cuda_status(e);
 }
 
 int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail) {

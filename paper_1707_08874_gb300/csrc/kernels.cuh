@@ -19,4 +19,31 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,
                          double nf, double* Kf, cudaStream_t st);
 
+// ---- Langevin step (langevin.cu) ----
+// scalar arguments of the update / step-size rule
+struct LangevinArgs {
+  double eps_max, kappa;  // eps = min(eps_max, kappa / K_max), kappa <= 0: eps_max
+  double fixed_eps;       // > 0: use this step and `step` instead of the rule and the state
+  unsigned long long seed;
+  long long step;
+};
+// observables record per replica (doubles): plaq_s re,im | plaq_t re,im | poly re,im |
+// poly_inv re,im | condensate re,im | unitarity | K_max | eps | t | step | spare
+constexpr int kObsFields = 16;
+// Langevin state per replica (doubles): t | step | eps of the last step | spare
+constexpr int kStateFields = 4;
+
+cudaError_t launch_gauge_drift(const Plan& p, const double* U, double* Ui, double beta, double* K, int acc,
+                               cudaStream_t st);
+cudaError_t launch_kmax(const Plan& p, const double* K, unsigned long long* slots, cudaStream_t st);
+cudaError_t launch_update(const Plan& p, double* U, const double* K, const LangevinArgs& a,
+                          const unsigned long long* slots, const double* state, cudaStream_t st);
+cudaError_t launch_cool(const Plan& p, double* U, int n_cool, double alpha0, double* F, double* Om, double* Omi,
+                        unsigned long long* slots, cudaStream_t st);
+cudaError_t launch_obs_partial(const Plan& p, const double* U, double* Ui, const double* Gdiag, double* part,
+                               bool invert, cudaStream_t st);
+cudaError_t launch_obs_final(const Plan& p, const double* part, bool has_g, double nf, const unsigned long long* slots,
+                             const LangevinArgs& a, double* state, double* obs, int advance, cudaStream_t st);
+int obs_partial_doubles(const Plan& p);
+
 }  // namespace cl

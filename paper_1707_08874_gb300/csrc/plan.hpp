@@ -118,6 +118,18 @@ struct Plan {
   CopyDesc* d_copies = nullptr;
   ExtAddDesc* d_extadd = nullptr;
   GatherDesc* d_gather = nullptr;
+  // Langevin-step buffers (all replicas): G blocks, drift, link inverses,
+  // cooling fields, reduction partials and max slots
+  double* d_Gdiag = nullptr;
+  double* d_Gfwd = nullptr;
+  double* d_Gbwd = nullptr;
+  double* d_K = nullptr;
+  double* d_Ui = nullptr;
+  double* d_F = nullptr;
+  double* d_Om = nullptr;
+  double* d_Omi = nullptr;
+  double* d_part = nullptr;
+  unsigned long long* d_slots = nullptr;
   size_t device_bytes = 0;
   int launches_per_eval = 0;
   // per-launch timing (cl_profile_enable)
