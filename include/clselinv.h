@@ -99,11 +99,15 @@ typedef struct cl_langevin_params {
  * Record layouts used by the Langevin calls (device arrays of doubles):
  *   state [B][4]:  t (Langevin time) | step count | eps of the last step | spare
  *                  (caller zero-initialises; the step count keys the noise)
- *   obs   [B][16]: plaq_s re,im | plaq_t re,im | P re,im | P' re,im |
- *                  condensate re,im | unitarity norm | K_max | eps | t | step | spare
+ *   obs   [B][20]: plaq_s re,im | plaq_t re,im | P re,im | P' re,im |
+ *                  condensate re,im | unitarity norm | K_max | eps | t | step | spare |
+ *                  density re,im | spare, spare
  *   plaquettes (1/3) Tr U_P averaged over the 3V spatial / 3V temporal
  *   plaquettes; P, P' = (1/(3 Ns^3)) sum Tr prod_t U_{x,t}^{+1 / -1};
- *   condensate = (nf/V) sum_x Tr G_xx; unitarity = (1/4V) sum Tr(U U^dag) - 3.
+ *   condensate = (nf/V) sum_x Tr G_xx; unitarity = (1/4V) sum Tr(U U^dag) - 3;
+ *   density n = (nf/V) Tr(G dD/dmu) = (nf/V) d log det D / d mu, from the
+ *   temporal blocks G_{x,x+t}, G_{x+t,x} only (Sec. 3: the fermionic
+ *   observables need only G where D is non-zero).
  */
 
 /*
@@ -204,12 +208,13 @@ int cl_link_update(cl_plan* plan, double* links, const double* K, double eps, un
 int cl_gauge_cool(cl_plan* plan, double* links, int n_cool, double alpha0, cudaStream_t stream);
 
 /*
- * cl_observables -- plaquettes, Polyakov loops, unitarity norm and (when
- * Gdiag != NULL) the chiral condensate of the current links into obs [B][16]
- * (layout above; eps, t, step fields are zero).
+ * cl_observables -- plaquettes, Polyakov loops, unitarity norm, and from the
+ * selected blocks (when given) the chiral condensate (Gdiag) and the quark-
+ * number density (Gfwd, Gbwd at chemical potential mu), into obs [B][20]
+ * (layout above; eps, t, step fields are zero).  Gdiag/Gfwd/Gbwd may be NULL.
  */
-int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, double nf, double* obs,
-                   cudaStream_t stream);
+int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, const double* Gfwd, const double* Gbwd,
+                   double mu, double nf, double* obs, cudaStream_t stream);
 
 /*
  * cl_langevin_step -- one stochastic Euler step of Eq. 3-5 for every replica:
@@ -218,7 +223,7 @@ int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, doub
  * before the update (condensate from this step's G_xx), the update with noise
  * keyed by (seed, state.step), n_cool gauge-cooling steps, then
  * state.t += eps, state.step += 1.
- *   links device in/out; prm host struct; state device [B][4]; obs device [B][16].
+ *   links device in/out; prm host struct; state device [B][4]; obs device [B][20].
  */
 int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm, double* state, double* obs,
                      cudaStream_t stream);
@@ -289,7 +294,9 @@ int cl_profile_read(cl_plan* plan, cl_profile_entry* out, int cap, int* n);
 /*
  * cl_measure_peak -- measures an arithmetic peak of the current device with a
  * throughput kernel (independent FMA / MMA chains on every SM, ~10 ms):
- * unit 0 = FP64 tensor-core MMA (m8n8k4), 1 = FP64 FMA, 2 = FP32 FMA.
+ * unit 0 = FP64 tensor-core MMA (m8n8k4), 1 = FP64 FMA, 2 = FP32 FMA,
+ * 3 = BF16 tensor-core MMA (mma.sync m16n8k16, FP32 accumulate),
+ * 4 = INT8 tensor-core MMA (mma.sync m16n8k32, INT32 accumulate; "GFLOP/s" = Gop/s).
  * *gflops receives GFLOP/s.  Allocates and frees a small device buffer.
  */
 int cl_measure_peak(int unit, double* gflops);

@@ -184,6 +184,26 @@ def condensate(Gdiag, nf: float = 1.0) -> complex:
     return complex(nf * np.trace(Gd, axis1=-2, axis2=-1).sum() / V)
 
 
+def number_density(Ns: int, Nt: int, links, Gfwd, Gbwd, mu: float, nf: float = 1.0) -> complex:
+    """n = (nf/V) Tr(G dD/dmu) = (nf/V) d log det D / d mu from the temporal blocks:
+    dD_{x,x+t}/dmu = D_{x,x+t}, dD_{x+t,x}/dmu = -D_{x+t,x}  (Sec. 3: the fermionic
+    observables need only G where D is non-zero)."""
+    U = _c128(links)
+    V = volume(Ns, Nt)
+    s = np.arange(V)
+    x = s % Ns
+    y = (s // Ns) % Ns
+    z = (s // (Ns * Ns)) % Ns
+    t = s // (Ns ** 3)
+    eta = (-1.0) ** (x + y + z)
+    sg = np.where(t == Nt - 1, -1.0, 1.0)
+    ph = 0.5 * eta * sg
+    Df = ph[:, None, None] * np.exp(mu) * U[:, 3]
+    Db = -ph[:, None, None] * np.exp(-mu) * np.linalg.inv(U[:, 3])
+    tr = np.einsum("xij,xji->x", Gbwd[:, 3], Df) - np.einsum("xij,xji->x", Gfwd[:, 3], Db)
+    return complex(nf * tr.sum() / V)
+
+
 def neighbour_table(Ns: int, Nt: int) -> np.ndarray:
     """up[s, nu] = index of s + nu-hat (periodic), plain integer geometry."""
     V = volume(Ns, Nt)

@@ -215,6 +215,14 @@ def observables(U, Ns, Nt, Gdiag=None, nf=1.0):
     return out
 
 
+def observables_full(U, Ns, Nt, blocks, mu, nf=1.0):
+    """observables() plus the quark-number density from the selected blocks."""
+    from . import number_density
+    out = observables(U, Ns, Nt, blocks["Gdiag"], nf)
+    out["density"] = number_density(Ns, Nt, U, blocks["Gfwd"], blocks["Gbwd"], mu, nf)
+    return out
+
+
 def langevin_step(U, prm: dict, step: int, Ns: int, Nt: int, replica: int = 0):
     """One stochastic Euler step (Eq. 3-5) in the order of the library's step:
     K = K^g (+ K^f), eps from K_max, observables of the configuration before the
@@ -229,6 +237,9 @@ def langevin_step(U, prm: dict, step: int, Ns: int, Nt: int, replica: int = 0):
         Gd = r["Gdiag"]
     eps, km = step_size(K, prm["eps_max"], prm.get("kappa", 0.0))
     obs = observables(U, Ns, Nt, Gd, prm.get("nf", 1.0))
+    if Gd is not None:
+        from . import number_density
+        obs["density"] = number_density(Ns, Nt, U, r["Gfwd"], r["Gbwd"], prm["mu"], prm.get("nf", 1.0))
     obs["kmax"] = km
     obs["eps"] = eps
     eta = noise(prm["seed"], step, V, replica)

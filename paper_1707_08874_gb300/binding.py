@@ -58,15 +58,17 @@ class LangevinParams(ctypes.Structure):
 
 
 OBS_FIELDS = ["plaq_s_re", "plaq_s_im", "plaq_t_re", "plaq_t_im", "poly_re", "poly_im", "poly_inv_re",
-              "poly_inv_im", "cond_re", "cond_im", "unitarity", "kmax", "eps", "t", "step", "spare"]
+              "poly_inv_im", "cond_re", "cond_im", "unitarity", "kmax", "eps", "t", "step", "spare",
+              "density_re", "density_im", "spare2", "spare3"]
+OBS_LEN = len(OBS_FIELDS)
 
 
 def obs_dict(row) -> dict:
-    """One replica's observables record (16 doubles) as a dict of complex / float values."""
+    """One replica's observables record (20 doubles) as a dict of complex / float values."""
     r = [float(x) for x in row]
     return dict(plaq_s=complex(r[0], r[1]), plaq_t=complex(r[2], r[3]), poly=complex(r[4], r[5]),
                 poly_inv=complex(r[6], r[7]), condensate=complex(r[8], r[9]), unitarity=r[10], kmax=r[11],
-                eps=r[12], t=r[13], step=r[14])
+                eps=r[12], t=r[13], step=r[14], density=complex(r[16], r[17]))
 
 
 EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
@@ -108,7 +110,7 @@ def load(build_if_missing: bool = True):
     L.cl_gauge_drift.argtypes = [P, P, D, P, P]
     L.cl_link_update.argtypes = [P, P, P, D, ctypes.c_ulonglong, ctypes.c_longlong, P]
     L.cl_gauge_cool.argtypes = [P, P, I, D, P]
-    L.cl_observables.argtypes = [P, P, P, D, P, P]
+    L.cl_observables.argtypes = [P, P, P, P, P, D, D, P, P]
     L.cl_langevin_step.argtypes = [P, P, ctypes.POINTER(LangevinParams), P, P, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
@@ -256,9 +258,10 @@ class Plan:
         _check(load().cl_gauge_cool(self._h, _dev(links, "links"), int(n_cool), float(alpha0), _stream(stream)),
                "cl_gauge_cool")
 
-    def observables(self, links, Gdiag, nf: float, obs, stream=None):
-        _check(load().cl_observables(self._h, _dev(links, "links"), _dev(Gdiag, "Gdiag"), float(nf),
-                                     self._dbl(obs, "obs"), _stream(stream)), "cl_observables")
+    def observables(self, links, Gdiag, Gfwd, Gbwd, mu: float, nf: float, obs, stream=None):
+        _check(load().cl_observables(self._h, _dev(links, "links"), _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"),
+                                     _dev(Gbwd, "Gbwd"), float(mu), float(nf), self._dbl(obs, "obs"),
+                                     _stream(stream)), "cl_observables")
 
     def langevin_step(self, links, params: dict, state, obs, stream=None):
         prm = LangevinParams(**params)

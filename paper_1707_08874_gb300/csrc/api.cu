@@ -269,12 +269,12 @@ int cl_link_update(cl_plan* plan, double* links, const double* K, double eps, un
   return cuda_status(cl::launch_update(plan->p, links, K, a, plan->p.d_slots, nullptr, stream));
 }
 
-int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, double nf, double* obs,
-                   cudaStream_t stream) {
+int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, const double* Gfwd, const double* Gbwd,
+                   double mu, double nf, double* obs, cudaStream_t stream) {
   if (!compute_ready(plan) || !links || !obs) return CL_ERR_INVALID_ARG;
   Plan& p = plan->p;
   cl::LangevinArgs a{0.0, 0.0, 0.0, 0ull, 0};
-  cudaError_t e = cl::launch_obs_partial(p, links, p.d_Ui, Gdiag, p.d_part, true, stream);
+  cudaError_t e = cl::launch_obs_partial(p, links, p.d_Ui, Gdiag, Gfwd, Gbwd, mu, p.d_part, true, stream);
   if (e == cudaSuccess)
     e = cl::launch_obs_final(p, p.d_part, Gdiag != nullptr, nf, p.d_slots, a, nullptr, obs, 0, stream);
   return cuda_status(e);
@@ -294,7 +294,9 @@ int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm
   cl::LangevinArgs a{prm->eps_max, prm->kappa, 0.0, prm->seed, 0};
   cudaError_t e = cl::launch_gauge_drift(p, links, p.d_Ui, prm->beta, p.d_K, ferm ? 1 : 0, stream);
   if (e == cudaSuccess) e = cl::launch_kmax(p, p.d_K, p.d_slots, stream);
-  if (e == cudaSuccess) e = cl::launch_obs_partial(p, links, p.d_Ui, ferm ? p.d_Gdiag : nullptr, p.d_part, false, stream);
+  if (e == cudaSuccess)
+    e = cl::launch_obs_partial(p, links, p.d_Ui, ferm ? p.d_Gdiag : nullptr, ferm ? p.d_Gfwd : nullptr,
+                               ferm ? p.d_Gbwd : nullptr, prm->mu, p.d_part, false, stream);
   if (e == cudaSuccess) e = cl::launch_update(p, links, p.d_K, a, p.d_slots, state, stream);
   if (e == cudaSuccess && prm->n_cool > 0)
     e = cl::launch_cool(p, links, prm->n_cool, prm->alpha_cool, p.d_F, p.d_Om, p.d_Omi, p.d_slots, stream);

@@ -28,8 +28,9 @@ struct LangevinArgs {
   long long step;
 };
 // observables record per replica (doubles): plaq_s re,im | plaq_t re,im | poly re,im |
-// poly_inv re,im | condensate re,im | unitarity | K_max | eps | t | step | spare
-constexpr int kObsFields = 16;
+// poly_inv re,im | condensate re,im | unitarity | K_max | eps | t | step | spare |
+// density re,im | spare, spare
+constexpr int kObsFields = 20;
 // Langevin state per replica (doubles): t | step | eps of the last step | spare
 constexpr int kStateFields = 4;
 
@@ -40,8 +41,8 @@ cudaError_t launch_update(const Plan& p, double* U, const double* K, const Lange
                           const unsigned long long* slots, const double* state, cudaStream_t st);
 cudaError_t launch_cool(const Plan& p, double* U, int n_cool, double alpha0, double* F, double* Om, double* Omi,
                         unsigned long long* slots, cudaStream_t st);
-cudaError_t launch_obs_partial(const Plan& p, const double* U, double* Ui, const double* Gdiag, double* part,
-                               bool invert, cudaStream_t st);
+cudaError_t launch_obs_partial(const Plan& p, const double* U, double* Ui, const double* Gdiag, const double* Gfwd,
+                               const double* Gbwd, double mu, double* part, bool invert, cudaStream_t st);
 cudaError_t launch_obs_final(const Plan& p, const double* part, bool has_g, double nf, const unsigned long long* slots,
                              const LangevinArgs& a, double* state, double* obs, int advance, cudaStream_t st);
 int obs_partial_doubles(const Plan& p);

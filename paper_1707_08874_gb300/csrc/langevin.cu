@@ -320,11 +320,14 @@ __global__ void k_clear_slot(unsigned long long* slots, int which) {
 }
 
 // Observables, first pass: per-block partial sums (fixed order) of
-// [plaq_s re,im | plaq_t re,im | poly re,im | poly_inv re,im | cond re,im | unitarity]
+// [plaq_s re,im | plaq_t re,im | poly re,im | poly_inv re,im | cond re,im | unitarity |
+//  density re,im]; density = Tr(G_{x+t,x} dD_{x,x+t}/dmu + G_{x,x+t} dD_{x+t,x}/dmu)
 constexpr int kObsBlock = 128;
-constexpr int kObsN = 11;
+constexpr int kObsN = 13;
 __global__ void __launch_bounds__(kObsBlock) k_obs_partial(const double* __restrict__ U, const double* __restrict__ Ui,
-                                                           const double* __restrict__ Gdiag, Geo4 g,
+                                                           const double* __restrict__ Gdiag,
+                                                           const double* __restrict__ Gfwd,
+                                                           const double* __restrict__ Gbwd, double chem, Geo4 g,
                                                            double* __restrict__ part) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t rep = blockIdx.y;
@@ -361,6 +364,19 @@ __global__ void __launch_bounds__(kObsBlock) k_obs_partial(const double* __restr
       const double2 t = tr3(G);
       v[8] = t.x;
       v[9] = t.y;
+    }
+    if (Gfwd && Gbwd) {
+      // dD_{x,x+t}/dmu = D_{x,x+t} = 1/2 eta_t s_t e^{mu} U; dD_{x+t,x}/dmu = -D_{x+t,x} = 1/2 eta_t s_t e^{-mu} U^{-1}
+      const LatticeGeo lg{g.Ns, g.Nt, g.V};
+      const double ph = 0.5 * lg.phase(s, 3);
+      M3 gf, gb;
+      load_m3(Gfwd + ((rep * g.V + s) * 4 + 3) * 18, gf);
+      load_m3(Gbwd + ((rep * g.V + s) * 4 + 3) * 18, gb);
+      const double2 a = tr3(mul_m3(gb, load_link(U, rep, g.V, s, 3)));
+      const double2 b = tr3(mul_m3(gf, load_link(Ui, rep, g.V, s, 3)));
+      const double ef = ph * exp(chem), eb = ph * exp(-chem);
+      v[11] = ef * a.x + eb * b.x;
+      v[12] = ef * a.y + eb * b.y;
     }
     for (int nu = 0; nu < 4; ++nu) {
       const M3 u = load_link(U, rep, g.V, s, nu);
@@ -412,6 +428,9 @@ __global__ void k_obs_final(const double* __restrict__ part, int nblk, Geo4 g, d
   const double kmax = read_max(slots + 4 * rep);
   o[11] = kmax;
   o[12] = o[13] = o[14] = o[15] = 0.0;
+  o[16] = has_g ? nf * v[11] / V : 0.0;
+  o[17] = has_g ? nf * v[12] / V : 0.0;
+  o[18] = o[19] = 0.0;
   if (advance) {
     const double eps = a.fixed_eps > 0 ? a.fixed_eps : step_eps(kmax, a.eps_max, a.kappa);
     double* st = state + 4 * rep;
@@ -464,12 +483,12 @@ cudaError_t launch_cool(const Plan& p, double* U, int n_cool, double alpha0, dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_obs_partial(const Plan& p, const double* U, double* Ui, const double* Gdiag, double* part,
-                               bool invert, cudaStream_t st) {
+cudaError_t launch_obs_partial(const Plan& p, const double* U, double* Ui, const double* Gdiag, const double* Gfwd,
+                               const double* Gbwd, double mu, double* part, bool invert, cudaStream_t st) {
   const Geo4 g{p.Ns, p.Nt, p.V};
   if (invert) k_invert_links<<<grid_links(p), 128, 0, st>>>(U, Ui, p.V);
   const dim3 gs((unsigned)((p.V + kObsBlock - 1) / kObsBlock), (unsigned)p.batch);
-  k_obs_partial<<<gs, kObsBlock, 0, st>>>(U, Ui, Gdiag, g, part);
+  k_obs_partial<<<gs, kObsBlock, 0, st>>>(U, Ui, Gdiag, Gfwd, Gbwd, mu, g, part);
   return cudaGetLastError();
 }
 

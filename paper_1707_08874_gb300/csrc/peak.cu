@@ -49,10 +49,69 @@ __global__ void p_dmma(double* out) {
   for (int q = 0; q < 4; ++q) s += c[q][0] + c[q][1];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// BF16 tensor MMA (mma.sync m16n8k16, FP32 accumulate); every chain gets its
+// own operand registers so no two MMAs are identical
+__global__ void p_bmma(double* out) {
+  const unsigned lane = threadIdx.x & 31;
+  unsigned a[4][4], b[4][2];
+  float c[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[q][i] = 0x3c003c00u + lane * 7u + q * 131u + i * 17u;
+    b[q][0] = 0x3b803b80u + lane * 3u + q * 11u;
+    b[q][1] = 0x3b803b80u + lane * 5u + q * 13u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[q][i] = 0.f;
+  }
+  for (int it = 0; it < kIters / 4; ++it)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+f"(c[q][0]), "+f"(c[q][1]), "+f"(c[q][2]), "+f"(c[q][3])
+          : "r"(a[q][0]), "r"(a[q][1]), "r"(a[q][2]), "r"(a[q][3]), "r"(b[q][0]), "r"(b[q][1]));
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s += c[q][i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+// INT8 tensor MMA (mma.sync m16n8k32, INT32 accumulate), distinct operands per chain
+__global__ void p_imma(double* out) {
+  const unsigned lane = threadIdx.x & 31;
+  unsigned a[4][4], b[4][2];
+  int c[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[q][i] = 0x01020304u * (lane + 1) + q * 0x01010101u + i;
+    b[q][0] = 0x02030405u * (lane + 3) + q;
+    b[q][1] = 0x03040506u * (lane + 5) + q;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[q][i] = 0;
+  }
+  for (int it = 0; it < kIters / 4; ++it)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      asm volatile(
+          "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+r"(c[q][0]), "+r"(c[q][1]), "+r"(c[q][2]), "+r"(c[q][3])
+          : "r"(a[q][0]), "r"(a[q][1]), "r"(a[q][2]), "r"(a[q][3]), "r"(b[q][0]), "r"(b[q][1]));
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s += c[q][i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 }  // namespace
 
 extern "C" int cl_measure_peak(int unit, double* gflops) {
-  if (!gflops || unit < 0 || unit > 2) return CL_ERR_INVALID_ARG;
+  if (!gflops || unit < 0 || unit > 4) return CL_ERR_INVALID_ARG;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -72,9 +131,15 @@ extern "C" int cl_measure_peak(int unit, double* gflops) {
     } else if (unit == 1) {
       p_dfma<<<blocks, threads>>>(buf, 0.999, 1e-3);
       flops = 2.0 * 8 * kIters * (double)n;
-    } else {
+    } else if (unit == 2) {
       p_ffma<<<blocks, threads>>>(buf, 0.999f, 1e-3f);
       flops = 2.0 * 16 * kIters * (double)n;
+    } else if (unit == 3) {
+      p_bmma<<<blocks, threads>>>(buf);
+      flops = 2.0 * 16 * 8 * 16 * 4 * (kIters / 4) * (double)(n / 32);
+    } else {
+      p_imma<<<blocks, threads>>>(buf);
+      flops = 2.0 * 16 * 8 * 32 * 4 * (kIters / 4) * (double)(n / 32);
     }
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);

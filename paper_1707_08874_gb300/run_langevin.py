@@ -53,7 +53,7 @@ def main(argv=None):
                                  sigma_im=0.1 if args.start == "random" else 0.0)
     U = torch.from_numpy(U0).to("cuda")
     state = torch.zeros((args.batch, 4), dtype=torch.float64, device="cuda")
-    obs = torch.zeros((args.batch, 16), dtype=torch.float64, device="cuda")
+    obs = torch.zeros((args.batch, B.OBS_LEN), dtype=torch.float64, device="cuda")
     prm = dict(beta=args.beta, m=args.m, mu=args.mu, nf=args.nf, eps_max=args.eps_max, kappa=args.kappa,
                alpha_cool=args.alpha_cool, seed=args.seed, n_cool=args.n_cool, fermions=1)
     out = open(args.out, "w") if args.out else sys.stdout
@@ -72,7 +72,7 @@ def main(argv=None):
         r0 = rows[0]
         for k in ("t", "eps", "kmax", "unitarity"):
             rec[k] = r0[k]
-        for k in ("plaq_s", "plaq_t", "poly", "poly_inv", "condensate"):
+        for k in ("plaq_s", "plaq_t", "poly", "poly_inv", "condensate", "density"):
             rec[k] = [r0[k].real, r0[k].imag]
             if args.batch > 1:
                 m = np.mean([r[k] for r in rows])

@@ -76,14 +76,17 @@ def test_gauge_cooling(plan, links2):
 def test_observables(plan, links2):
     B = _B()
     V = NS ** 3 * NT
-    Gd = np.stack([oracle.drift_eval(NS, NT, links2[b], 0.05, 0.25)["Gdiag"] for b in range(2)])
-    obs = torch.zeros((2, 16), dtype=torch.float64, device="cuda")
-    plan.observables(_dev(links2), _dev(Gd), 1.0, obs)
+    res = [oracle.drift_eval(NS, NT, links2[b], 0.05, 0.25) for b in range(2)]
+    Gd = np.stack([r["Gdiag"] for r in res])
+    Gf = np.stack([r["Gfwd"] for r in res])
+    Gb = np.stack([r["Gbwd"] for r in res])
+    obs = torch.zeros((2, 20), dtype=torch.float64, device="cuda")
+    plan.observables(_dev(links2), _dev(Gd), _dev(Gf), _dev(Gb), 0.25, 1.0, obs)
     o = obs.cpu().numpy()
     for b in range(2):
         got = B.obs_dict(o[b])
-        want = L.observables(links2[b], NS, NT, Gd[b])
-        for k in ("plaq_s", "plaq_t", "poly", "poly_inv", "condensate"):
+        want = L.observables_full(links2[b], NS, NT, res[b], 0.25)
+        for k in ("plaq_s", "plaq_t", "poly", "poly_inv", "condensate", "density"):
             assert abs(got[k] - want[k]) < 1e-12 * max(1.0, abs(want[k])), k
         assert abs(got["unitarity"] - want["unitarity"]) < 1e-12 * max(1.0, want["unitarity"])
 
@@ -97,7 +100,7 @@ def test_langevin_steps_match_oracle(plan, links2, kappa, n_cool):
                n_cool=n_cool, fermions=1)
     U = _dev(links2)
     state = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
-    obs = torch.zeros((2, 16), dtype=torch.float64, device="cuda")
+    obs = torch.zeros((2, 20), dtype=torch.float64, device="cuda")
     ref = [links2[0].copy(), links2[1].copy()]
     t = [0.0, 0.0]
     for step in range(2):
@@ -111,7 +114,7 @@ def test_langevin_steps_match_oracle(plan, links2, kappa, n_cool):
             go = B.obs_dict(o[b])
             assert abs(go["eps"] - eps) < 1e-9 * eps  # eps = kappa / K_max inherits the drift error
             assert abs(go["kmax"] - ro["kmax"]) < 1e-9 * ro["kmax"]
-            for k in ("plaq_s", "plaq_t", "poly", "poly_inv", "condensate"):
+            for k in ("plaq_s", "plaq_t", "poly", "poly_inv", "condensate", "density"):
                 assert abs(go[k] - ro[k]) < 1e-9 * max(1.0, abs(ro[k])), (step, b, k)
             assert go["step"] == step + 1 and abs(go["t"] - t[b]) < 1e-9 * t[b]
     got = U.cpu().numpy()
@@ -128,7 +131,7 @@ def test_pure_gauge_su3_stays_unitary():
     prm = dict(beta=5.5, m=0.05, mu=0.0, nf=1.0, eps_max=1e-2, kappa=0.0, alpha_cool=0.05, seed=1,
                n_cool=0, fermions=0)
     state = torch.zeros((1, 4), dtype=torch.float64, device="cuda")
-    obs = torch.zeros((1, 16), dtype=torch.float64, device="cuda")
+    obs = torch.zeros((1, 20), dtype=torch.float64, device="cuda")
     for _ in range(20):
         p.langevin_step(U, prm, state, obs)
     torch.cuda.synchronize()

@@ -289,3 +289,15 @@ def test_unit_column_solves_match_inverse(rand):
     cols = np.array([0, 1, 2, 400, 767])
     X = oracle.solve_unit_columns(LU, piv, cols)
     np.testing.assert_allclose(X, G[:, cols], atol=1e-13 * np.abs(G).max())
+
+
+def test_number_density_is_mu_derivative(rand):
+    """n = (1/V) d log det D / d mu, evaluated from the temporal selected blocks."""
+    U, D, res = rand
+    h = 1e-5
+    dp = _logdet(U, mu=MU + h)
+    dm = _logdet(U, mu=MU - h)
+    fd = complex(dp.real - dm.real, np.angle(np.exp(1j * (dp.imag - dm.imag)))) / (2 * h)
+    V = NS ** 3 * NT
+    n = oracle.number_density(NS, NT, U, res["Gfwd"], res["Gbwd"], MU)
+    assert abs(n * V - fd) < 1e-6 * abs(fd)
