@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp64_emu", "mixed"], default="fp64")
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -176,7 +176,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = B.CL_FP64 if args.precision == "fp64" else B.CL_MIXED_FP32
+    prec = {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[args.precision]
     bsz = args.batch
     plan = B.Plan.analyze(NS, NT, bsz, prec)
     info = plan.info
@@ -196,7 +196,7 @@ def run_ours(args, rank, world, local):
     st, _ = plan.get_status()
     if st != B.CL_OK:
         raise RuntimeError("drift evaluation reported %s" % B.error_string(st))
-    peak_unit = 0 if prec == B.CL_FP64 else 2
+    peak_unit = {B.CL_FP64: 0, B.CL_FP64_EMU: 3, B.CL_MIXED_FP32: 2}[prec]
     peak_gflops = B.measure_peak(peak_unit)
 
     clocks = Clocks(local)
@@ -251,12 +251,16 @@ def run_ours(args, rank, world, local):
     gemm_flops = g.get("flops", 0.0) / max(1, g.get("launches", 1))
     achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
     peak = peak_gflops / 1e3
+    if prec == B.CL_FP64_EMU:
+        peak /= 28.0  # 28 BF16 digit products per FP64-equivalent product
     total_prof_ms = sum(v["total_ms"] for v in prof.values())
     flops_eval = info["factor_flops"] + info["selinv_flops"]
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == B.CL_FP64 else "f32", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": {B.CL_FP64: "f64", B.CL_FP64_EMU: "f64 (exact bf16 digit products, fp32 accumulate)",
+                  B.CL_MIXED_FP32: "f32"}[prec], "data": "synthetic",
         "config": {"workload": "8^3x4 lattice, m=0.05, mu=0.25, links exp(i c.lambda), c ~ N(0,0.5)+iN(0,0.1)",
                    "lattice": "8^3x4", "batch": bsz, "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single",
@@ -264,11 +268,13 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": world * bsz / (e2e_ms / 1e3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": info["launches_per_eval"] * args.steps,
-        "roofline": {"bound": "tensor" if prec == B.CL_FP64 else "alu", "kernel": "gemm",
+        "roofline": {"bound": "alu" if prec == B.CL_MIXED_FP32 else "tensor", "kernel": "gemm",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None,
-                     "peak_source": ("FP64 MMA (mma.sync m8n8k4) throughput measured live on this GPU"
-                                     if prec == B.CL_FP64 else "FP32 FMA throughput measured live on this GPU"),
+                     "peak_source": {B.CL_FP64: "FP64 MMA (mma.sync m8n8k4) throughput measured live on this GPU",
+                                     B.CL_FP64_EMU: "BF16 MMA (mma.sync m16n8k16) throughput measured live on this "
+                                                    "GPU / 28 digit products (FP64-equivalent ceiling)",
+                                     B.CL_MIXED_FP32: "FP32 FMA throughput measured live on this GPU"}[prec],
                      "traffic": NCU_TRAFFIC.get((args.precision, bsz)),
                      "gemm_share_of_kernel_time": g.get("total_ms", 0.0) / total_prof_ms if total_prof_ms else None},
         "front_tflops": flops_eval * bsz / (ms / 1e3) / 1e12,

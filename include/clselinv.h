@@ -52,6 +52,8 @@ extern "C" {
 /* arithmetic of the sparse factorisation and selected inversion */
 #define CL_FP64 0       /* all front arithmetic in FP64 (FP64 tensor-core MMA) */
 #define CL_MIXED_FP32 1 /* FP32 fronts, FP64 input/output and drift            */
+#define CL_FP64_EMU 2   /* FP64 fronts; the front GEMMs run as exact 7-digit
+                           BF16 products on the tensor cores (FP64 accuracy)    */
 
 typedef struct cl_plan cl_plan;
 
@@ -59,7 +61,7 @@ typedef struct cl_plan cl_plan;
 typedef struct cl_plan_info {
   int Ns, Nt, V, N;          /* lattice and matrix order N = 3V                */
   int batch;                 /* replicas per call                               */
-  int precision;             /* CL_FP64 or CL_MIXED_FP32                        */
+  int precision;             /* CL_FP64, CL_MIXED_FP32 or CL_FP64_EMU           */
   int n_supernodes;          /* separators of the nested dissection            */
   int n_levels;              /* height of the elimination tree + 1              */
   int max_front;             /* largest front order (unknowns)                  */
@@ -117,7 +119,7 @@ typedef struct cl_langevin_params {
  *   Ns, Nt     even extents >= 4 (even for the staggered phases, >= 4 so that
  *              s+nu and s-nu are distinct sites)
  *   batch      number of independent lattices (replicas) per call, >= 1
- *   precision  CL_FP64 or CL_MIXED_FP32
+ *   precision  CL_FP64, CL_MIXED_FP32 or CL_FP64_EMU
  *   plan       out: library-owned handle, release with cl_destroy_plan
  * Builds the elimination tree, supernodes, front index maps and the launch
  * schedule on the host, then allocates and uploads all device memory the

@@ -24,6 +24,7 @@ CL_ERR_TIMEOUT = 6
 CL_ERR_UNSUPPORTED = 7
 CL_FP64 = 0
 CL_MIXED_FP32 = 1
+CL_FP64_EMU = 2
 
 _lib = None
 

@@ -135,14 +135,15 @@ int64_t tiles(int M, int N) {
 void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision) {
   if (Ns < 4 || Nt < 4 || (Ns & 1) || (Nt & 1)) throw std::invalid_argument("Ns, Nt must be even and >= 4");
   if (Ns > 64 || Nt > 128) throw std::invalid_argument("lattice too large");
-  if (precision != CL_FP64 && precision != CL_MIXED_FP32) throw std::invalid_argument("precision");
+  if (precision != CL_FP64 && precision != CL_MIXED_FP32 && precision != CL_FP64_EMU)
+    throw std::invalid_argument("precision");
   p.Ns = Ns;
   p.Nt = Nt;
   p.V = Ns * Ns * Ns * Nt;
   p.N = 3 * p.V;
   p.batch = batch;
   p.precision = precision;
-  p.panel = precision == CL_FP64 ? kPanelFP64 : kPanelFP32;
+  p.panel = precision == CL_FP64 ? kPanelFP64 : precision == CL_FP64_EMU ? kPanelEmu : kPanelFP32;
   Geo g{Ns, Nt, {Ns, Ns, Ns, Nt}};
   const int V = p.V;
 
@@ -428,6 +429,41 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision) {
     p.selinv_ops.push_back(cp);
   }
   p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, (4 * V + 127) / 128, -1});
+
+  // split-digit workspace of the FP64 emulation: per GEMM launch the problems
+  // are laid out one after the other from offset 0 (launches run in order)
+  p.emu.clear();
+  p.emu_words = p.emu_ints = 0;
+  if (precision == CL_FP64_EMU) {
+    p.emu.resize(p.gemm.size());
+    for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
+      for (const auto& op : *ops) {
+        if (op.kind != OP_GEMM) continue;
+        int64_t w = 0, in = 0;
+        int it = 0;
+        for (int d = op.d0; d < op.d1; ++d) {
+          const GemmDesc& g = p.gemm[d];
+          EmuDesc& e = p.emu[d];
+          e.Mp = (g.M + 63) / 64 * 64;
+          e.Np = (g.N + 31) / 32 * 32;
+          e.Kp = (g.K + 31) / 32 * 32;
+          const int64_t nch = e.Kp / 32;
+          e.adig = w;
+          w += (7LL * e.Mp * e.Kp + 63) / 64 * 64;
+          e.bdig = w;
+          w += (7LL * e.Kp * e.Np + 63) / 64 * 64;
+          e.aexp = in;
+          in += nch * e.Mp;
+          e.bexp = in;
+          in += nch * e.Np;
+          e.it0 = it;
+          e.items = (int)(e.Mp * nch + (e.Np / 32) * nch);
+          it += e.items;
+        }
+        p.emu_words = std::max(p.emu_words, w);
+        p.emu_ints = std::max(p.emu_ints, in);
+      }
+  }
 }
 
 }  // namespace cl

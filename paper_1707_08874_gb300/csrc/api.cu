@@ -38,6 +38,9 @@ void free_device(Plan& p) {
   cudaFree(p.d_copies);
   cudaFree(p.d_extadd);
   cudaFree(p.d_gather);
+  cudaFree(p.d_emu);
+  cudaFree(p.d_emu_words);
+  cudaFree(p.d_emu_ints);
   for (double* q : {p.d_Gdiag, p.d_Gfwd, p.d_Gbwd, p.d_K, p.d_Ui, p.d_F, p.d_Om, p.d_Omi, p.d_part}) cudaFree(q);
   cudaFree(p.d_slots);
   cudaSetDevice(prev);
@@ -49,7 +52,7 @@ int cuda_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA;
 }
 
-size_t elem_bytes(const Plan& p) { return p.precision == CL_FP64 ? sizeof(double2) : sizeof(float2); }
+size_t elem_bytes(const Plan& p) { return p.precision == CL_MIXED_FP32 ? sizeof(float2) : sizeof(double2); }
 
 int setup_device(Plan& p) {
   cudaGetDevice(&p.device);
@@ -89,6 +92,12 @@ int setup_device(Plan& p) {
       (e = upload(p.d_part, nullptr, B * cl::obs_partial_doubles(p) * sizeof(double), total)) != cudaSuccess ||
       (e = upload(p.d_slots, nullptr, B * 4 * sizeof(unsigned long long), total)) != cudaSuccess)
     return cuda_status(e);
+  if (p.precision == CL_FP64_EMU) {
+    if ((e = upload(p.d_emu, p.emu.data(), p.emu.size() * sizeof(cl::EmuDesc), total)) != cudaSuccess ||
+        (e = upload(p.d_emu_words, nullptr, B * p.emu_words * sizeof(unsigned), total)) != cudaSuccess ||
+        (e = upload(p.d_emu_ints, nullptr, B * p.emu_ints * sizeof(int), total)) != cudaSuccess)
+      return cuda_status(e);
+  }
   p.device_bytes = total;
   return CL_OK;
 }
@@ -102,7 +111,7 @@ const char* kFamilyName[cl::F_COUNT] = {"zero",  "assemble", "extend_add", "pane
 // products (8 real flops per complex multiply-add) and bytes that must cross
 // DRAM (reads + writes of the data the op touches once)
 void op_work(const Plan& p, const cl::Op& op, int& family, double& flops, double& bytes) {
-  const double es = p.precision == CL_FP64 ? 16.0 : 8.0, B = p.batch;
+  const double es = p.precision == CL_MIXED_FP32 ? 8.0 : 16.0, B = p.batch;
   flops = bytes = 0;
   switch (op.kind) {
     case cl::OP_ZERO: family = cl::F_ZERO; bytes = es * p.pool_elems * B; break;
@@ -175,8 +184,8 @@ int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double
 
 int run(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, double mu, double* Gd,
         double* Gf, double* Gb, cudaStream_t st) {
-  if (p.precision == CL_FP64) return run_ops<double2, double>(p, ops, links, m, mu, Gd, Gf, Gb, st);
-  return run_ops<float2, float>(p, ops, links, m, mu, Gd, Gf, Gb, st);
+  if (p.precision == CL_MIXED_FP32) return run_ops<float2, float>(p, ops, links, m, mu, Gd, Gf, Gb, st);
+  return run_ops<double2, double>(p, ops, links, m, mu, Gd, Gf, Gb, st);
 }
 
 int make_plan(int Ns, int Nt, int batch, int precision, cl_plan** out, bool device) {

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const GemmDesc* __restrict__ d
 }  // namespace
 
 cudaError_t launch_gemm(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
+  if (p.precision == CL_FP64_EMU) return launch_gemm_emu(p, op, arena, st);
   const dim3 grid((unsigned)op.blocks, (unsigned)p.batch);
   k_gemm_f64<<<grid, 128, 0, st>>>(p.d_gemm, op.d0, op.d1, arena, p.arena_elems);
   return cudaGetLastError();

@@ -1,0 +1,343 @@
+// FP64-accurate complex GEMM on the BF16 tensor cores (precision CL_FP64_EMU).
+//
+// GB300's FP64 pipe delivers ~1.1 TFLOP/s, its BF16 tensor pipe ~590 TFLOP/s
+// through mma.sync.  Each FP64 operand is written exactly as
+//   a = sign * 2^e * sum_{p=1..7} d_p 2^{-8p} + (truncation < 2^{e-56}),
+// with integer digits 0 <= d_p <= 255 (exact in BF16) and one exponent e per
+// row (A) or column (B) and per chunk of 32 complex k.  The product is the sum
+// over digit pairs p + q <= 8 (28 BF16 products) of integer dot products: each
+// one is exact in the FP32 accumulator for the leading levels (sums < 2^24) and
+// rounded below FP64 resolution for the others.  Level sums are scaled by
+// powers of two and accumulated across chunks in triple-float (three FP32
+// words, error-free two-sums), relative to the largest row / column exponent;
+// FP64 arithmetic appears only in the epilogue.  Accuracy equals an FP64 GEMM
+// to within a small factor (numpy emulation of the same digits and roundings:
+// normwise relative error 4e-16 - 1.1e-15 against 5e-16 - 1e-15 for FP64).
+//
+// Complex products are one real product of twice the size, as in the FP64
+// kernel: A is the real M x 2K matrix of interleaved pairs; B is expanded into
+// [[br, bi], [-bi, br]] blocks when its fragment is loaded from shared memory.
+#include "kernels.cuh"
+
+namespace cl {
+namespace {
+
+constexpr int kDig = 7;       // base-256 digits per operand
+constexpr int kLevels = 7;    // digit pairs p + q <= 6 (0-based) -> 28 products
+constexpr int kChunk = 32;    // complex k per exponent chunk (64 real k)
+constexpr int kStrideW = 36;  // shared-memory row stride in 32-bit words (32 + 4 pad)
+
+__device__ __forceinline__ int exp_of(double v) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  return E == 0 ? -2000 : E - 1023;  // zero / subnormal count as absent
+}
+
+// BF16 bit patterns of the 7 digits of |v| 2^{-e} (< 1), truncated, with v's sign
+__device__ __forceinline__ void digits(double v, int e, unsigned short (&d)[kDig]) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned short sgn = b < 0 ? 0x8000u : 0u;
+  unsigned long long X = 0;
+  if (E != 0 && E != 0x7FF) {
+    const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = (E - 1023) + 4 - e;  // X = m 2^sh = |v| 2^{56-e}; sh <= 3
+    if (sh >= 0) X = m << sh;
+    else if (sh > -64) X = m >> (-sh);
+  }
+#pragma unroll
+  for (int p = 0; p < kDig; ++p) {
+    const unsigned dg = (unsigned)(X >> (48 - 8 * p)) & 0xFFu;
+    d[p] = dg ? (unsigned short)((__float_as_uint((float)dg) >> 16) | sgn) : (unsigned short)0;
+  }
+}
+
+// Split pass: one warp per item.  A items (row, chunk): lanes take the 32
+// complex k of the chunk.  B items (32 columns, chunk): lanes take a column
+// and loop over the chunk's k.  Padding (rows >= M, columns >= N, k >= K) is
+// written as zero digits so the GEMM needs no bounds checks.
+__global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
+                                                   int d0, int d1, const double2* __restrict__ arena,
+                                                   int64_t stride, unsigned* __restrict__ words,
+                                                   int* __restrict__ ints, int64_t wstride, int64_t istride,
+                                                   int total) {
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= total) return;
+  int lo = d0, hi = d1 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ed[mid].it0 <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmDesc g = gd[lo];
+  const EmuDesc e = ed[lo];
+  const double2* base = arena + blockIdx.y * stride;
+  unsigned* W = words + blockIdx.y * wstride;
+  int* I = ints + blockIdx.y * istride;
+  const int nch = e.Kp / kChunk;
+  int it = item - e.it0;
+  const int nA = e.Mp * nch;
+  if (it < nA) {
+    const int row = it / nch, c = it % nch;
+    const int k = c * kChunk + lane;
+    double2 v = make_double2(0, 0);
+    if (row < g.M && k < g.K) v = base[g.a + (int64_t)row * g.lda + k];
+    int ex = max(exp_of(v.x), exp_of(v.y));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+    const int ee = ex + 1;
+    if (lane == 0) I[e.aexp + (int64_t)c * e.Mp + row] = ee;
+    unsigned short dr[kDig], di[kDig];
+    digits(v.x, ee, dr);
+    digits(v.y, ee, di);
+    unsigned* dst = W + e.adig + (int64_t)row * e.Kp + k;
+#pragma unroll
+    for (int p = 0; p < kDig; ++p) dst[(int64_t)p * e.Mp * e.Kp] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
+  } else {
+    it -= nA;
+    const int grp = it / nch, c = it % nch;
+    const int n = grp * 32 + lane;
+    int ex = -2000;
+    for (int kk = 0; kk < kChunk; ++kk) {
+      const int k = c * kChunk + kk;
+      if (n < g.N && k < g.K) {
+        const double2 v = base[g.b + (int64_t)k * g.ldb + n];
+        ex = max(ex, max(exp_of(v.x), exp_of(v.y)));
+      }
+    }
+    const int ee = ex + 1;
+    I[e.bexp + (int64_t)c * e.Np + n] = ee;
+    for (int kk = 0; kk < kChunk; ++kk) {
+      const int k = c * kChunk + kk;
+      double2 v = make_double2(0, 0);
+      if (n < g.N && k < g.K) v = base[g.b + (int64_t)k * g.ldb + n];
+      unsigned short dr[kDig], di[kDig];
+      digits(v.x, ee, dr);
+      digits(v.y, ee, di);
+      unsigned* dst = W + e.bdig + (int64_t)k * e.Np + n;
+#pragma unroll
+      for (int p = 0; p < kDig; ++p) dst[(int64_t)p * e.Kp * e.Np] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
+    }
+  }
+}
+
+__device__ __forceinline__ void bmma(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                     unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float pow2f(int k) { return k < -126 ? 0.f : __int_as_float((k + 127) << 23); }
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+
+constexpr int kSmemA = kDig * 64 * kStrideW;  // words
+constexpr int kSmemB = kDig * kChunk * kStrideW;
+constexpr size_t kEmuSmemBytes = (size_t)(kSmemA + kSmemB) * 4 + (64 + 32) * 2 * sizeof(int);
+
+// 128 threads, 2 x 2 warps; each warp owns 32 rows x 32 real columns
+// (2 x 4 MMA tiles of 16 x 8); CTA tile 64 complex rows x 32 complex columns.
+__global__ void __launch_bounds__(128, 2) k_gemm_emu(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
+                                                     int d0, int d1, double2* __restrict__ arena, int64_t stride,
+                                                     const unsigned* __restrict__ words, const int* __restrict__ ints,
+                                                     int64_t wstride, int64_t istride) {
+  extern __shared__ __align__(16) unsigned smem[];
+  unsigned* As = smem;
+  unsigned* Bs = smem + kSmemA;
+  int* rsc = reinterpret_cast<int*>(Bs + kSmemB);  // [64] row exponent of the chunk minus the row maximum
+  int* csc = rsc + 64;                             // [32] same for the columns
+  int* Rm = csc + 32;                              // [64] row maxima
+  int* Sm = Rm + 64;                               // [32] column maxima
+
+  const int di = find_desc(gd, d0, d1, blockIdx.x);
+  const GemmDesc g = gd[di];
+  const EmuDesc e = ed[di];
+  const int t = blockIdx.x - g.blk0;
+  const int row0 = (t / g.tilesN) * kTileM, col0 = (t % g.tilesN) * kTileN;
+  const unsigned* Wd = words + blockIdx.y * wstride;
+  const int* Id = ints + blockIdx.y * istride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 16;  // complex offsets in the tile
+  const int nch = e.Kp / kChunk;
+
+  // reference exponents: maxima over all chunks
+  if (tid < 64) {
+    int m = -4000;
+    for (int c = 0; c < nch; ++c) m = max(m, Id[e.aexp + (int64_t)c * e.Mp + row0 + tid]);
+    Rm[tid] = m;
+  } else if (tid < 96) {
+    int m = -4000;
+    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid - 64]);
+    Sm[tid - 64] = m;
+  }
+
+  float h[2][4][4], mi[2][4][4], lo[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) h[i][j][r] = mi[i][j][r] = lo[i][j][r] = 0.f;
+
+  for (int c = 0; c < nch; ++c) {
+    // stage the chunk's digits: A [7][64 rows][32 words], B [7][32 k][32 words]
+    for (int q = tid; q < kDig * 64 * 8; q += 128) {
+      const int p = q / (64 * 8), r = (q / 8) % 64, piece = q % 8;
+      cp16(As + (p * 64 + r) * kStrideW + piece * 4,
+           Wd + e.adig + (int64_t)p * e.Mp * e.Kp + (int64_t)(row0 + r) * e.Kp + c * kChunk + piece * 4);
+    }
+    for (int q = tid; q < kDig * kChunk * 8; q += 128) {
+      const int p = q / (kChunk * 8), k = (q / 8) % kChunk, piece = q % 8;
+      cp16(Bs + (p * kChunk + k) * kStrideW + piece * 4,
+           Wd + e.bdig + (int64_t)p * e.Kp * e.Np + (int64_t)(c * kChunk + k) * e.Np + col0 + piece * 4);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    __syncthreads();  // Rm / Sm visible (first chunk) before the scale factors
+    if (tid < 64) rsc[tid] = Id[e.aexp + (int64_t)c * e.Mp + row0 + tid] - Rm[tid];
+    else if (tid < 96) csc[tid - 64] = Id[e.bexp + (int64_t)c * e.Np + col0 + tid - 64] - Sm[tid - 64];
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();
+
+#pragma unroll 1
+    for (int L = 0; L < kLevels; ++L) {
+      float acc[2][4][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+#pragma unroll 1
+      for (int p = 0; p <= L; ++p) {
+        const unsigned* Ap = As + p * 64 * kStrideW;
+        const unsigned* Bq = Bs + (L - p) * kChunk * kStrideW;
+#pragma unroll
+        for (int ks = 0; ks < kChunk / 8; ++ks) {
+          unsigned a[2][4], b[4][2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const unsigned* r0 = Ap + (wm + 16 * i + gq) * kStrideW + ks * 8 + tq;
+            const unsigned* r1 = r0 + 8 * kStrideW;
+            a[i][0] = r0[0];
+            a[i][1] = r1[0];
+            a[i][2] = r0[4];
+            a[i][3] = r1[4];
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int nc = wn + 4 * j + (gq >> 1);
+            const unsigned w0 = Bq[(ks * 8 + tq) * kStrideW + nc];
+            const unsigned w1 = Bq[(ks * 8 + tq + 4) * kStrideW + nc];
+            if (gq & 1) {  // real column 2n+1: (bi, br)
+              b[j][0] = __byte_perm(w0, 0, 0x1032);
+              b[j][1] = __byte_perm(w1, 0, 0x1032);
+            } else {  // real column 2n: (br, -bi)
+              b[j][0] = w0 ^ 0x80000000u;
+              b[j][1] = w1 ^ 0x80000000u;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bmma(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
+        }
+      }
+      // fold the level: acc * 2^{(e_i - R_i) + (f_n - S_n) - 16 - 8L} into triple-float
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int row = wm + 16 * i + gq + (r >> 1) * 8;
+            const int nc = wn + 4 * j + tq;
+            const float x = acc[i][j][r] * pow2f(rsc[row] + csc[nc] - 16 - 8 * L);
+            float s, e1, s2, e2;
+            two_sum(h[i][j][r], x, s, e1);
+            h[i][j][r] = s;
+            two_sum(mi[i][j][r], e1, s2, e2);
+            mi[i][j][r] = s2;
+            lo[i][j][r] += e2;
+          }
+    }
+    // renormalise (h, mi, lo)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float s, e1, s2, e2;
+          two_sum(h[i][j][r], mi[i][j][r], s, e1);
+          two_sum(e1, lo[i][j][r], s2, e2);
+          h[i][j][r] = s;
+          mi[i][j][r] = s2;
+          lo[i][j][r] = e2;
+        }
+    __syncthreads();
+  }
+
+  // epilogue: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value
+  double2* C = arena + blockIdx.y * stride + g.c;
+  const double sg = g.neg ? -1.0 : 1.0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int rl = wm + 16 * i + gq + rr * 8, cl = wn + 4 * j + tq;
+        const int r = row0 + rl, cc = col0 + cl;
+        if (r >= g.M || cc >= g.N) continue;
+        if ((r >= g.mask0 && r < g.mask1) || (cc >= g.mask0 && cc < g.mask1)) continue;
+        const int ex = Rm[rl] + Sm[cl];
+        double2 v;
+        double* vp = &v.x;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const int q = 2 * rr + part;
+          float s, e1;
+          two_sum(h[i][j][q], mi[i][j][q], s, e1);
+          const double val = (double)s + (double)(e1 + lo[i][j][q]);
+          vp[part] = sg * ldexp(val, ex);
+        }
+        double2* pc = C + (int64_t)r * g.ldc + cc;
+        if (g.beta) v = cadd(v, *pc);
+        *pc = v;
+      }
+}
+
+}  // namespace
+
+size_t emu_smem_bytes() { return kEmuSmemBytes; }
+
+cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
+  // opt in to > 48 KB of dynamic shared memory (a host-side attribute of the
+  // function on the current device; cheap, so set on every launch)
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmuSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
+  const dim3 gs((unsigned)((items + 7) / 8), (unsigned)p.batch);
+  k_emu_split<<<gs, 256, 0, st>>>(p.d_gemm, p.d_emu, op.d0, op.d1, arena, p.arena_elems, p.d_emu_words, p.d_emu_ints,
+                                  p.emu_words, p.emu_ints, items);
+  const dim3 gg((unsigned)op.blocks, (unsigned)p.batch);
+  k_gemm_emu<<<gg, 128, kEmuSmemBytes, st>>>(p.d_gemm, p.d_emu, op.d0, op.d1, arena, p.arena_elems, p.d_emu_words,
+                                             p.d_emu_ints, p.emu_words, p.emu_ints);
+  return cudaGetLastError();
+}
+
+}  // namespace cl

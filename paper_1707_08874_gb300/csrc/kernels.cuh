@@ -14,6 +14,8 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
 // batched complex GEMM over the descriptors of one OP_GEMM
 cudaError_t launch_gemm(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t st);
+// FP64-accurate GEMM on the BF16 tensor cores (split pass + digit GEMM)
+cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

@@ -17,6 +17,7 @@ constexpr int kTileN = 32;
 constexpr int kLeafSites = 8;
 constexpr int kPanelFP64 = 48;
 constexpr int kPanelFP32 = 48;
+constexpr int kPanelEmu = 48;
 
 struct SNode {
   std::vector<int> sep;       // sites eliminated at this supernode (front order)
@@ -77,6 +78,16 @@ struct GatherDesc {
   int blk0;
 };
 
+// Split-digit workspace of one GEMM problem in the FP64-emulation path
+// (CL_FP64_EMU): digit planes of A ([7][Mp][Kp] words) and B ([7][Kp][Np]),
+// chunk exponents ([Kp/32][Mp] and [Kp/32][Np] ints); padded sizes.
+struct EmuDesc {
+  int64_t adig, bdig;  // word offsets in the replica's word workspace
+  int64_t aexp, bexp;  // int offsets in the replica's int workspace
+  int Mp, Np, Kp;      // Mp % 64 == 0, Np % 32 == 0, Kp % 32 == 0 (complex)
+  int it0, items;      // split-pass warp items of this problem inside its launch
+};
+
 enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT };
 
 struct Op {
@@ -106,6 +117,8 @@ struct Plan {
   std::vector<CopyDesc> copies;
   std::vector<ExtAddDesc> extadd;
   std::vector<GatherDesc> gather;
+  std::vector<EmuDesc> emu;                         // parallel to gemm (CL_FP64_EMU only)
+  int64_t emu_words = 0, emu_ints = 0;              // workspace per replica
   std::vector<Op> factor_ops, selinv_ops;
   // device memory
   void* d_arena = nullptr;       // batch * arena_elems complex (precision-dependent)
@@ -118,6 +131,9 @@ struct Plan {
   CopyDesc* d_copies = nullptr;
   ExtAddDesc* d_extadd = nullptr;
   GatherDesc* d_gather = nullptr;
+  EmuDesc* d_emu = nullptr;
+  unsigned* d_emu_words = nullptr;
+  int* d_emu_ints = nullptr;
   // Langevin-step buffers (all replicas): G blocks, drift, link inverses,
   // cooling fields, reduction partials and max slots
   double* d_Gdiag = nullptr;

@@ -51,13 +51,23 @@ def _run(plan, U, m=M, mu=MU, nf=1.0):
     return {k: v.cpu().numpy() for k, v in out.items()}, st
 
 
+PRECS = ["fp64", "fp64_emu"]
+
+
+def _prec(B, name):
+    return {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[name]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("ns,nt,seed", [(4, 4, 1707), (4, 4, 1), (6, 4, 1707), (4, 6, 3)])
-def test_fp64_parity_small(ns, nt, seed):
+def test_fp64_parity_small(ns, nt, seed, prec):
+    """FP64 fronts, and FP64 fronts whose GEMMs are exact BF16 digit products
+    (CL_FP64_EMU): both held to the FP64 bar."""
     B = _binding()
     U = inputs.random_links(ns, nt, seed=seed)
     ref = oracle.drift_eval(ns, nt, U, M, MU)
     tol, kappa = _tol(oracle.dirac_dense(ns, nt, U, M, MU))
-    plan = B.Plan.analyze(ns, nt, 1, B.CL_FP64)
+    plan = B.Plan.analyze(ns, nt, 1, _prec(B, prec))
     got, st = _run(plan, U)
     assert st == B.CL_OK
     for name, key in (("Gdiag", "Gdiag"), ("Gfwd", "Gfwd"), ("Gbwd", "Gbwd")):
@@ -85,11 +95,12 @@ def test_fp64_free_field_and_su3():
     plan.close()
 
 
-def test_fp64_batch_replicas_independent():
+@pytest.mark.parametrize("prec", PRECS)
+def test_fp64_batch_replicas_independent(prec):
     """A batch of replicas gives each replica's own result (no cross-talk)."""
     B = _binding()
     U = inputs.random_links(4, 4, seed=40, batch=3)
-    plan = B.Plan.analyze(4, 4, 3, B.CL_FP64)
+    plan = B.Plan.analyze(4, 4, 3, _prec(B, prec))
     got, st = _run(plan, U)
     assert st == B.CL_OK
     for b in range(3):
@@ -100,11 +111,12 @@ def test_fp64_batch_replicas_independent():
     plan.close()
 
 
-def test_fp64_repeatable_bitwise():
+@pytest.mark.parametrize("prec", PRECS)
+def test_fp64_repeatable_bitwise(prec):
     """Two evaluations of the same links give identical bits (no atomics)."""
     B = _binding()
     U = inputs.random_links(6, 4, seed=5)
-    plan = B.Plan.analyze(6, 4, 1, B.CL_FP64)
+    plan = B.Plan.analyze(6, 4, 1, _prec(B, prec))
     a, _ = _run(plan, U)
     b, _ = _run(plan, U)
     assert np.array_equal(a["Kf"], b["Kf"]) and np.array_equal(a["Gfwd"], b["Gfwd"])
@@ -125,17 +137,27 @@ def test_nonfinite_status():
     plan.close()
 
 
-def test_fp64_full_size_sampled():
+@pytest.fixture(scope="module")
+def full_size():
+    ns, nt = 8, 4
+    U = inputs.random_links(ns, nt, seed=1707)
+    D = oracle.dirac_dense(ns, nt, U, M, MU)
+    tol, kappa = _tol(D)
+    LU, piv, info = oracle.lu(D)
+    assert info == 0
+    return U, D, tol, LU, piv
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fp64_full_size_sampled(prec, full_size):
     """8^3 x 4 (the benchmark workload, batch 1): sampled columns of D^{-1} from
     the oracle's LU, every selected block touching them, the drift of the links
     whose both blocks are known, and D G = 1 on every site."""
     B = _binding()
     ns, nt = 8, 4
     V = ns ** 3 * nt
-    U = inputs.random_links(ns, nt, seed=1707)
-    D = oracle.dirac_dense(ns, nt, U, M, MU)
-    tol, kappa = _tol(D)
-    plan = B.Plan.analyze(ns, nt, 1, B.CL_FP64)
+    U, D, tol, LU, piv = full_size
+    plan = B.Plan.analyze(ns, nt, 1, _prec(B, prec))
     got, st = _run(plan, U)
     assert st == B.CL_OK
     Gd, Gf, Gb, K = got["Gdiag"][0], got["Gfwd"][0], got["Gbwd"][0], got["Kf"][0]
@@ -156,8 +178,6 @@ def test_fp64_full_size_sampled():
     ys = rng.choice(V, 6, replace=False)
     sites = sorted(set(int(y) for y in ys) | {int(up[y, nu]) for y in ys for nu in range(4)})
     cols = np.array([3 * s + a for s in sites for a in range(3)])
-    LU, piv, info = oracle.lu(D)
-    assert info == 0
     X = oracle.solve_unit_columns(LU, piv, cols)
     col = {s: X[:, 3 * i:3 * i + 3] for i, s in enumerate(sites)}
     scale = np.sqrt((np.abs(Gf) ** 2).sum((-1, -2))).max()
