@@ -436,30 +436,35 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision) {
   p.emu_words = p.emu_ints = 0;
   if (precision == CL_FP64_EMU) {
     p.emu.resize(p.gemm.size());
-    for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
-      for (const auto& op : *ops) {
+    for (auto* ops : {&p.factor_ops, &p.selinv_ops})
+      for (auto& op : *ops) {
         if (op.kind != OP_GEMM) continue;
         int64_t w = 0, in = 0;
-        int it = 0;
+        int it = 0, blk = 0;
         for (int d = op.d0; d < op.d1; ++d) {
-          const GemmDesc& g = p.gemm[d];
+          GemmDesc& g = p.gemm[d];
           EmuDesc& e = p.emu[d];
-          e.Mp = (g.M + 63) / 64 * 64;
+          e.Mp = (g.M + kEmuTileM - 1) / kEmuTileM * kEmuTileM;
           e.Np = (g.N + 31) / 32 * 32;
           e.Kp = (g.K + 31) / 32 * 32;
           const int64_t nch = e.Kp / 32;
           e.adig = w;
           w += (7LL * e.Mp * e.Kp + 63) / 64 * 64;
           e.bdig = w;
-          w += (7LL * e.Kp * e.Np + 63) / 64 * 64;
+          w += (7LL * 2 * e.Np * e.Kp + 63) / 64 * 64;
           e.aexp = in;
           in += nch * e.Mp;
           e.bexp = in;
           in += nch * e.Np;
           e.it0 = it;
-          e.items = (int)(e.Mp * nch + (e.Np / 32) * nch);
+          e.items = (int)(e.Mp * nch + e.Np * nch);
           it += e.items;
+          // this precision tiles the GEMMs by kEmuTileM rows
+          g.blk0 = blk;
+          g.tilesN = e.Np / 32;
+          blk += (e.Mp / kEmuTileM) * g.tilesN;
         }
+        op.blocks = blk;
         p.emu_words = std::max(p.emu_words, w);
         p.emu_ints = std::max(p.emu_ints, in);
       }

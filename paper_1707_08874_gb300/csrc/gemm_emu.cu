@@ -10,7 +10,7 @@
 // rounded below FP64 resolution for the others.  Level sums are scaled by
 // powers of two and accumulated across chunks in triple-float (three FP32
 // words, error-free two-sums), relative to the largest row / column exponent;
-// FP64 arithmetic appears only in the epilogue.  Accuracy equals an FP64 GEMM
+// FP64 arithmetic appears only in the epilogue (two additions per output).  Accuracy equals an FP64 GEMM
 // to within a small factor (numpy emulation of the same digits and roundings:
 // normwise relative error 4e-16 - 1.1e-15 against 5e-16 - 1e-15 for FP64).
 //
@@ -53,9 +53,13 @@ __device__ __forceinline__ void digits(double v, int e, unsigned short (&d)[kDig
 }
 
 // Split pass: one warp per item.  A items (row, chunk): lanes take the 32
-// complex k of the chunk.  B items (32 columns, chunk): lanes take a column
-// and loop over the chunk's k.  Padding (rows >= M, columns >= N, k >= K) is
-// written as zero digits so the GEMM needs no bounds checks.
+// complex k of the chunk; digits go to A[p][row][k] as (re, im) BF16 pairs.
+// B items (column n, chunk): lanes take the chunk's 32 k; the real embedding
+// of b = br + i bi is written directly, k-contiguous, as two rows of B'^T:
+//   row 2n   : (br, -bi)   (real column 2n of [[br, bi], [-bi, br]] per k)
+//   row 2n+1 : (bi,  br)
+// so the GEMM loads both operands with ldmatrix and no per-element work.
+// Padding (rows >= M, columns >= N, k >= K) gets zero digits.
 __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
                                                    int d0, int d1, const double2* __restrict__ arena,
                                                    int64_t stride, unsigned* __restrict__ words,
@@ -78,46 +82,37 @@ __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ 
   const int nch = e.Kp / kChunk;
   int it = item - e.it0;
   const int nA = e.Mp * nch;
-  if (it < nA) {
-    const int row = it / nch, c = it % nch;
-    const int k = c * kChunk + lane;
-    double2 v = make_double2(0, 0);
-    if (row < g.M && k < g.K) v = base[g.a + (int64_t)row * g.lda + k];
-    int ex = max(exp_of(v.x), exp_of(v.y));
+  const bool isA = it < nA;
+  if (!isA) it -= nA;
+  const int line = it / nch, c = it % nch;  // row (A) or complex column (B)
+  const int k = c * kChunk + lane;
+  double2 v = make_double2(0, 0);
+  if (isA) {
+    if (line < g.M && k < g.K) v = base[g.a + (int64_t)line * g.lda + k];
+  } else {
+    if (line < g.N && k < g.K) v = base[g.b + (int64_t)k * g.ldb + line];
+  }
+  int ex = max(exp_of(v.x), exp_of(v.y));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
-    const int ee = ex + 1;
-    if (lane == 0) I[e.aexp + (int64_t)c * e.Mp + row] = ee;
-    unsigned short dr[kDig], di[kDig];
-    digits(v.x, ee, dr);
-    digits(v.y, ee, di);
-    unsigned* dst = W + e.adig + (int64_t)row * e.Kp + k;
+  for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+  const int ee = ex + 1;
+  unsigned short dr[kDig], di[kDig];
+  digits(v.x, ee, dr);
+  digits(v.y, ee, di);
+  if (isA) {
+    if (lane == 0) I[e.aexp + (int64_t)c * e.Mp + line] = ee;
+    unsigned* dst = W + e.adig + (int64_t)line * e.Kp + k;
 #pragma unroll
     for (int p = 0; p < kDig; ++p) dst[(int64_t)p * e.Mp * e.Kp] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
   } else {
-    it -= nA;
-    const int grp = it / nch, c = it % nch;
-    const int n = grp * 32 + lane;
-    int ex = -2000;
-    for (int kk = 0; kk < kChunk; ++kk) {
-      const int k = c * kChunk + kk;
-      if (n < g.N && k < g.K) {
-        const double2 v = base[g.b + (int64_t)k * g.ldb + n];
-        ex = max(ex, max(exp_of(v.x), exp_of(v.y)));
-      }
-    }
-    const int ee = ex + 1;
-    I[e.bexp + (int64_t)c * e.Np + n] = ee;
-    for (int kk = 0; kk < kChunk; ++kk) {
-      const int k = c * kChunk + kk;
-      double2 v = make_double2(0, 0);
-      if (n < g.N && k < g.K) v = base[g.b + (int64_t)k * g.ldb + n];
-      unsigned short dr[kDig], di[kDig];
-      digits(v.x, ee, dr);
-      digits(v.y, ee, di);
-      unsigned* dst = W + e.bdig + (int64_t)k * e.Np + n;
+    if (lane == 0) I[e.bexp + (int64_t)c * e.Np + line] = ee;
+    unsigned* dst0 = W + e.bdig + (int64_t)(2 * line) * e.Kp + k;
+    unsigned* dst1 = dst0 + e.Kp;
+    const int64_t plane = (int64_t)2 * e.Np * e.Kp;
 #pragma unroll
-      for (int p = 0; p < kDig; ++p) dst[(int64_t)p * e.Kp * e.Np] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
+    for (int p = 0; p < kDig; ++p) {
+      dst0[p * plane] = (unsigned)dr[p] | ((unsigned)(di[p] ^ (di[p] ? 0x8000u : 0u)) << 16);
+      dst1[p * plane] = (unsigned)di[p] | ((unsigned)dr[p] << 16);
     }
   }
 }
@@ -139,50 +134,71 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) 
 
 __device__ __forceinline__ float pow2f(int k) { return k < -126 ? 0.f : __int_as_float((k + 127) << 23); }
 
+// f * 2^ex as a double, built from the float's bits with integer operations
+// (exact; the FP64 pipe is GB300's scarcest unit).  Zero / subnormal floats
+// and results below the double range give 0; sign flipped when neg.
+__device__ __forceinline__ double f2d_scaled(float f, int ex, bool neg) {
+  const unsigned u = __float_as_uint(f);
+  const int e = (int)((u >> 23) & 0xFFu);
+  if (e == 0) return 0.0;
+  const int ed = e - 127 + 1023 + ex;
+  if (ed <= 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)((u >> 31) ^ (neg ? 1u : 0u)) << 63;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)ed << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
 }
 
-constexpr int kSmemA = kDig * 64 * kStrideW;  // words
-constexpr int kSmemB = kDig * kChunk * kStrideW;
-constexpr size_t kEmuSmemBytes = (size_t)(kSmemA + kSmemB) * 4 + (64 + 32) * 2 * sizeof(int);
+__device__ __forceinline__ void ldsm4(unsigned (&r)[4], const unsigned* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
 
-// 128 threads, 2 x 2 warps; each warp owns 32 rows x 32 real columns
-// (2 x 4 MMA tiles of 16 x 8); CTA tile 64 complex rows x 32 complex columns.
-__global__ void __launch_bounds__(128, 2) k_gemm_emu(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
+constexpr int kEmuTM = 128;                        // rows per CTA
+constexpr int kSmemA = kDig * kEmuTM * kStrideW;   // words
+constexpr int kSmemB = kDig * 64 * kStrideW;       // 64 real columns (32 complex)
+constexpr size_t kEmuSmemBytes = (size_t)(kSmemA + kSmemB) * 4 + (kEmuTM + 32) * 2 * sizeof(int);
+
+// 256 threads = 4 x 2 warps; each warp owns 32 rows x 32 real columns
+// (2 x 4 MMA tiles of 16 x 8); CTA tile 128 rows x 32 complex columns.
+__global__ void __launch_bounds__(256, 1) k_gemm_emu(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
                                                      int d0, int d1, double2* __restrict__ arena, int64_t stride,
                                                      const unsigned* __restrict__ words, const int* __restrict__ ints,
                                                      int64_t wstride, int64_t istride) {
   extern __shared__ __align__(16) unsigned smem[];
   unsigned* As = smem;
   unsigned* Bs = smem + kSmemA;
-  int* rsc = reinterpret_cast<int*>(Bs + kSmemB);  // [64] row exponent of the chunk minus the row maximum
-  int* csc = rsc + 64;                             // [32] same for the columns
-  int* Rm = csc + 32;                              // [64] row maxima
-  int* Sm = Rm + 64;                               // [32] column maxima
+  int* rsc = reinterpret_cast<int*>(Bs + kSmemB);  // [128] chunk exponent minus the row maximum
+  int* csc = rsc + kEmuTM;                         // [32]  same for the complex columns
+  int* Rm = csc + 32;                              // [128] row maxima
+  int* Sm = Rm + kEmuTM;                           // [32]  column maxima
 
   const int di = find_desc(gd, d0, d1, blockIdx.x);
   const GemmDesc g = gd[di];
   const EmuDesc e = ed[di];
   const int t = blockIdx.x - g.blk0;
-  const int row0 = (t / g.tilesN) * kTileM, col0 = (t % g.tilesN) * kTileN;
+  const int row0 = (t / g.tilesN) * kEmuTM, col0 = (t % g.tilesN) * kTileN;
   const unsigned* Wd = words + blockIdx.y * wstride;
   const int* Id = ints + blockIdx.y * istride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gq = lane >> 2, tq = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 16;  // complex offsets in the tile
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 16;  // row / complex column offsets of the warp
   const int nch = e.Kp / kChunk;
 
-  // reference exponents: maxima over all chunks
-  if (tid < 64) {
+  if (tid < kEmuTM) {
     int m = -4000;
     for (int c = 0; c < nch; ++c) m = max(m, Id[e.aexp + (int64_t)c * e.Mp + row0 + tid]);
     Rm[tid] = m;
-  } else if (tid < 96) {
+  } else if (tid < kEmuTM + 32) {
     int m = -4000;
-    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid - 64]);
-    Sm[tid - 64] = m;
+    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid - kEmuTM]);
+    Sm[tid - kEmuTM] = m;
   }
 
   float h[2][4][4], mi[2][4][4], lo[2][4][4];
@@ -193,24 +209,37 @@ __global__ void __launch_bounds__(128, 2) k_gemm_emu(const GemmDesc* __restrict_
 #pragma unroll
       for (int r = 0; r < 4; ++r) h[i][j][r] = mi[i][j][r] = lo[i][j][r] = 0.f;
 
+  // ldmatrix lane addressing: A rows (lane & 15), k half (lane >> 4);
+  // B' rows n_r = 8j + (lane & 7) + 8 ((lane >> 4) & 1), k half ((lane >> 3) & 1)
+  const int a_row = lane & 15, a_kw = (lane >> 4) * 4;
+  const int b_row = (lane & 7) + ((lane >> 4) & 1) * 8, b_kw = ((lane >> 3) & 1) * 4;
+
   for (int c = 0; c < nch; ++c) {
-    // stage the chunk's digits: A [7][64 rows][32 words], B [7][32 k][32 words]
-    for (int q = tid; q < kDig * 64 * 8; q += 128) {
-      const int p = q / (64 * 8), r = (q / 8) % 64, piece = q % 8;
-      cp16(As + (p * 64 + r) * kStrideW + piece * 4,
+    for (int q = tid; q < kDig * kEmuTM * 8; q += 256) {
+      const int p = q / (kEmuTM * 8), r = (q / 8) % kEmuTM, piece = q % 8;
+      cp16(As + (p * kEmuTM + r) * kStrideW + piece * 4,
            Wd + e.adig + (int64_t)p * e.Mp * e.Kp + (int64_t)(row0 + r) * e.Kp + c * kChunk + piece * 4);
     }
-    for (int q = tid; q < kDig * kChunk * 8; q += 128) {
-      const int p = q / (kChunk * 8), k = (q / 8) % kChunk, piece = q % 8;
-      cp16(Bs + (p * kChunk + k) * kStrideW + piece * 4,
-           Wd + e.bdig + (int64_t)p * e.Kp * e.Np + (int64_t)(c * kChunk + k) * e.Np + col0 + piece * 4);
+    for (int q = tid; q < kDig * 64 * 8; q += 256) {
+      const int p = q / (64 * 8), r = (q / 8) % 64, piece = q % 8;
+      cp16(Bs + (p * 64 + r) * kStrideW + piece * 4,
+           Wd + e.bdig + (int64_t)p * 2 * e.Np * e.Kp + (int64_t)(2 * col0 + r) * e.Kp + c * kChunk + piece * 4);
     }
     asm volatile("cp.async.commit_group;\n" ::);
-    __syncthreads();  // Rm / Sm visible (first chunk) before the scale factors
-    if (tid < 64) rsc[tid] = Id[e.aexp + (int64_t)c * e.Mp + row0 + tid] - Rm[tid];
-    else if (tid < 96) csc[tid - 64] = Id[e.bexp + (int64_t)c * e.Np + col0 + tid - 64] - Sm[tid - 64];
+    __syncthreads();  // row / column maxima visible before the scale factors
+    if (tid < kEmuTM) rsc[tid] = Id[e.aexp + (int64_t)c * e.Mp + row0 + tid] - Rm[tid];
+    else if (tid < kEmuTM + 32) csc[tid - kEmuTM] = Id[e.bexp + (int64_t)c * e.Np + col0 + tid - kEmuTM] - Sm[tid - kEmuTM];
     asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
+
+    float scl[2][4][2];  // 2^{(e_i - R_i) + (f_n - S_n) - 16} per owned (row pair, column)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+          scl[i][j][rr] = pow2f(rsc[wm + 16 * i + gq + 8 * rr] + csc[wn + 4 * j + tq] - 16);
 
 #pragma unroll 1
     for (int L = 0; L < kLevels; ++L) {
@@ -223,58 +252,46 @@ __global__ void __launch_bounds__(128, 2) k_gemm_emu(const GemmDesc* __restrict_
           for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
 #pragma unroll 1
       for (int p = 0; p <= L; ++p) {
-        const unsigned* Ap = As + p * 64 * kStrideW;
-        const unsigned* Bq = Bs + (L - p) * kChunk * kStrideW;
+        const unsigned* Ap = As + (p * kEmuTM + wm + a_row) * kStrideW + a_kw;
+        const unsigned* Bq = Bs + ((L - p) * 64 + 2 * wn + b_row) * kStrideW + b_kw;
 #pragma unroll
         for (int ks = 0; ks < kChunk / 8; ++ks) {
           unsigned a[2][4], b[4][2];
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const unsigned* r0 = Ap + (wm + 16 * i + gq) * kStrideW + ks * 8 + tq;
-            const unsigned* r1 = r0 + 8 * kStrideW;
-            a[i][0] = r0[0];
-            a[i][1] = r1[0];
-            a[i][2] = r0[4];
-            a[i][3] = r1[4];
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int nc = wn + 4 * j + (gq >> 1);
-            const unsigned w0 = Bq[(ks * 8 + tq) * kStrideW + nc];
-            const unsigned w1 = Bq[(ks * 8 + tq + 4) * kStrideW + nc];
-            if (gq & 1) {  // real column 2n+1: (bi, br)
-              b[j][0] = __byte_perm(w0, 0, 0x1032);
-              b[j][1] = __byte_perm(w1, 0, 0x1032);
-            } else {  // real column 2n: (br, -bi)
-              b[j][0] = w0 ^ 0x80000000u;
-              b[j][1] = w1 ^ 0x80000000u;
-            }
-          }
+          ldsm4(a[0], Ap + ks * 8);
+          ldsm4(a[1], Ap + 16 * kStrideW + ks * 8);
+          unsigned t4[4];
+          ldsm4(t4, Bq + ks * 8);
+          b[0][0] = t4[0]; b[0][1] = t4[1]; b[1][0] = t4[2]; b[1][1] = t4[3];
+          ldsm4(t4, Bq + 16 * kStrideW + ks * 8);
+          b[2][0] = t4[0]; b[2][1] = t4[1]; b[3][0] = t4[2]; b[3][1] = t4[3];
 #pragma unroll
           for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) bmma(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
         }
       }
-      // fold the level: acc * 2^{(e_i - R_i) + (f_n - S_n) - 16 - 8L} into triple-float
+      // fold: levels 0, 1 into (h, mi, lo); levels >= 2 are below 2^-32 of the
+      // leading level and go straight into (mi, lo)
+      const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int row = wm + 16 * i + gq + (r >> 1) * 8;
-            const int nc = wn + 4 * j + tq;
-            const float x = acc[i][j][r] * pow2f(rsc[row] + csc[nc] - 16 - 8 * L);
+            const float x = acc[i][j][r] * (scl[i][j][r >> 1] * cL);
             float s, e1, s2, e2;
-            two_sum(h[i][j][r], x, s, e1);
-            h[i][j][r] = s;
-            two_sum(mi[i][j][r], e1, s2, e2);
+            if (L < 2) {
+              two_sum(h[i][j][r], x, s, e1);
+              h[i][j][r] = s;
+              two_sum(mi[i][j][r], e1, s2, e2);
+            } else {
+              two_sum(mi[i][j][r], x, s2, e2);
+            }
             mi[i][j][r] = s2;
             lo[i][j][r] += e2;
           }
     }
-    // renormalise (h, mi, lo)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -291,9 +308,11 @@ __global__ void __launch_bounds__(128, 2) k_gemm_emu(const GemmDesc* __restrict_
     __syncthreads();
   }
 
-  // epilogue: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value
+  // epilogue: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value.
+  // Two exact float -> double conversions by bit manipulation, then at most
+  // two FP64 additions per real output.
   double2* C = arena + blockIdx.y * stride + g.c;
-  const double sg = g.neg ? -1.0 : 1.0;
+  const bool neg = g.neg != 0;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -305,16 +324,15 @@ __global__ void __launch_bounds__(128, 2) k_gemm_emu(const GemmDesc* __restrict_
         if (r >= g.M || cc >= g.N) continue;
         if ((r >= g.mask0 && r < g.mask1) || (cc >= g.mask0 && cc < g.mask1)) continue;
         const int ex = Rm[rl] + Sm[cl];
-        double2 v;
-        double* vp = &v.x;
+        double vv[2];
 #pragma unroll
         for (int part = 0; part < 2; ++part) {
           const int q = 2 * rr + part;
           float s, e1;
           two_sum(h[i][j][q], mi[i][j][q], s, e1);
-          const double val = (double)s + (double)(e1 + lo[i][j][q]);
-          vp[part] = sg * ldexp(val, ex);
+          vv[part] = f2d_scaled(s, ex, neg) + f2d_scaled(e1 + lo[i][j][q], ex, neg);
         }
+        double2 v = make_double2(vv[0], vv[1]);
         double2* pc = C + (int64_t)r * g.ldc + cc;
         if (g.beta) v = cadd(v, *pc);
         *pc = v;
@@ -335,7 +353,7 @@ cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStr
   k_emu_split<<<gs, 256, 0, st>>>(p.d_gemm, p.d_emu, op.d0, op.d1, arena, p.arena_elems, p.d_emu_words, p.d_emu_ints,
                                   p.emu_words, p.emu_ints, items);
   const dim3 gg((unsigned)op.blocks, (unsigned)p.batch);
-  k_gemm_emu<<<gg, 128, kEmuSmemBytes, st>>>(p.d_gemm, p.d_emu, op.d0, op.d1, arena, p.arena_elems, p.d_emu_words,
+  k_gemm_emu<<<gg, 256, kEmuSmemBytes, st>>>(p.d_gemm, p.d_emu, op.d0, op.d1, arena, p.arena_elems, p.d_emu_words,
                                              p.d_emu_ints, p.emu_words, p.emu_ints);
   return cudaGetLastError();
 }

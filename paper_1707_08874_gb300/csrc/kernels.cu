@@ -94,107 +94,145 @@ __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, cons
 // ---------------------------------------------------------------------------
 // In-place inverse of one diagonal panel block (bp <= kMaxPanel) by
 // Gauss-Jordan elimination with partial (row) pivoting inside the panel; the
-// row interchanges are undone on the columns at the end.  A pivot below
-// 1e-13 * max|block| records CL_ERR_SINGULAR (supernode, column).
+// row interchanges are undone on the columns at the end.  Pivots are chosen by
+// max(|re|, |im|), compared through the ordered bit patterns of the absolute
+// values (integer work only).  A pivot below 1e-13 * max|block| records
+// CL_ERR_SINGULAR (supernode, column).  Threads form a 16 x 16 grid; thread
+// (ty, tx) owns rows ty + 16a and columns tx + 16b of the panel.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPanel = 48;
+
+__device__ __forceinline__ long long mag_key(double2 v) {
+  const long long a = __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFll;
+  const long long b = __double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFll;
+  return a > b ? a : b;
+}
+__device__ __forceinline__ long long mag_key(float2 v) {
+  const int a = __float_as_int(v.x) & 0x7FFFFFFF, b = __float_as_int(v.y) & 0x7FFFFFFF;
+  return a > b ? a : b;
+}
+__device__ __forceinline__ double key_value(long long k, double) { return __longlong_as_double(k); }
+__device__ __forceinline__ double key_value(long long k, float) { return (double)__int_as_float((int)k); }
+__device__ __forceinline__ long long value_key(double v, double) { return __double_as_longlong(v); }
+__device__ __forceinline__ long long value_key(double v, float) { return __float_as_int((float)v); }
 
 template <typename T, typename R>
 __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
                                                        int64_t stride, int* __restrict__ status) {
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
-  const int bp = d.bp, tid = threadIdx.x;
+  const int bp = d.bp, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   __shared__ T S[kMaxPanel][kMaxPanel + 1];
   __shared__ T fcol[kMaxPanel];
   __shared__ int piv[kMaxPanel];
-  __shared__ R red[256];
+  __shared__ long long wmax[8];
+  __shared__ T sinv;
   __shared__ int sp;
-  R amax = 0;
-  for (int e = tid; e < bp * bp; e += blockDim.x) {
-    const int i = e / bp, j = e % bp;
-    T v = A[(int64_t)i * d.ld + j];
-    S[i][j] = v;
-    amax = fmax(amax, (R)hypot(v.x, v.y));
-  }
-  red[tid] = amax;
+  __shared__ long long sthr;
+  long long km = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < bp && j < bp) {
+        const T v = A[(int64_t)i * d.ld + j];
+        S[i][j] = v;
+        km = max(km, mag_key(v));
+      }
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = km;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
-    __syncthreads();
+  if (tid == 0) {
+    long long m = wmax[0];
+    for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
+    const double rel = sizeof(R) == 8 ? 1e-13 : 1e-6;  // singular-pivot threshold by precision
+    sthr = value_key(rel * key_value(m, R(0)), R(0));
   }
-  const R scale = red[0];
   __syncthreads();
+  const long long thr = sthr;
   for (int c = 0; c < bp; ++c) {
     if (tid < 32) {  // pivot search over rows c..bp-1, ties keep the lowest row
-      R best = -1;
+      long long best = -1;
       int bi = c;
       for (int i = c + tid; i < bp; i += 32) {
-        R v = hypot(S[i][c].x, S[i][c].y);
-        if (v > best) { best = v; bi = i; }
+        const long long k = mag_key(S[i][c]);
+        if (k > best) { best = k; bi = i; }
       }
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        R ob = __shfl_down_sync(0xffffffffu, best, o);
-        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        const long long ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
         sp = bi;
         piv[c] = bi;
-        if (!(best >= (R)1e-13 * scale)) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
+        if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
       }
     }
     __syncthreads();
     const int p = sp;
-    if (p != c)
-      for (int j = tid; j < bp; j += blockDim.x) {
-        T t = S[c][j];
-        S[c][j] = S[p][j];
-        S[p][j] = t;
-      }
+    if (p != c && tid < bp) {
+      const T t = S[c][tid];
+      S[c][tid] = S[p][tid];
+      S[p][tid] = t;
+    }
     __syncthreads();
-    const T pv = S[c][c];
-    const R n2 = pv.x * pv.x + pv.y * pv.y;
-    T inv;
-    inv.x = pv.x / n2;
-    inv.y = -pv.y / n2;
-    for (int i = tid; i < bp; i += blockDim.x) fcol[i] = S[i][c];
+    if (tid < bp) fcol[tid] = S[tid][c];
+    if (tid == 0) {
+      const T pv = S[c][c];
+      const R n2 = pv.x * pv.x + pv.y * pv.y;
+      T inv;
+      inv.x = pv.x / n2;
+      inv.y = -pv.y / n2;
+      sinv = inv;
+    }
     __syncthreads();
-    for (int j = tid; j < bp; j += blockDim.x) S[c][j] = (j == c) ? inv : cmul(S[c][j], inv);
+    const T inv = sinv;
+    if (tid < bp) S[c][tid] = (tid == c) ? inv : cmul(S[c][tid], inv);
     __syncthreads();
-    for (int e = tid; e < bp * bp; e += blockDim.x) {
-      const int i = e / bp, j = e % bp;
-      if (i == c) continue;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int i = ty + 16 * a;
+      if (i >= bp || i == c) continue;
       const T f = fcol[i];
-      if (j == c) {
-        T v = cmul(f, inv);
-        v.x = -v.x;
-        v.y = -v.y;
-        S[i][c] = v;
-      } else {
-        T v = S[i][j];
-        T w = S[c][j];
-        v.x -= f.x * w.x - f.y * w.y;
-        v.y -= f.x * w.y + f.y * w.x;
-        S[i][j] = v;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int j = tx + 16 * b;
+        if (j >= bp) continue;
+        if (j == c) {
+          const T v = cmul(f, inv);
+          S[i][c] = T{-v.x, -v.y};
+        } else {
+          T v = S[i][j];
+          const T w = S[c][j];
+          v.x -= f.x * w.x - f.y * w.y;
+          v.y -= f.x * w.y + f.y * w.x;
+          S[i][j] = v;
+        }
       }
     }
     __syncthreads();
   }
   for (int c = bp - 1; c >= 0; --c) {
     const int p = piv[c];
-    if (p != c)
-      for (int i = tid; i < bp; i += blockDim.x) {
-        T t = S[i][c];
-        S[i][c] = S[i][p];
-        S[i][p] = t;
-      }
+    if (p != c && tid < bp) {
+      const T t = S[tid][c];
+      S[tid][c] = S[tid][p];
+      S[tid][p] = t;
+    }
     __syncthreads();
   }
-  for (int e = tid; e < bp * bp; e += blockDim.x) {
-    const int i = e / bp, j = e % bp;
-    A[(int64_t)i * d.ld + j] = S[i][j];
-  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < bp && j < bp) A[(int64_t)i * d.ld + j] = S[i][j];
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -13,11 +13,12 @@ namespace cl {
 // GEMM tile in complex elements (rows x cols); shared by host schedule and kernels.
 constexpr int kTileM = 64;
 constexpr int kTileN = 32;
+constexpr int kEmuTileM = 128;
 // Sites per leaf of the nested dissection and pivoting panel (unknowns) by precision.
 constexpr int kLeafSites = 8;
 constexpr int kPanelFP64 = 48;
 constexpr int kPanelFP32 = 48;
-constexpr int kPanelEmu = 48;
+constexpr int kPanelEmu = 24;
 
 struct SNode {
   std::vector<int> sep;       // sites eliminated at this supernode (front order)
@@ -79,12 +80,14 @@ struct GatherDesc {
 };
 
 // Split-digit workspace of one GEMM problem in the FP64-emulation path
-// (CL_FP64_EMU): digit planes of A ([7][Mp][Kp] words) and B ([7][Kp][Np]),
-// chunk exponents ([Kp/32][Mp] and [Kp/32][Np] ints); padded sizes.
+// (CL_FP64_EMU): digit planes of A ([7][Mp][Kp] words) and of the real
+// embedding of B, transposed ([7][2 Np][Kp] words); chunk exponents
+// ([Kp/32][Mp] and [Kp/32][Np] ints); padded sizes.  CTA tiles are
+// kEmuTileM rows x kTileN complex columns.
 struct EmuDesc {
   int64_t adig, bdig;  // word offsets in the replica's word workspace
   int64_t aexp, bexp;  // int offsets in the replica's int workspace
-  int Mp, Np, Kp;      // Mp % 64 == 0, Np % 32 == 0, Kp % 32 == 0 (complex)
+  int Mp, Np, Kp;      // Mp % 128 == 0, Np % 32 == 0, Kp % 32 == 0 (complex)
   int it0, items;      // split-pass warp items of this problem inside its launch
 };
 
