@@ -6,8 +6,14 @@ extraction) and cl_fermion_drift, links already resident in HBM.  The e2e
 figure repeats the step through the same C ABI with the links copied from
 pinned host memory and the drift copied back every step.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64_emu|fp64|mixed]
                     [--batch B] [--impl ours|reference]
+
+Precisions: fp64 = FP64 fronts on the FP64 MMA pipe; fp64_emu (default) = FP64
+fronts whose GEMMs run as exact 7-digit BF16 products on the tensor cores
+(held to the same FP64 parity bar in the tests); mixed = FP32 fronts.  The
+JSON line also carries a quick comparison of the three on the same links
+("precisions": rate and drift error against the native FP64 result).
 
 Multi-GPU: replicas only (independent lattices per rank, no data-path
 collective); value = evaluations of all ranks / max-over-ranks time.
@@ -39,7 +45,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["fp64", "fp64_emu", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp64_emu", "mixed"], default="fp64_emu")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / emulated / mixed comparison")
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -166,6 +173,34 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def compare_precisions(B, torch, links, bsz, steps=3):
+    """Quick timing of the three front precisions on the same links, and the
+    drift error of each against the native FP64 GPU result (replica 0)."""
+    out, ref = {}, None
+    names = [("fp64", B.CL_FP64), ("fp64_emu", B.CL_FP64_EMU), ("mixed", B.CL_MIXED_FP32)]
+    for name, prec in names:
+        plan = B.Plan.analyze(NS, NT, bsz, prec)
+        o = plan.alloc_outputs()
+        for _ in range(2):
+            plan.drift_eval(links, M, MU, 1.0, None, o["Gfwd"], o["Gbwd"], o["Kf"])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.drift_eval(links, M, MU, 1.0, None, o["Gfwd"], o["Gbwd"], o["Kf"])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        K = o["Kf"][0].cpu().numpy()
+        if ref is None:
+            ref = K
+        err = float(np.abs(K - ref).max() / np.abs(ref).max())
+        out[name] = {"evals_per_s": bsz / (ms / 1e3), "ms_per_step": ms, "drift_rel_err_vs_fp64": err}
+        plan.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1707_08874_gb300 import binding as B
@@ -282,6 +317,8 @@ def run_ours(args, rank, world, local):
         "kernel_ms_per_step": {k: v["total_ms"] / args.steps for k, v in prof.items()},
         "clocks": ck,
     }
+    if not args.no_compare:
+        line["precisions"] = compare_precisions(B, torch, links, bsz)
     if not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_emu(const GemmDesc* __restrict_
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-#pragma unroll 1
+#pragma unroll 2
       for (int p = 0; p <= L; ++p) {
         const unsigned* Ap = As + (p * kEmuTM + wm + a_row) * kStrideW + a_kw;
         const unsigned* Bq = Bs + ((L - p) * 64 + 2 * wn + b_row) * kStrideW + b_kw;

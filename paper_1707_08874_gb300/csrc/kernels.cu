@@ -122,12 +122,11 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
   const int bp = d.bp, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  __shared__ T S[kMaxPanel][kMaxPanel + 1];
-  __shared__ T fcol[kMaxPanel];
-  __shared__ int piv[kMaxPanel];
+  __shared__ T S[kMaxPanel][kMaxPanel + 1];  // physical rows; logical row i lives in S[rmap[i]]
+  __shared__ T fcol[kMaxPanel], prow[kMaxPanel];
+  __shared__ int rmap[kMaxPanel], piv[kMaxPanel];
   __shared__ long long wmax[8];
   __shared__ T sinv;
-  __shared__ int sp;
   __shared__ long long sthr;
   long long km = 0;
 #pragma unroll
@@ -141,6 +140,7 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
         km = max(km, mag_key(v));
       }
     }
+  if (tid < bp) rmap[tid] = tid;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
   if ((tid & 31) == 0) wmax[tid >> 5] = km;
@@ -154,11 +154,13 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   __syncthreads();
   const long long thr = sthr;
   for (int c = 0; c < bp; ++c) {
-    if (tid < 32) {  // pivot search over rows c..bp-1, ties keep the lowest row
+    // (1) warp 0: pivot among logical rows c..bp-1 (ties keep the lowest),
+    //     exchange it into logical position c, reciprocal of the pivot
+    if (tid < 32) {
       long long best = -1;
       int bi = c;
       for (int i = c + tid; i < bp; i += 32) {
-        const long long k = mag_key(S[i][c]);
+        const long long k = mag_key(S[rmap[i]][c]);
         if (k > best) { best = k; bi = i; }
       }
 #pragma unroll
@@ -168,36 +170,41 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
-        sp = bi;
         piv[c] = bi;
+        const int pc = rmap[bi];
+        rmap[bi] = rmap[c];
+        rmap[c] = pc;
         if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
+        const T pv = S[pc][c];
+        const R n2 = pv.x * pv.x + pv.y * pv.y;
+        T inv;
+        inv.x = pv.x / n2;
+        inv.y = -pv.y / n2;
+        sinv = inv;
       }
     }
     __syncthreads();
-    const int p = sp;
-    if (p != c && tid < bp) {
-      const T t = S[c][tid];
-      S[c][tid] = S[p][tid];
-      S[p][tid] = t;
-    }
-    __syncthreads();
-    if (tid < bp) fcol[tid] = S[tid][c];
-    if (tid == 0) {
-      const T pv = S[c][c];
-      const R n2 = pv.x * pv.x + pv.y * pv.y;
-      T inv;
-      inv.x = pv.x / n2;
-      inv.y = -pv.y / n2;
-      sinv = inv;
-    }
-    __syncthreads();
+    // (2) multipliers (column c of every logical row) and the scaled pivot row
     const T inv = sinv;
-    if (tid < bp) S[c][tid] = (tid == c) ? inv : cmul(S[c][tid], inv);
+    if (tid < bp) {
+      fcol[tid] = S[rmap[tid]][c];
+      prow[tid] = (tid == c) ? inv : cmul(S[rmap[c]][tid], inv);
+    }
     __syncthreads();
+    // (3) eliminate column c from every other logical row; row c <- pivot row
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int i = ty + 16 * a;
-      if (i >= bp || i == c) continue;
+      if (i >= bp) continue;
+      T* Si = S[rmap[i]];
+      if (i == c) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const int j = tx + 16 * b;
+          if (j < bp) Si[j] = prow[j];
+        }
+        continue;
+      }
       const T f = fcol[i];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
@@ -205,24 +212,27 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
         if (j >= bp) continue;
         if (j == c) {
           const T v = cmul(f, inv);
-          S[i][c] = T{-v.x, -v.y};
+          Si[c] = T{-v.x, -v.y};
         } else {
-          T v = S[i][j];
-          const T w = S[c][j];
+          T v = Si[j];
+          const T w = prow[j];
           v.x -= f.x * w.x - f.y * w.y;
           v.y -= f.x * w.y + f.y * w.x;
-          S[i][j] = v;
+          Si[j] = v;
         }
       }
     }
     __syncthreads();
   }
+  // logical rows are in rmap order; undo the column interchanges in reverse
+  // order (they mirror the row interchanges of the pivoting) and store
   for (int c = bp - 1; c >= 0; --c) {
     const int p = piv[c];
     if (p != c && tid < bp) {
-      const T t = S[tid][c];
-      S[tid][c] = S[tid][p];
-      S[tid][p] = t;
+      T* Sr = S[rmap[tid]];
+      const T t = Sr[c];
+      Sr[c] = Sr[p];
+      Sr[p] = t;
     }
     __syncthreads();
   }
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < bp && j < bp) A[(int64_t)i * d.ld + j] = S[i][j];
+      if (i < bp && j < bp) A[(int64_t)i * d.ld + j] = S[rmap[i]][j];
     }
 }
 
