@@ -213,7 +213,9 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
     prec = {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[args.precision]
     bsz = args.batch
-    plan = B.Plan.analyze(NS, NT, bsz, prec)
+    from paper_1707_08874_gb300 import autotune
+    panel = autotune.tune_panel(NS, NT, bsz, prec, use_cache=False)
+    plan = B.Plan.analyze_ex(NS, NT, bsz, prec, panel)
     info = plan.info
     U = inputs.random_links(NS, NT, seed=inputs.BASE_SEED + rank * bsz, batch=bsz)
     links_host = torch.from_numpy(U).pin_memory()
@@ -297,7 +299,7 @@ def run_ours(args, rank, world, local):
         "dtype": {B.CL_FP64: "f64", B.CL_FP64_EMU: "f64 (exact bf16 digit products, fp32 accumulate)",
                   B.CL_MIXED_FP32: "f32"}[prec], "data": "synthetic",
         "config": {"workload": "8^3x4 lattice, m=0.05, mu=0.25, links exp(i c.lambda), c ~ N(0,0.5)+iN(0,0.1)",
-                   "lattice": "8^3x4", "batch": bsz, "precision": args.precision,
+                   "lattice": "8^3x4", "batch": bsz, "precision": args.precision, "panel": panel,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set > L2 (front pool %.0f MB per replica)" % (info["front_bytes"] / bsz / 1e6)},
         "e2e": {"value": world * bsz / (e2e_ms / 1e3), "unit": "evals/s", "h2d_bytes_per_step": h2d,

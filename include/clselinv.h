@@ -56,6 +56,7 @@ extern "C" {
                            BF16 products on the tensor cores (FP64 accuracy)    */
 
 typedef struct cl_plan cl_plan;
+typedef struct cl_group cl_group;
 
 /* Summary of a plan (host values, no device access). */
 typedef struct cl_plan_info {
@@ -127,6 +128,15 @@ typedef struct cl_langevin_params {
  * extents, CL_ERR_OOM / CL_ERR_CUDA on allocation or copy failure.
  */
 int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan);
+
+/*
+ * cl_analyze_ex -- cl_analyze with an explicit pivoting-panel width
+ * (unknowns, a multiple of 3 in 3..48; 0 = the precision's default: 48 for
+ * CL_FP64 / CL_MIXED_FP32, 24 for CL_FP64_EMU).  Narrower panels shorten the
+ * serial chain of FP64 panel inverses, wider ones make fewer, larger GEMMs;
+ * the autotuner in the Python package picks it per shape by timing.
+ */
+int cl_analyze_ex(int Ns, int Nt, int batch, int precision, int panel, cl_plan** plan);
 
 /*
  * cl_analyze_symbolic -- the host half of cl_analyze only (no device memory,
@@ -302,6 +312,31 @@ int cl_profile_read(cl_plan* plan, cl_profile_entry* out, int cap, int* n);
  * *gflops receives GFLOP/s.  Allocates and frees a small device buffer.
  */
 int cl_measure_peak(int unit, double* gflops);
+
+/*
+ * Groups: several plans (lattice shapes of uneven size, each with its own
+ * batch of replicas) evaluated side by side -- the "ragged" batch of the
+ * method's production use -- and the whole fixed schedule captured once into
+ * a CUDA graph.
+ *
+ * cl_group_create -- group of nplans existing plans (not owned: destroy the
+ *   group before its plans).  Creates one non-blocking stream per plan.
+ * cl_group_drift_eval -- for every plan i: cl_drift_eval(plans[i], links[i],
+ *   m, mu, nf, NULL, Gfwd[i], Gbwd[i], Kf[i]) on the plan's own stream, forked
+ *   from and joined back into `stream` (arrays of nplans device pointers).
+ * cl_group_capture -- captures one cl_group_drift_eval with these pointers
+ *   into a CUDA graph (stream capture on an internal stream, so `stream` may
+ *   be the legacy default stream; nothing is executed; profiling must be
+ *   off).  Later launches read whatever the captured buffers then hold.
+ * cl_group_launch -- replays the captured graph on `stream` (one launch).
+ */
+int cl_group_create(int nplans, cl_plan* const* plans, cl_group** group);
+int cl_group_drift_eval(cl_group* group, const double* const* links, double m, double mu, double nf,
+                        double* const* Gfwd, double* const* Gbwd, double* const* Kf, cudaStream_t stream);
+int cl_group_capture(cl_group* group, const double* const* links, double m, double mu, double nf,
+                     double* const* Gfwd, double* const* Gbwd, double* const* Kf, cudaStream_t stream);
+int cl_group_launch(cl_group* group, cudaStream_t stream);
+void cl_group_destroy(cl_group* group);
 
 /* cl_destroy_plan -- frees the plan and all its device memory (NULL is a no-op). */
 void cl_destroy_plan(cl_plan* plan);

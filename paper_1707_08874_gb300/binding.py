@@ -75,7 +75,8 @@ def obs_dict(row) -> dict:
 EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
            "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
            "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
-           "cl_observables", "cl_langevin_step", "cl_destroy_plan", "cl_error_string"]
+           "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
+           "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string"]
 
 
 def lib_path() -> str:
@@ -113,12 +114,20 @@ def load(build_if_missing: bool = True):
     L.cl_gauge_cool.argtypes = [P, P, I, D, P]
     L.cl_observables.argtypes = [P, P, P, P, P, D, D, P, P]
     L.cl_langevin_step.argtypes = [P, P, ctypes.POINTER(LangevinParams), P, P, P]
+    L.cl_analyze_ex.argtypes = [I, I, I, I, I, ctypes.POINTER(P)]
+    PP = ctypes.POINTER(P)
+    L.cl_group_create.argtypes = [I, PP, PP]
+    L.cl_group_drift_eval.argtypes = [P, PP, D, D, D, PP, PP, PP, P]
+    L.cl_group_capture.argtypes = [P, PP, D, D, D, PP, PP, PP, P]
+    L.cl_group_launch.argtypes = [P, P]
+    L.cl_group_destroy.argtypes = [P]
+    L.cl_group_destroy.restype = None
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
     L.cl_error_string.restype = ctypes.c_char_p
     for f in EXPORTS:
-        if f not in ("cl_destroy_plan", "cl_error_string"):
+        if f not in ("cl_destroy_plan", "cl_error_string", "cl_group_destroy"):
             getattr(L, f).restype = I
     _lib = L
     return L
@@ -178,6 +187,12 @@ class Plan:
     def analyze(cls, Ns: int, Nt: int, batch: int = 1, precision: int = CL_FP64) -> "Plan":
         h = ctypes.c_void_p()
         _check(load().cl_analyze(Ns, Nt, batch, precision, ctypes.byref(h)), "cl_analyze")
+        return cls(h, False)
+
+    @classmethod
+    def analyze_ex(cls, Ns: int, Nt: int, batch: int, precision: int, panel: int) -> "Plan":
+        h = ctypes.c_void_p()
+        _check(load().cl_analyze_ex(Ns, Nt, batch, precision, panel, ctypes.byref(h)), "cl_analyze_ex")
         return cls(h, False)
 
     @classmethod
@@ -286,3 +301,42 @@ class Plan:
         kw = dict(dtype=torch.complex128, device="cuda")
         return dict(Gdiag=torch.empty((B, V, 3, 3), **kw), Gfwd=torch.empty((B, V, 4, 3, 3), **kw),
                     Gbwd=torch.empty((B, V, 4, 3, 3), **kw), Kf=torch.empty((B, V, 4, 8), **kw))
+
+
+class Group:
+    """cl_group: plans of several lattice shapes evaluated side by side, with
+    optional CUDA-graph capture of the whole schedule."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        self._h = ctypes.c_void_p()
+        _check(load().cl_group_create(len(self.plans), arr, ctypes.byref(self._h)), "cl_group_create")
+
+    @staticmethod
+    def _ptrs(ts, name):
+        return (ctypes.c_void_p * len(ts))(*[_dev(t, name).value for t in ts])
+
+    def drift_eval(self, links, m, mu, nf, Gfwd, Gbwd, Kf, stream=None):
+        _check(load().cl_group_drift_eval(self._h, self._ptrs(links, "links"), float(m), float(mu), float(nf),
+                                          self._ptrs(Gfwd, "Gfwd"), self._ptrs(Gbwd, "Gbwd"),
+                                          self._ptrs(Kf, "Kf"), _stream(stream)), "cl_group_drift_eval")
+
+    def capture(self, links, m, mu, nf, Gfwd, Gbwd, Kf, stream=None):
+        _check(load().cl_group_capture(self._h, self._ptrs(links, "links"), float(m), float(mu), float(nf),
+                                       self._ptrs(Gfwd, "Gfwd"), self._ptrs(Gbwd, "Gbwd"),
+                                       self._ptrs(Kf, "Kf"), _stream(stream)), "cl_group_capture")
+
+    def launch(self, stream=None):
+        _check(load().cl_group_launch(self._h, _stream(stream)), "cl_group_launch")
+
+    def close(self):
+        if self._h:
+            load().cl_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -132,7 +132,7 @@ int64_t tiles(int M, int N) {
 
 }  // namespace
 
-void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision) {
+void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) {
   if (Ns < 4 || Nt < 4 || (Ns & 1) || (Nt & 1)) throw std::invalid_argument("Ns, Nt must be even and >= 4");
   if (Ns > 64 || Nt > 128) throw std::invalid_argument("lattice too large");
   if (precision != CL_FP64 && precision != CL_MIXED_FP32 && precision != CL_FP64_EMU)
@@ -143,7 +143,9 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision) {
   p.N = 3 * p.V;
   p.batch = batch;
   p.precision = precision;
-  p.panel = precision == CL_FP64 ? kPanelFP64 : precision == CL_FP64_EMU ? kPanelEmu : kPanelFP32;
+  if (panel != 0 && (panel < 3 || panel > 48 || panel % 3 != 0)) throw std::invalid_argument("panel");
+  p.panel = panel ? panel
+                  : (precision == CL_FP64 ? kPanelFP64 : precision == CL_FP64_EMU ? kPanelEmu : kPanelFP32);
   Geo g{Ns, Nt, {Ns, Ns, Ns, Nt}};
   const int V = p.V;
 

@@ -93,6 +93,7 @@ int setup_device(Plan& p) {
       (e = upload(p.d_slots, nullptr, B * 4 * sizeof(unsigned long long), total)) != cudaSuccess)
     return cuda_status(e);
   if (p.precision == CL_FP64_EMU) {
+    if ((e = cl::emu_prepare()) != cudaSuccess) return cuda_status(e);
     if ((e = upload(p.d_emu, p.emu.data(), p.emu.size() * sizeof(cl::EmuDesc), total)) != cudaSuccess ||
         (e = upload(p.d_emu_words, nullptr, B * p.emu_words * sizeof(unsigned), total)) != cudaSuccess ||
         (e = upload(p.d_emu_ints, nullptr, B * p.emu_ints * sizeof(int), total)) != cudaSuccess)
@@ -188,14 +189,14 @@ int run(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, 
   return run_ops<double2, double>(p, ops, links, m, mu, Gd, Gf, Gb, st);
 }
 
-int make_plan(int Ns, int Nt, int batch, int precision, cl_plan** out, bool device) {
+int make_plan(int Ns, int Nt, int batch, int precision, int panel, cl_plan** out, bool device) {
   if (!out) return CL_ERR_INVALID_ARG;
   *out = nullptr;
   if (device && batch < 1) return CL_ERR_INVALID_ARG;
   cl_plan* plan = new (std::nothrow) cl_plan();
   if (!plan) return CL_ERR_OOM;
   try {
-    cl::analyze_host(plan->p, Ns, Nt, device ? batch : 1, precision);
+    cl::analyze_host(plan->p, Ns, Nt, device ? batch : 1, precision, panel);
   } catch (const std::invalid_argument&) {
     delete plan;
     return CL_ERR_INVALID_ARG;
@@ -223,11 +224,15 @@ int make_plan(int Ns, int Nt, int batch, int precision, cl_plan** out, bool devi
 extern "C" {
 
 int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan) {
-  return make_plan(Ns, Nt, batch, precision, plan, true);
+  return make_plan(Ns, Nt, batch, precision, 0, plan, true);
+}
+
+int cl_analyze_ex(int Ns, int Nt, int batch, int precision, int panel, cl_plan** plan) {
+  return make_plan(Ns, Nt, batch, precision, panel, plan, true);
 }
 
 int cl_analyze_symbolic(int Ns, int Nt, int precision, cl_plan** plan) {
-  return make_plan(Ns, Nt, 1, precision, plan, false);
+  return make_plan(Ns, Nt, 1, precision, 0, plan, false);
 }
 
 int cl_factor(cl_plan* plan, const double* links, double m, double mu, cudaStream_t stream) {

@@ -343,11 +343,13 @@ __global__ void __launch_bounds__(256, 1) k_gemm_emu(const GemmDesc* __restrict_
 
 size_t emu_smem_bytes() { return kEmuSmemBytes; }
 
+// opt the GEMM kernel in to > 48 KB of dynamic shared memory on the current
+// device (done when a plan is set up, outside any stream capture)
+cudaError_t emu_prepare() {
+  return cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmuSmemBytes);
+}
+
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
-  // opt in to > 48 KB of dynamic shared memory (a host-side attribute of the
-  // function on the current device; cheap, so set on every launch)
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmuSmemBytes);
-  if (e != cudaSuccess) return e;
   const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
   const dim3 gs((unsigned)((items + 7) / 8), (unsigned)p.batch);
   k_emu_split<<<gs, 256, 0, st>>>(p.d_gemm, p.d_emu, op.d0, op.d1, arena, p.arena_elems, p.d_emu_words, p.d_emu_ints,

@@ -16,6 +16,7 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, double2* arena, cudaStream_
 cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t st);
 // FP64-accurate GEMM on the BF16 tensor cores (split pass + digit GEMM)
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
+cudaError_t emu_prepare();
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

@@ -165,7 +165,8 @@ struct Plan {
 // kernel families for profiling records
 enum Family { F_ZERO, F_ASSEMBLE, F_EXTADD, F_PANEL, F_GEMM, F_COPY, F_GATHER, F_EXTRACT, F_DRIFT, F_COUNT };
 
-// host analysis (analyze.cpp); throws std::runtime_error on invalid input
-void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision);
+// host analysis (analyze.cpp); throws std::invalid_argument on invalid input.
+// panel: pivoting panel width in unknowns (multiple of 3, 3..48), 0 = default
+void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel = 0);
 
 }  // namespace cl

@@ -121,3 +121,10 @@ def test_flop_counts_scale(lib):
     n = sorted(f)
     slope = np.log(f[n[-1]] / f[n[0]]) / np.log(n[-1] / n[0])
     assert 1.5 < slope < 3.0
+
+
+@pytest.mark.parametrize("panel", [1, 4, 50, -3])
+def test_invalid_panel_width_rejected(lib, panel):
+    """cl_analyze_ex validates the panel width on the host before any device work."""
+    h = ctypes.c_void_p()
+    assert lib.cl_analyze_ex(4, 4, 1, B.CL_FP64, panel, ctypes.byref(h)) == B.CL_ERR_INVALID_ARG
