@@ -73,6 +73,7 @@ typedef struct cl_plan_info {
   double front_bytes;        /* device bytes of the front pool (all replicas)   */
   double device_bytes;       /* all device memory held by the plan              */
   int launches_per_eval;     /* library kernel launches of one cl_drift_eval    */
+  double workspace_bytes;    /* digit workspace of CL_FP64_EMU (all replicas)   */
 } cl_plan_info;
 
 /* Per-kernel timing record filled by cl_profile_read. */

@@ -41,7 +41,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_levels", ctypes.c_int), ("max_front", ctypes.c_int), ("max_pivot_block", ctypes.c_int),
                 ("panel", ctypes.c_int), ("factor_flops", ctypes.c_double), ("selinv_flops", ctypes.c_double),
                 ("front_bytes", ctypes.c_double), ("device_bytes", ctypes.c_double),
-                ("launches_per_eval", ctypes.c_int)]
+                ("launches_per_eval", ctypes.c_int), ("workspace_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -360,6 +360,7 @@ int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info) {
     for (const auto& op : *ops)
       if (op.kind != cl::OP_ZERO && op.blocks > 0) ++launches;
   info->launches_per_eval = launches;
+  info->workspace_bytes = (double)p.batch * (4.0 * p.emu_words + 4.0 * p.emu_ints);
   return CL_OK;
 }
 

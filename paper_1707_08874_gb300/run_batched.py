@@ -32,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--tune", action="store_true", help="autotune the panel width per shape")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--warm", type=int, default=2, help="graph launches before the timed ones")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -61,7 +62,7 @@ def main(argv=None):
     kf = [o["Kf"] for o in outs]
     group.drift_eval(links, 0.05, 0.25, 1.0, gf, gb, kf)   # warm-up, uncaptured
     group.capture(links, 0.05, 0.25, 1.0, gf, gb, kf)
-    for _ in range(2):
+    for _ in range(args.warm):
         group.launch()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -80,7 +81,8 @@ def main(argv=None):
     flops = sum((p.info["factor_flops"] + p.info["selinv_flops"]) * c for p, (_, _, c) in zip(plans, shapes))
     rec = {"precision": args.precision, "shapes": args.shapes, "replicas": total, "ms_per_step": ms,
            "evals_per_s": total / (ms / 1e3), "front_tflops": flops / (ms / 1e3) / 1e12, "panels": panels,
-           "device_gb": sum(p.info["device_bytes"] for p in plans) / 1e9, "per_shape": []}
+           "device_gb": sum(p.info["device_bytes"] for p in plans) / 1e9,
+           "workspace_gb": sum(p.info["workspace_bytes"] for p in plans) / 1e9, "per_shape": []}
     for (ns, nt, cnt), p, o, l in zip(shapes, plans, outs, links):
         entry = {"lattice": "%dx%d" % (ns, nt), "replicas": cnt, "max_front": p.info["max_front"]}
         if not args.no_check and prec != B.CL_FP64:

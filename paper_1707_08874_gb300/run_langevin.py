@@ -1,7 +1,7 @@
 """Complex-Langevin runs with the exact fermion drift (Sec. 4.1 set-up).
 
     python -m paper_1707_08874_gb300.run_langevin --Ns 8 --Nt 4 --beta 5.0 --steps 200 \
-        [--precision fp64|mixed] [--batch B] [--n-cool 5] [--out run.jsonl]
+        [--precision fp64_emu|fp64|mixed] [--batch B] [--n-cool 5] [--out run.jsonl]
 
 Each line of output is one step of replica 0 (and the replica means): Langevin
 time, step size, K_max, plaquettes, Polyakov loops, condensate, unitarity
@@ -33,7 +33,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--seed", type=int, default=1707)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp64_emu", "mixed"], default="fp64_emu")
     ap.add_argument("--start", choices=["random", "su3", "cold"], default="random")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
@@ -44,7 +44,7 @@ def main(argv=None):
     from . import binding as B
     from . import inputs
 
-    prec = B.CL_FP64 if args.precision == "fp64" else B.CL_MIXED_FP32
+    prec = {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[args.precision]
     plan = B.Plan.analyze(args.Ns, args.Nt, args.batch, prec)
     if args.start == "cold":
         U0 = np.stack([inputs.unit_links(args.Ns, args.Nt)] * args.batch)
