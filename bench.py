@@ -53,6 +53,22 @@ def parse():
     return ap.parse_args()
 
 
+def replica_seed(rank: int, bsz: int) -> int:
+    """Seed of replica 0 of this rank: ranks hold disjoint replica streams."""
+    from paper_1707_08874_gb300 import inputs
+    return inputs.BASE_SEED + rank * bsz
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise max of per-rank timings (the slowest rank sets the rate)."""
+    import torch
+    if dist is None:
+        return list(values)
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -217,7 +233,7 @@ def run_ours(args, rank, world, local):
     panel = autotune.tune_panel(NS, NT, bsz, prec, use_cache=False)
     plan = B.Plan.analyze_ex(NS, NT, bsz, prec, panel)
     info = plan.info
-    U = inputs.random_links(NS, NT, seed=inputs.BASE_SEED + rank * bsz, batch=bsz)
+    U = inputs.random_links(NS, NT, seed=replica_seed(rank, bsz), batch=bsz)
     links_host = torch.from_numpy(U).pin_memory()
     links = links_host.to("cuda", non_blocking=True)
     out = plan.alloc_outputs()
@@ -276,10 +292,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_ms = t0.elapsed_time(t1) / args.steps
 
-    if dist:
-        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, "cuda")
     if rank != 0:
         return
     value = world * bsz / (ms / 1e3)

@@ -36,12 +36,16 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp64_emu", "mixed"], default="fp64_emu")
     ap.add_argument("--start", choices=["random", "su3", "cold"], default="random")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--checkpoint", default=None, help="write a checkpoint here at the end (and every --every steps)")
+    ap.add_argument("--every", type=int, default=0)
+    ap.add_argument("--resume", default=None, help="continue from this checkpoint")
     args = ap.parse_args(argv)
 
     import numpy as np
     import torch
 
     from . import binding as B
+    from . import checkpoint
     from . import inputs
 
     prec = {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[args.precision]
@@ -51,8 +55,12 @@ def main(argv=None):
     else:
         U0 = inputs.random_links(args.Ns, args.Nt, seed=args.seed, batch=args.batch,
                                  sigma_im=0.1 if args.start == "random" else 0.0)
+    state0 = np.zeros((args.batch, 4))
+    if args.resume:
+        U0, state0, saved = checkpoint.load(args.resume)
+        args.kappa = saved.get("kappa", args.kappa)
     U = torch.from_numpy(U0).to("cuda")
-    state = torch.zeros((args.batch, 4), dtype=torch.float64, device="cuda")
+    state = torch.from_numpy(state0).to("cuda")
     obs = torch.zeros((args.batch, B.OBS_LEN), dtype=torch.float64, device="cuda")
     prm = dict(beta=args.beta, m=args.m, mu=args.mu, nf=args.nf, eps_max=args.eps_max, kappa=args.kappa,
                alpha_cool=args.alpha_cool, seed=args.seed, n_cool=args.n_cool, fermions=1)
@@ -64,7 +72,7 @@ def main(argv=None):
         o = obs.cpu().numpy()
         st, _ = plan.get_status()
         rows = [B.obs_dict(r) for r in o]
-        if args.kappa <= 0 and step < args.calib:
+        if prm["kappa"] <= 0 and step < args.calib:
             kcal.append(float(np.mean([r["kmax"] for r in rows])))
             if step == args.calib - 1:
                 prm["kappa"] = args.eps_max * float(np.mean(kcal))
@@ -81,6 +89,10 @@ def main(argv=None):
         if st != B.CL_OK:
             print(json.dumps({"error": B.error_string(st), "step": step + 1}), file=out, flush=True)
             break
+        if args.checkpoint and args.every and (step + 1) % args.every == 0:
+            checkpoint.save(args.checkpoint, U, state, prm)
+    if args.checkpoint:
+        checkpoint.save(args.checkpoint, U, state, prm)
     plan.close()
 
 

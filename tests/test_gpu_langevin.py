@@ -140,3 +140,36 @@ def test_pure_gauge_su3_stays_unitary():
     assert np.abs(I3 - np.eye(3)).max() < 1e-12
     assert B.obs_dict(obs.cpu().numpy()[0])["unitarity"] < 1e-12
     p.close()
+
+
+def test_checkpoint_resume_bitwise(tmp_path):
+    """4 steps straight == 2 steps, checkpoint, reload into fresh buffers, 2
+    steps: the noise of step n depends only on (seed, n, link, replica)."""
+    B = _B()
+    from paper_1707_08874_gb300 import checkpoint
+    prm = dict(beta=5.0, m=0.05, mu=0.25, nf=1.0, eps_max=1e-3, kappa=2e-3, alpha_cool=0.05, seed=77,
+               n_cool=1, fermions=1)
+    U0 = inputs.random_links(NS, NT, seed=12, batch=2)
+    p = B.Plan.analyze(NS, NT, 2, B.CL_FP64_EMU)
+
+    def run(U, state, n):
+        obs = torch.zeros((2, 20), dtype=torch.float64, device="cuda")
+        for _ in range(n):
+            p.langevin_step(U, prm, state, obs)
+        torch.cuda.synchronize()
+
+    Ua = _dev(U0)
+    sa = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    run(Ua, sa, 4)
+    Ub = _dev(U0)
+    sb = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    run(Ub, sb, 2)
+    path = str(tmp_path / "ck.npz")
+    checkpoint.save(path, Ub, sb, prm)
+    U2, s2, prm2 = checkpoint.load(path)
+    assert prm2 == prm
+    Uc, sc = _dev(U2), _dev(s2)
+    run(Uc, sc, 2)
+    assert np.array_equal(Ua.cpu().numpy(), Uc.cpu().numpy())
+    assert np.array_equal(sa.cpu().numpy(), sc.cpu().numpy())
+    p.close()

@@ -197,3 +197,24 @@ def test_fp64_full_size_sampled(prec, full_size):
     kmax = np.abs(K).max()
     assert np.abs(K[ys] - Kref[ys]).max() < tol * kmax
     plan.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_singular_panel_reported(prec):
+    """m = 0, mu = 0 and one temporal link of -1 on the ring of sites
+    (1,1,1,t): the ring's holonomy cancels the antiperiodic sign, so that leaf's
+    pivot block has an exact zero mode (static pivoting cannot avoid it) and the
+    status word names the supernode; a regular configuration clears it."""
+    B = _binding()
+    plan = B.Plan.analyze(4, 4, 1, _prec(B, prec))
+    leaf = [i for i in range(plan.info["n_supernodes"]) if 21 in plan.node(i)["sep"]][0]
+    U = inputs.unit_links(4, 4)
+    U[21, 3] = -np.eye(3)
+    links = torch.from_numpy(U[None].copy()).to("cuda")
+    out = plan.alloc_outputs()
+    plan.drift_eval(links, 0.0, 0.0, 1.0, out["Gdiag"], out["Gfwd"], out["Gbwd"], out["Kf"])
+    st, detail = plan.get_status()
+    assert st == B.CL_ERR_SINGULAR and detail[0] == leaf
+    got, st = _run(plan, inputs.random_links(4, 4, seed=8))
+    assert st == B.CL_OK
+    plan.close()
