@@ -358,7 +358,8 @@ int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info) {
   int launches = 1;  // drift
   for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
     for (const auto& op : *ops)
-      if (op.kind != cl::OP_ZERO && op.blocks > 0) ++launches;
+      if (op.kind != cl::OP_ZERO && op.blocks > 0)
+        launches += (op.kind == cl::OP_GEMM && p.precision == CL_FP64_EMU) ? 2 : 1;  // split + GEMM
   info->launches_per_eval = launches;
   info->workspace_bytes = (double)p.batch * (4.0 * p.emu_words + 4.0 * p.emu_ints);
   return CL_OK;

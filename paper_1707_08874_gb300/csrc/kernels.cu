@@ -175,11 +175,20 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
         rmap[bi] = rmap[c];
         rmap[c] = pc;
         if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
+        // 1/pv = conj(pv) / |pv|^2; the reciprocal of |pv|^2 from a
+        // single-precision seed refined by two Newton steps (24 -> 48 -> 96
+        // bits), a short dependent chain on the serial path of the panel
         const T pv = S[pc][c];
         const R n2 = pv.x * pv.x + pv.y * pv.y;
+        R r = (R)(1.0f / (float)n2);
+        if (sizeof(R) == 8) {
+          r = r * ((R)2 - n2 * r);
+          r = r * ((R)2 - n2 * r);
+        }
+        if (!(n2 > 0) || !isfinite(r)) r = (R)1 / n2;  // zero / overflow / NaN: plain division
         T inv;
-        inv.x = pv.x / n2;
-        inv.y = -pv.y / n2;
+        inv.x = pv.x * r;
+        inv.y = -pv.y * r;
         sinv = inv;
       }
     }
