@@ -211,7 +211,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   std::vector<int64_t> level_tmp(p.n_levels, 0);
   for (int i = 0; i < nn; ++i) {
     SNode& n = nodes[i];
-    int64_t need = std::max<int64_t>(2LL * b * n.nf, 2LL * n.r * n.k);
+    int64_t need = std::max<int64_t>(4LL * b * n.nf, 2LL * n.r * n.k);  // two TR/TC sets (look-ahead)
     need = (need + 15) / 16 * 16;
     n.tmp = p.pool_elems + level_tmp[n.level];
     level_tmp[n.level] += need;
@@ -283,25 +283,28 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   std::vector<std::vector<int>> by_level(p.n_levels);
   for (int i = 0; i < nn; ++i) by_level[nodes[i].level].push_back(i);
 
+  const Mask2 none{0, 0, 0, 0};
   auto add_gemm = [&](int blk, int64_t a, int lda, int64_t bb, int ldb, int64_t c, int ldc, int M, int N,
-                      int K, int neg, int beta, int m0, int m1) {
-    GemmDesc d{a, bb, c, lda, ldb, ldc, M, N, K, neg, beta, m0, m1, blk, (N + kTileN - 1) / kTileN};
+                      int K, int neg, int beta, Mask2 rm, Mask2 cm) {
+    GemmDesc d{a, bb, c, lda, ldb, ldc, M, N, K, neg, beta, rm, cm, blk, (N + kTileN - 1) / kTileN};
     p.gemm.push_back(d);
     return (int)tiles(M, N);
   };
-  auto add_copy = [&](int blk, int64_t src, int lds, int64_t dst, int ldd, int rows, int cols, int rm0, int rm1,
-                      int cm0, int cm1) {
-    CopyDesc d{src, dst, lds, ldd, rows, cols, rm0, rm1, cm0, cm1, blk};
+  auto add_copy = [&](int blk, int64_t src, int lds, int64_t dst, int ldd, int rows, int cols, Mask2 rm,
+                      Mask2 cm) {
+    CopyDesc d{src, dst, lds, ldd, rows, cols, rm, cm, blk};
     p.copies.push_back(d);
     return (int)(((int64_t)rows * cols + 255) / 256);
   };
 
   p.factor_ops.push_back(Op{OP_ZERO, 0, 0, 0, -1});
   p.factor_ops.push_back(Op{OP_ASSEMBLE, 0, 0, (4 * V + 127) / 128, -1});
+  std::vector<int> level_last_copy(p.n_levels, -1);
   for (int h = 0; h < p.n_levels; ++h) {
     const auto& lv = by_level[h];
     if (h > 0) {
       Op op{OP_EXTADD, (int)p.extadd.size(), 0, 0, h};
+      op.wait = level_last_copy[h - 1];  // the children's Schur complements are complete
       int blk = 0;
       for (int i : lv) {
         const SNode& P = nodes[i];
@@ -330,24 +333,33 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       op.blocks = blk;
       if (op.d1 > op.d0) p.factor_ops.push_back(op);
     }
+    // Blocked sweep of the pivot panels with a one-panel look-ahead.  Stream 0
+    // (critical): panel inverse, panel products TR/TC, the update of the
+    // next panel's row and column strips and the entries the next panel
+    // reads from the current one.  Stream 1: the bulk rank-b update of the
+    // rest of the front and the write-back of the panel.  TR/TC alternate
+    // between two workspace sets by panel parity.
     int maxk = 0;
     for (int i : lv) maxk = std::max(maxk, nodes[i].k);
-    for (int c0 = 0; c0 < maxk; c0 += b) {
+    int last_copy = -1;  // op index of the previous step's stream-1 write-back
+    for (int c0 = 0, step = 0; c0 < maxk; c0 += b, ++step) {
+      const int set = step & 1;
+      auto tR_of = [&](const SNode& n) { return n.tmp + (int64_t)set * 2 * b * n.nf; };
+      auto tC_of = [&](const SNode& n) { return tR_of(n) + (int64_t)b * n.nf; };
       Op pinv{OP_PANEL, (int)p.panels.size(), 0, 0, h};
       Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
       int blk1 = 0;
       for (int i : lv) {
         const SNode& n = nodes[i];
         if (c0 >= n.k) continue;
-        int bp = std::min(b, n.k - c0);
+        const int bp = std::min(b, n.k - c0);
         p.panels.push_back(PanelDesc{n.off + (int64_t)c0 * n.nf + c0, n.nf, bp, i, c0});
         if (n.nf == bp) continue;  // nothing outside the panel
-        int64_t tR = n.tmp, tC = n.tmp + (int64_t)b * n.nf;
-        // TR = Y * R_old  (bp x nf), TC = -C_old * Y (nf x bp)
-        blk1 += add_gemm(blk1, n.off + (int64_t)c0 * n.nf + c0, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, tR, n.nf,
-                         bp, n.nf, bp, 0, 0, 0, 0);
-        blk1 += add_gemm(blk1, n.off + c0, n.nf, n.off + (int64_t)c0 * n.nf + c0, n.nf, tC, bp, n.nf, bp, bp, 1,
-                         0, 0, 0);
+        // TR = Y * R_old (bp x nf), TC = -C_old * Y (nf x bp)
+        blk1 += add_gemm(blk1, n.off + (int64_t)c0 * n.nf + c0, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, tR_of(n),
+                         n.nf, bp, n.nf, bp, 0, 0, none, none);
+        blk1 += add_gemm(blk1, n.off + c0, n.nf, n.off + (int64_t)c0 * n.nf + c0, n.nf, tC_of(n), bp, n.nf, bp, bp,
+                         1, 0, none, none);
       }
       pinv.d1 = (int)p.panels.size();
       pinv.blocks = pinv.d1 - pinv.d0;
@@ -355,28 +367,68 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       g1.d1 = (int)p.gemm.size();
       g1.blocks = blk1;
       if (g1.d1 == g1.d0) continue;
+      g1.signal = true;
+      const int g1_idx = (int)p.factor_ops.size();
       p.factor_ops.push_back(g1);
+      // next-panel strips and the entries the next panel reads (stream 0)
+      Op st{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+      Op ec{OP_COPY, (int)p.copies.size(), 0, 0, h};
+      int blks = 0, blke = 0;
+      for (int i : lv) {
+        const SNode& n = nodes[i];
+        if (c0 >= n.k) continue;
+        const int bp = std::min(b, n.k - c0), c1 = c0 + b;
+        if (n.nf == bp || c1 >= n.k) continue;
+        const int b1 = std::min(b, n.k - c1);
+        const int64_t tR = tR_of(n), tC = tC_of(n);
+        // row strip: A[c1.., j] -= C_old[c1.., :] TR[:, j], j outside panel p
+        blks += add_gemm(blks, n.off + (int64_t)c1 * n.nf + c0, n.nf, tR, n.nf, n.off + (int64_t)c1 * n.nf, n.nf, b1,
+                         n.nf, bp, 1, 1, none, Mask2{c0, c0 + bp, 0, 0});
+        // column strip: A[r, c1..] -= C_old[r, :] TR[:, c1..], r outside panels p and p+1
+        blks += add_gemm(blks, n.off + c0, n.nf, tR + c1, n.nf, n.off + c1, n.nf, n.nf, b1, bp, 1, 1,
+                         Mask2{c0, c0 + bp, c1, c1 + b1}, none);
+        // swept entries of panel p that panel p+1 reads: A[c1.., c0..] = TC, A[c0.., c1..] = TR
+        blke += add_copy(blke, tC + (int64_t)c1 * bp, bp, n.off + (int64_t)c1 * n.nf + c0, n.nf, b1, bp, none, none);
+        blke += add_copy(blke, tR + c1, n.nf, n.off + (int64_t)c0 * n.nf + c1, n.nf, bp, b1, none, none);
+      }
+      st.d1 = (int)p.gemm.size();
+      st.blocks = blks;
+      ec.d1 = (int)p.copies.size();
+      ec.blocks = blke;
+      if (st.d1 > st.d0) {
+        st.wait = last_copy;  // the previous bulk update and write-back touched these strips
+        p.factor_ops.push_back(st);
+        p.factor_ops.push_back(ec);
+      }
+      // bulk update and write-back of panel p (stream 1)
       Op g2{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
       Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
       int blk2 = 0, blk3 = 0;
       for (int i : lv) {
         const SNode& n = nodes[i];
         if (c0 >= n.k) continue;
-        int bp = std::min(b, n.k - c0);
+        const int bp = std::min(b, n.k - c0), c1 = c0 + b;
         if (n.nf == bp) continue;
-        int64_t tR = n.tmp, tC = n.tmp + (int64_t)b * n.nf;
-        // rest: A[r][c] -= C_old[r] * TR[c] for r, c outside the panel
-        blk2 += add_gemm(blk2, n.off + c0, n.nf, tR, n.nf, n.off, n.nf, n.nf, n.nf, bp, 1, 1, c0, c0 + bp);
-        blk3 += add_copy(blk3, tC, bp, n.off + c0, n.nf, n.nf, bp, c0, c0 + bp, 0, 0);
-        blk3 += add_copy(blk3, tR, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, bp, n.nf, 0, 0, c0, c0 + bp);
+        const int b1 = c1 < n.k ? std::min(b, n.k - c1) : 0;
+        const Mask2 pp{c0, c0 + bp, c1, c1 + b1};  // panels p and p+1
+        const int64_t tR = tR_of(n), tC = tC_of(n);
+        blk2 += add_gemm(blk2, n.off + c0, n.nf, tR, n.nf, n.off, n.nf, n.nf, n.nf, bp, 1, 1, pp, pp);
+        blk3 += add_copy(blk3, tC, bp, n.off + c0, n.nf, n.nf, bp, pp, none);
+        blk3 += add_copy(blk3, tR, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, bp, n.nf, none, pp);
       }
       g2.d1 = (int)p.gemm.size();
       g2.blocks = blk2;
+      g2.stream = 1;
+      g2.wait = g1_idx;
       cp.d1 = (int)p.copies.size();
       cp.blocks = blk3;
+      cp.stream = 1;
+      cp.signal = true;
       p.factor_ops.push_back(g2);
+      last_copy = (int)p.factor_ops.size();
       p.factor_ops.push_back(cp);
     }
+    level_last_copy[h] = last_copy;
   }
 
   // selected inversion: root to leaves
@@ -404,8 +456,8 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       if (n.r == 0) continue;
       int64_t tSJ = n.tmp, tJS = n.tmp + (int64_t)n.r * n.k;
       int64_t SS = n.off + (int64_t)n.k * n.nf + n.k, SJ = n.off + (int64_t)n.k * n.nf, JS = n.off + n.k;
-      blk1 += add_gemm(blk1, SS, n.nf, SJ, n.nf, tSJ, n.k, n.r, n.k, n.r, 0, 0, 0, 0);   // G_SJ = G_SS (-Lhat)
-      blk1 += add_gemm(blk1, JS, n.nf, SS, n.nf, tJS, n.r, n.k, n.r, n.r, 1, 0, 0, 0);   // G_JS = -Uhat G_SS
+      blk1 += add_gemm(blk1, SS, n.nf, SJ, n.nf, tSJ, n.k, n.r, n.k, n.r, 0, 0, none, none);  // G_SJ = G_SS (-Lhat)
+      blk1 += add_gemm(blk1, JS, n.nf, SS, n.nf, tJS, n.r, n.k, n.r, n.r, 1, 0, none, none);  // G_JS = -Uhat G_SS
     }
     g1.d1 = (int)p.gemm.size();
     g1.blocks = blk1;
@@ -419,9 +471,9 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       int64_t tSJ = n.tmp, tJS = n.tmp + (int64_t)n.r * n.k;
       int64_t SJ = n.off + (int64_t)n.k * n.nf, JS = n.off + n.k;
       // G_JJ = Ainv - Uhat G_SJ = Ainv + G_JS (-Lhat)... written as Ainv + tJS * F_SJ
-      blk2 += add_gemm(blk2, tJS, n.r, SJ, n.nf, n.off, n.nf, n.k, n.k, n.r, 0, 1, 0, 0);
-      blk3 += add_copy(blk3, tSJ, n.k, SJ, n.nf, n.r, n.k, 0, 0, 0, 0);
-      blk3 += add_copy(blk3, tJS, n.r, JS, n.nf, n.k, n.r, 0, 0, 0, 0);
+      blk2 += add_gemm(blk2, tJS, n.r, SJ, n.nf, n.off, n.nf, n.k, n.k, n.r, 0, 1, none, none);
+      blk3 += add_copy(blk3, tSJ, n.k, SJ, n.nf, n.r, n.k, none, none);
+      blk3 += add_copy(blk3, tJS, n.r, JS, n.nf, n.k, n.r, none, none);
     }
     g2.d1 = (int)p.gemm.size();
     g2.blocks = blk2;
@@ -433,11 +485,14 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, (4 * V + 127) / 128, -1});
 
   // split-digit workspace of the FP64 emulation: per GEMM launch the problems
-  // are laid out one after the other from offset 0 (launches run in order)
+  // are laid out one after the other from the start of that launch's stream
+  // region (launches of one stream run in order; the factorisation's second
+  // stream gets a region of its own after the first one's)
   p.emu.clear();
   p.emu_words = p.emu_ints = 0;
   if (precision == CL_FP64_EMU) {
     p.emu.resize(p.gemm.size());
+    int64_t max_w[2] = {0, 0}, max_in[2] = {0, 0};
     for (auto* ops : {&p.factor_ops, &p.selinv_ops})
       for (auto& op : *ops) {
         if (op.kind != OP_GEMM) continue;
@@ -467,9 +522,20 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
           blk += (e.Mp / kEmuTileM) * g.tilesN;
         }
         op.blocks = blk;
-        p.emu_words = std::max(p.emu_words, w);
-        p.emu_ints = std::max(p.emu_ints, in);
+        max_w[op.stream] = std::max(max_w[op.stream], w);
+        max_in[op.stream] = std::max(max_in[op.stream], in);
       }
+    for (auto& op : p.factor_ops) {
+      if (op.kind != OP_GEMM || op.stream == 0) continue;
+      for (int d = op.d0; d < op.d1; ++d) {
+        p.emu[d].adig += max_w[0];
+        p.emu[d].bdig += max_w[0];
+        p.emu[d].aexp += max_in[0];
+        p.emu[d].bexp += max_in[0];
+      }
+    }
+    p.emu_words = max_w[0] + max_w[1];
+    p.emu_ints = max_in[0] + max_in[1];
   }
 }
 

@@ -43,6 +43,15 @@ void free_device(Plan& p) {
   cudaFree(p.d_emu_ints);
   for (double* q : {p.d_Gdiag, p.d_Gfwd, p.d_Gbwd, p.d_K, p.d_Ui, p.d_F, p.d_Om, p.d_Omi, p.d_part}) cudaFree(q);
   cudaFree(p.d_slots);
+  for (void* ev : p.op_events)
+    if (ev) cudaEventDestroy((cudaEvent_t)ev);
+  p.op_events.clear();
+  for (void* ev : {p.fork_event, p.join_events[0], p.join_events[1]})
+    if (ev) cudaEventDestroy((cudaEvent_t)ev);
+  for (void* s : p.streams)
+    if (s) cudaStreamDestroy((cudaStream_t)s);
+  p.fork_event = p.join_events[0] = p.join_events[1] = nullptr;
+  p.streams[0] = p.streams[1] = nullptr;
   cudaSetDevice(prev);
   p.has_device = false;
 }
@@ -92,6 +101,30 @@ int setup_device(Plan& p) {
       (e = upload(p.d_part, nullptr, B * cl::obs_partial_doubles(p) * sizeof(double), total)) != cudaSuccess ||
       (e = upload(p.d_slots, nullptr, B * 4 * sizeof(unsigned long long), total)) != cudaSuccess)
     return cuda_status(e);
+  // streams and events of the two-stream factorisation
+  bool two_streams = false;
+  for (const auto& op : p.factor_ops) two_streams |= op.stream != 0;
+  if (two_streams) {
+    int lo = 0, hi = 0;
+    cudaStream_t s0 = nullptr, s1 = nullptr;
+    if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&s0, cudaStreamNonBlocking, hi)) != cudaSuccess)
+      return cuda_status(e);
+    p.streams[0] = s0;
+    if ((e = cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, lo)) != cudaSuccess) return cuda_status(e);
+    p.streams[1] = s1;
+    cudaEvent_t ev = nullptr;
+    for (void** slot : {&p.fork_event, &p.join_events[0], &p.join_events[1]}) {
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+      *slot = ev;
+    }
+    p.op_events.assign(p.factor_ops.size(), nullptr);
+    for (size_t i = 0; i < p.factor_ops.size(); ++i) {
+      if (!p.factor_ops[i].signal) continue;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+      p.op_events[i] = ev;
+    }
+  }
   if (p.precision == CL_FP64_EMU) {
     if ((e = cl::emu_prepare()) != cudaSuccess) return cuda_status(e);
     if ((e = upload(p.d_emu, p.emu.data(), p.emu.size() * sizeof(cl::EmuDesc), total)) != cudaSuccess ||
@@ -164,23 +197,58 @@ void prof_end(Plan& p, cudaStream_t st, cudaEvent_t e0, int family, double flops
 }
 
 template <typename T, typename R>
+int launch_one(Plan& p, const cl::Op& op, T* arena, const double* links, double m, double mu, double* Gd,
+               double* Gf, double* Gb, cudaStream_t st) {
+  if (op.blocks == 0 && op.kind != cl::OP_ZERO) return CL_OK;
+  cudaEvent_t e0;
+  prof_begin(p, st, e0);
+  cudaError_t e = cl::launch_op<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (p.profiling) {
+    int fam;
+    double fl, by;
+    op_work(p, op, fam, fl, by);
+    prof_end(p, st, e0, fam, fl, by);
+  }
+  return CL_OK;
+}
+
+// Runs a schedule on the caller's stream.  A schedule with look-ahead (ops
+// tagged for stream 1) runs on the plan's two streams: both are forked from
+// the caller's stream, each op first waits for the op whose event it names,
+// ops that signal record their event, and the caller's stream joins both at
+// the end.  The same ops issued in list order on one stream give the same
+// result (the list order is a valid sequential order).
+template <typename T, typename R>
 int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, double mu, double* Gd,
             double* Gf, double* Gb, cudaStream_t st) {
   T* arena = static_cast<T*>(p.d_arena);
-  for (const auto& op : ops) {
-    if (op.blocks == 0 && op.kind != cl::OP_ZERO) continue;
-    cudaEvent_t e0;
-    prof_begin(p, st, e0);
-    cudaError_t e = cl::launch_op<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, st);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (p.profiling) {
-      int fam;
-      double fl, by;
-      op_work(p, op, fam, fl, by);
-      prof_end(p, st, e0, fam, fl, by);
+  const bool two = &ops == &p.factor_ops && p.streams[1] != nullptr;
+  if (!two) {
+    for (const auto& op : ops) {
+      const int r = launch_one<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, st);
+      if (r != CL_OK) return r;
     }
+    return CL_OK;
   }
-  return CL_OK;
+  cudaStream_t ss[2] = {(cudaStream_t)p.streams[0], (cudaStream_t)p.streams[1]};
+  cudaError_t e = cudaEventRecord((cudaEvent_t)p.fork_event, st);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], (cudaEvent_t)p.fork_event, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const cl::Op& op = ops[i];
+    cudaStream_t s = ss[op.stream];
+    if (op.wait >= 0 && (e = cudaStreamWaitEvent(s, (cudaEvent_t)p.op_events[op.wait], 0)) != cudaSuccess)
+      return cuda_status(e);
+    const int r = launch_one<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, s);
+    if (r != CL_OK) return r;
+    if (op.signal && (e = cudaEventRecord((cudaEvent_t)p.op_events[i], s)) != cudaSuccess) return cuda_status(e);
+  }
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventRecord((cudaEvent_t)p.join_events[k], ss[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, (cudaEvent_t)p.join_events[k], 0);
+  }
+  return cuda_status(e);
 }
 
 int run(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, double mu, double* Gd,

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128) k_gemm_f64(const GemmDesc* __restrict__ d
     for (int j = 0; j < 4; ++j) {
       const int r = row0 + wm + 8 * i + g, c = col0 + wn + 4 * j + tig;
       if (r >= d.M || c >= d.N) continue;
-      if ((r >= d.mask0 && r < d.mask1) || (c >= d.mask0 && c < d.mask1)) continue;
+      if (d.rmask.hit(r) || d.cmask.hit(c)) continue;
       double2 v = make_double2(sg * acc[i][j][0], sg * acc[i][j][1]);
       double2* p = C + (int64_t)r * d.ldc + c;
       if (d.beta) v = cadd(v, *p);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const GemmDesc* __restrict__ d
     for (int j = 0; j < 2; ++j) {
       const int r = row0 + tr + 16 * i, c = col0 + tc + 16 * j;
       if (r >= d.M || c >= d.N) continue;
-      if ((r >= d.mask0 && r < d.mask1) || (c >= d.mask0 && c < d.mask1)) continue;
+      if (d.rmask.hit(r) || d.cmask.hit(c)) continue;
       float2 v = make_float2(sg * acc[i][j].x, sg * acc[i][j].y);
       float2* p = C + (int64_t)r * d.ldc + c;
       if (d.beta) {

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_emu(const GemmDesc* __restrict_
         const int rl = wm + 16 * i + gq + rr * 8, cl = wn + 4 * j + tq;
         const int r = row0 + rl, cc = col0 + cl;
         if (r >= g.M || cc >= g.N) continue;
-        if ((r >= g.mask0 && r < g.mask1) || (cc >= g.mask0 && cc < g.mask1)) continue;
+        if (g.rmask.hit(r) || g.cmask.hit(cc)) continue;
         const int ex = Rm[rl] + Sm[cl];
         double vv[2];
 #pragma unroll

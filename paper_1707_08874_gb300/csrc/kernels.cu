@@ -264,7 +264,7 @@ __global__ void k_copy(const CopyDesc* __restrict__ ds, int d0, int d1, T* __res
   const int64_t e = (int64_t)(blockIdx.x - d.blk0) * 256 + threadIdx.x;
   if (e >= (int64_t)d.rows * d.cols) return;
   const int i = (int)(e / d.cols), j = (int)(e % d.cols);
-  if ((i >= d.rm0 && i < d.rm1) || (j >= d.cm0 && j < d.cm1)) return;
+  if (d.rmask.hit(i) || d.cmask.hit(j)) return;
   T* A = arena + blockIdx.y * stride;
   A[d.dst + (int64_t)i * d.ldd + j] = A[d.src + (int64_t)i * d.lds + j];
 }

@@ -31,14 +31,20 @@ struct SNode {
   int64_t tmp = 0;            // offset of this front's workspace (elements)
 };
 
+// Two excluded index ranges [r0, r1) and [r2, r3) (empty ranges allowed).
+struct Mask2 {
+  int r0, r1, r2, r3;
+  __host__ __device__ bool hit(int i) const { return (i >= r0 && i < r1) || (i >= r2 && i < r3); }
+};
+
 // C = beta*C + (neg ? -1 : +1) * A * B on one front; offsets are elements of the
-// replica arena; rows and columns inside [mask0, mask1) of C are left untouched.
+// replica arena; rows in `rmask` and columns in `cmask` of C are left untouched.
 struct GemmDesc {
   int64_t a, b, c;
   int lda, ldb, ldc;
   int M, N, K;
   int neg, beta;
-  int mask0, mask1;
+  Mask2 rmask, cmask;
   int blk0, tilesN;  // first CTA of this problem inside its launch; tiles along N
 };
 
@@ -49,13 +55,13 @@ struct PanelDesc {
   int node, col0;
 };
 
-// dst[i][j] = src[i][j] for i < rows, j < cols, skipping rows in [rm0,rm1) and
-// columns in [cm0,cm1).
+// dst[i][j] = src[i][j] for i < rows, j < cols, skipping rows in `rmask` and
+// columns in `cmask`.
 struct CopyDesc {
   int64_t src, dst;
   int lds, ldd;
   int rows, cols;
-  int rm0, rm1, cm0, cm1;
+  Mask2 rmask, cmask;
   int blk0;
 };
 
@@ -93,11 +99,20 @@ struct EmuDesc {
 
 enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT };
 
+// One scheduled launch.  The factorisation runs on two streams: the
+// critical chain (panel inverses, panel products, next-panel strips) on the
+// caller's stream (stream 0) and the bulk rank-b updates with the panel
+// write-back on an internal stream (stream 1).  `wait` names an earlier op on
+// the other stream whose completion must precede this one (-1: none);
+// `signal` records the completion event of this op.
 struct Op {
   OpKind kind;
   int d0, d1;     // descriptor range in the table of this kind
   int blocks;     // CTAs per replica
   int level;
+  int stream = 0;
+  int wait = -1;
+  bool signal = false;
 };
 
 struct Plan {
@@ -160,6 +175,13 @@ struct Plan {
   };
   bool profiling = false;
   std::vector<ProfRec> prof;
+  // the factorisation's two streams (0: high-priority panel chain, 1: bulk
+  // updates) and the events of its cross-stream dependencies, created with
+  // the device state
+  void* streams[2] = {nullptr, nullptr};
+  std::vector<void*> op_events;  // per factor op (nullptr when it does not signal)
+  void* fork_event = nullptr;
+  void* join_events[2] = {nullptr, nullptr};
 };
 
 // kernel families for profiling records
