@@ -267,6 +267,32 @@ int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double m, double 
                           double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
 
 /*
+ * cl_zgemm_emu -- FP64-accurate complex GEMM on the BF16 tensor cores, the
+ * kernel behind CL_FP64_EMU (the dense front products of Sec. 3 - Schur
+ * updates and selected-inverse blocks - as one call):
+ *   C = [C if beta] + (-1 if neg) * A B
+ *   M, N, K     >= 1
+ *   A           device, M x K complex (interleaved re, im doubles), row-major, lda >= K
+ *   B           device, K x N complex, row-major, ldb >= N
+ *   C           device, M x N complex, row-major, ldc >= N (in / out); must not overlap A or B
+ *   beta, neg   0 or 1
+ *   work        device scratch of cl_zgemm_emu_workspace bytes, 256-byte aligned,
+ *               caller-owned, not used by another call in flight
+ *   status      device int[4] (caller-owned, zeroed by the caller): a tensor-core
+ *               wait that gives up records CL_ERR_TIMEOUT in status[0]
+ * A, B, C must be 16-byte aligned.  Each operand element is split into seven
+ * 8-bit digits per row (A) / column (B) and per 32-element k chunk; the 28
+ * leading digit products run as BF16 tcgen05 MMAs with FP32 accumulators in
+ * tensor memory, folded in triple-float and rounded once to FP64.  The paper
+ * computes in FP64; this path reproduces an FP64 GEMM's accuracy.  Returns
+ * CL_ERR_INVALID_ARG for bad sizes, strides, alignment or a short workspace,
+ * CL_ERR_CUDA on a launch failure; stream-ordered, no host synchronisation.
+ */
+int cl_zgemm_emu_workspace(int M, int N, int K, size_t* bytes);
+int cl_zgemm_emu(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                 int beta, int neg, void* work, size_t work_bytes, int* status, cudaStream_t stream);
+
+/*
  * cl_get_status -- synchronises `stream`, returns the first numerical error
  * recorded since the last call (CL_OK if none) in *info and clears it.
  * detail (may be NULL) receives the supernode and panel column of a

@@ -76,7 +76,8 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
            "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
-           "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string"]
+           "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
+           "cl_zgemm_emu_workspace", "cl_zgemm_emu"]
 
 
 def lib_path() -> str:
@@ -122,6 +123,8 @@ def load(build_if_missing: bool = True):
     L.cl_group_launch.argtypes = [P, P]
     L.cl_group_destroy.argtypes = [P]
     L.cl_group_destroy.restype = None
+    L.cl_zgemm_emu_workspace.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.cl_zgemm_emu.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, ctypes.c_size_t, P, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
@@ -150,6 +153,33 @@ def drift_eval_noalloc(Ns: int, Nt: int, links, m: float, mu: float, nf: float, 
     return load().cl_drift_eval_noalloc(Ns, Nt, _dev(links, "links"), float(m), float(mu), float(nf),
                                         _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
                                         _dev(Kf, "Kf"), _stream(stream))
+
+
+def zgemm_emu(A, B, C=None, beta: bool = False, neg: bool = False, stream=None):
+    """C = [C] +/- A @ B through cl_zgemm_emu (complex128 CUDA tensors, 2-D,
+    row-major with unit column stride).  Returns (C, status code of the
+    device status word)."""
+    import torch
+    L = load()
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.complex128, device=A.device)
+    nbytes = ctypes.c_size_t()
+    _check(L.cl_zgemm_emu_workspace(M, N, K, ctypes.byref(nbytes)), "cl_zgemm_emu_workspace")
+    work = torch.empty(nbytes.value, dtype=torch.uint8, device=A.device)
+    status = torch.zeros(4, dtype=torch.int32, device=A.device)
+    for t, n in ((A, "A"), (B, "B"), (C, "C")):
+        if not (t.is_cuda and t.dtype == torch.complex128 and t.dim() == 2 and t.stride(1) == 1):
+            raise TypeError("%s must be a 2-D complex128 CUDA tensor with unit column stride" % n)
+    _check(L.cl_zgemm_emu(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                          B.stride(0), ctypes.c_void_p(C.data_ptr()), C.stride(0), int(beta), int(neg),
+                          ctypes.c_void_p(work.data_ptr()), nbytes.value, ctypes.c_void_p(status.data_ptr()),
+                          _stream(stream)), "cl_zgemm_emu")
+    torch.cuda.synchronize()
+    return C, int(status[0].item())
 
 
 def _check(code: int, what: str):

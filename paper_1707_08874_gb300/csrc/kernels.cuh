@@ -17,6 +17,10 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t
 // FP64-accurate GEMM on the BF16 tensor cores (split pass + digit GEMM)
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 cudaError_t emu_prepare();
+// split pass + digit GEMM over descriptors [d0, d1) (tc: tcgen05 kernel and tiled digit layout)
+cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
+                       double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
+                       int* status, bool tc, cudaStream_t st);
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

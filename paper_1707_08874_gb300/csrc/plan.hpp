@@ -137,6 +137,7 @@ struct Plan {
   std::vector<GatherDesc> gather;
   std::vector<EmuDesc> emu;                         // parallel to gemm (CL_FP64_EMU only)
   int64_t emu_words = 0, emu_ints = 0;              // workspace per replica
+  bool emu_tc = true;                               // tcgen05 digit GEMM (false: mma.sync)
   std::vector<Op> factor_ops, selinv_ops;
   // device memory
   void* d_arena = nullptr;       // batch * arena_elems complex (precision-dependent)
