@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--panel", type=int, default=0, help="pivot-panel width (0: autotune)")
     return ap.parse_args()
 
 
@@ -230,7 +231,7 @@ def run_ours(args, rank, world, local):
     prec = {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[args.precision]
     bsz = args.batch
     from paper_1707_08874_gb300 import autotune
-    panel = autotune.tune_panel(NS, NT, bsz, prec, use_cache=False)
+    panel = args.panel or autotune.tune_panel(NS, NT, bsz, prec, use_cache=False)
     plan = B.Plan.analyze_ex(NS, NT, bsz, prec, panel)
     info = plan.info
     U = inputs.random_links(NS, NT, seed=replica_seed(rank, bsz), batch=bsz)

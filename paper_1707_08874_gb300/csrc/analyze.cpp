@@ -518,10 +518,12 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
           it += e.items;
           // this precision tiles the GEMMs by kEmuTileM rows
           g.blk0 = blk;
-          g.tilesN = e.Np / 32;
+          g.tilesN = e.Np / 16;  // 16 complex columns per CTA
           blk += (e.Mp / kEmuTileM) * g.tilesN;
         }
         op.blocks = blk;
+        op.single_chunk = true;
+        for (int d = op.d0; d < op.d1; ++d) op.single_chunk &= p.emu[d].Kp == 32;  // one exponent chunk
         max_w[op.stream] = std::max(max_w[op.stream], w);
         max_in[op.stream] = std::max(max_in[op.stream], in);
       }

@@ -65,6 +65,7 @@ size_t elem_bytes(const Plan& p) { return p.precision == CL_MIXED_FP32 ? sizeof(
 
 int setup_device(Plan& p) {
   cudaGetDevice(&p.device);
+  if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) != cudaSuccess) return CL_ERR_CUDA;
   size_t total = 0;
   cudaError_t e;
   const size_t arena = (size_t)p.arena_elems * p.batch * elem_bytes(p);

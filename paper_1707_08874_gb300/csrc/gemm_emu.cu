@@ -1,22 +1,31 @@
 // FP64-accurate complex GEMM on the BF16 tensor cores (precision CL_FP64_EMU).
 //
-// GB300's FP64 pipe delivers ~1.1 TFLOP/s, its BF16 tensor pipe ~590 TFLOP/s
-// through mma.sync.  Each FP64 operand is written exactly as
+// GB300's FP64 pipe delivers ~1.1 TFLOP/s; its BF16 tensor cores, driven by
+// tcgen05, two orders of magnitude more.  Each FP64 operand is written exactly
+// as
 //   a = sign * 2^e * sum_{p=1..7} d_p 2^{-8p} + (truncation < 2^{e-56}),
 // with integer digits 0 <= d_p <= 255 (exact in BF16) and one exponent e per
 // row (A) or column (B) and per chunk of 32 complex k.  The product is the sum
-// over digit pairs p + q <= 8 (28 BF16 products) of integer dot products: each
-// one is exact in the FP32 accumulator for the leading levels (sums < 2^24) and
-// rounded below FP64 resolution for the others.  Level sums are scaled by
-// powers of two and accumulated across chunks in triple-float (three FP32
-// words, error-free two-sums), relative to the largest row / column exponent;
-// FP64 arithmetic appears only in the epilogue (two additions per output).  Accuracy equals an FP64 GEMM
-// to within a small factor (numpy emulation of the same digits and roundings:
-// normwise relative error 4e-16 - 1.1e-15 against 5e-16 - 1e-15 for FP64).
+// over digit pairs p + q <= 6 (0-based: 28 BF16 products, 7 levels p + q) of
+// integer dot products: exact in the FP32 accumulator for the leading levels
+// (sums < 2^24) and rounded below FP64 resolution for the others.  Level sums
+// are scaled by powers of two and accumulated across chunks in triple-float
+// (three FP32 words, error-free two-sums), relative to the largest row /
+// column exponent; FP64 arithmetic appears only in the epilogue (two
+// additions per output).  Accuracy equals an FP64 GEMM to within a small
+// factor (numpy emulation of the same digits and roundings: normwise relative
+// error 4e-16 - 1.1e-15 against 5e-16 - 1e-15 for FP64).
 //
-// Complex products are one real product of twice the size, as in the FP64
-// kernel: A is the real M x 2K matrix of interleaved pairs; B is expanded into
-// [[br, bi], [-bi, br]] blocks when its fragment is loaded from shared memory.
+// Complex products are one real product of twice the size: A is the real
+// M x 2K matrix of interleaved (re, im) pairs, B is expanded into the real
+// 2K x 2N matrix of [[br, bi], [-bi, br]] blocks by the split pass.
+//
+// Two kernels per GEMM launch:
+//   k_emu_split    digits and exponents of A and B, written as tiles in the
+//                  order the tensor core reads shared memory;
+//   k_gemm_emu_tc  the digit products as tcgen05 MMAs with FP32 accumulators
+//                  in tensor memory, the fold and the FP64 epilogue.
+#include <algorithm>
 #include <cstring>
 
 #include "kernels.cuh"
@@ -24,10 +33,10 @@
 namespace cl {
 namespace {
 
-constexpr int kDig = 7;       // base-256 digits per operand
-constexpr int kLevels = 7;    // digit pairs p + q <= 6 (0-based) -> 28 products
-constexpr int kChunk = 32;    // complex k per exponent chunk (64 real k)
-constexpr int kStrideW = 36;  // shared-memory row stride in 32-bit words (32 + 4 pad)
+constexpr int kDig = 7;      // base-256 digits per operand
+constexpr int kLevels = 7;   // digit pairs p + q <= 6 (0-based) -> 28 products
+constexpr int kChunk = 32;   // complex k per exponent chunk (64 real k)
+constexpr int kTileCx = 16;  // complex columns of C per CTA (32 real columns of B')
 
 __device__ __forceinline__ int exp_of(double v) {
   const long long b = __double_as_longlong(v);
@@ -54,31 +63,38 @@ __device__ __forceinline__ void digits(double v, int e, unsigned short (&d)[kDig
   }
 }
 
-// Split pass: one warp per item.  A items (row, chunk): lanes take the 32
-// complex k of the chunk; digits go to A[p][row][k] as (re, im) BF16 pairs.
-// B items (column n, chunk): lanes take the chunk's 32 k; the real embedding
-// of b = br + i bi is written directly, k-contiguous, as two rows of B'^T:
-//   row 2n   : (br, -bi)   (real column 2n of [[br, bi], [-bi, br]] per k)
-//   row 2n+1 : (bi,  br)
-// so the GEMM loads both operands with ldmatrix and no per-element work.
-// Padding (rows >= M, columns >= N, k >= K) gets zero digits.
-// Tiled layout (tensor-core path): every (digit, 128-row block, chunk) of A
-// and every (digit, 64-real-column block, chunk) of B' is one contiguous tile
-// in the order the tensor core reads shared memory without swizzling: 16-k
-// slabs, inside a slab 8-row groups of two 8 x 8 core matrices (k 0-7, 8-15),
-// each core matrix 8 rows of 16 bytes.  A tile is then one bulk copy.
+// Digit tiles, laid out for the tensor core's no-swizzle K-major operand
+// format: 16-k slabs; inside a slab, 8-row groups of two 8 x 8 core matrices
+// (k 0-7, 8-15), each core matrix 8 rows of 16 bytes (256 bytes per group).
+//   A: per (128-row block, chunk) one 112 KB block [digit p][slab][16 groups]
+//      (4096 words per digit).
+//   B': per (32-real-column block, chunk) one 28 KB block [slab][digit q][4
+//      groups] (1792 words per slab): in a slab the seven digits' rows follow
+//      one another at the uniform 256-byte group stride, so one MMA of width
+//      N = 32 (7 - p) multiplies A digit p by B' digits q = 0 .. 6 - p at once.
+// Word (two BF16: re / im of one complex k) of A row `row`, lane = complex k
+// in the chunk:
 __device__ __forceinline__ int64_t a_tile_word(const EmuDesc& e, int nch, int p, int row, int c, int lane) {
-  const int64_t tile = ((int64_t)p * (e.Mp / 128) + row / 128) * nch + c;
+  const int64_t blk = (int64_t)(row / 128) * nch + c;
   const int r = row & 127;
-  return e.adig + tile * 4096 + (lane >> 3) * 1024 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 + (lane & 3);
+  return e.adig + (blk * kDig + p) * 4096 + (lane >> 3) * 1024 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 +
+         (lane & 3);
 }
+// ... and of B' row (real column of the embedding) `nreal`:
 __device__ __forceinline__ int64_t b_tile_word(const EmuDesc& e, int nch, int q, int nreal, int c, int lane) {
-  const int64_t tile = ((int64_t)q * (e.Np / 32) + nreal / 64) * nch + c;
-  const int r = nreal & 63;
-  return e.bdig + tile * 2048 + (lane >> 3) * 512 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 + (lane & 3);
+  const int64_t blk = (int64_t)(nreal / 32) * nch + c;
+  const int r = nreal & 31;
+  return e.bdig + blk * 7168 + (lane >> 3) * 1792 + q * 256 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 +
+         (lane & 3);
 }
 
-template <bool kTiled>
+// Split pass: one warp per item.  A items (row, chunk): lanes take the 32
+// complex k of the chunk and write (re, im) digit pairs.  B items (complex
+// column n, chunk): lanes take the chunk's 32 k; the real embedding of
+// b = br + i bi is written directly as two rows of B'^T:
+//   row 2n   : (br, -bi)   (real column 2n of [[br, bi], [-bi, br]] per k)
+//   row 2n+1 : (bi,  br)
+// Padding (rows >= M, columns >= N, k >= K) gets zero digits.
 __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
                                                    int d0, int d1, const double2* __restrict__ arena,
                                                    int64_t stride, unsigned* __restrict__ words,
@@ -118,47 +134,18 @@ __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ 
   unsigned short dr[kDig], di[kDig];
   digits(v.x, ee, dr);
   digits(v.y, ee, di);
-  if (kTiled) {
-    if (isA) {
-      if (lane == 0) I[e.aexp + (int64_t)c * e.Mp + line] = ee;
-#pragma unroll
-      for (int p = 0; p < kDig; ++p) W[a_tile_word(e, nch, p, line, c, lane)] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
-    } else {
-      if (lane == 0) I[e.bexp + (int64_t)c * e.Np + line] = ee;
-#pragma unroll
-      for (int p = 0; p < kDig; ++p) {
-        W[b_tile_word(e, nch, p, 2 * line, c, lane)] =
-            (unsigned)dr[p] | ((unsigned)(di[p] ^ (di[p] ? 0x8000u : 0u)) << 16);
-        W[b_tile_word(e, nch, p, 2 * line + 1, c, lane)] = (unsigned)di[p] | ((unsigned)dr[p] << 16);
-      }
-    }
-    return;
-  }
   if (isA) {
     if (lane == 0) I[e.aexp + (int64_t)c * e.Mp + line] = ee;
-    unsigned* dst = W + e.adig + (int64_t)line * e.Kp + k;
 #pragma unroll
-    for (int p = 0; p < kDig; ++p) dst[(int64_t)p * e.Mp * e.Kp] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
+    for (int p = 0; p < kDig; ++p) W[a_tile_word(e, nch, p, line, c, lane)] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
   } else {
     if (lane == 0) I[e.bexp + (int64_t)c * e.Np + line] = ee;
-    unsigned* dst0 = W + e.bdig + (int64_t)(2 * line) * e.Kp + k;
-    unsigned* dst1 = dst0 + e.Kp;
-    const int64_t plane = (int64_t)2 * e.Np * e.Kp;
 #pragma unroll
     for (int p = 0; p < kDig; ++p) {
-      dst0[p * plane] = (unsigned)dr[p] | ((unsigned)(di[p] ^ (di[p] ? 0x8000u : 0u)) << 16);
-      dst1[p * plane] = (unsigned)di[p] | ((unsigned)dr[p] << 16);
+      W[b_tile_word(e, nch, p, 2 * line, c, lane)] = (unsigned)dr[p] | ((unsigned)(di[p] ^ (di[p] ? 0x8000u : 0u)) << 16);
+      W[b_tile_word(e, nch, p, 2 * line + 1, c, lane)] = (unsigned)di[p] | ((unsigned)dr[p] << 16);
     }
   }
-}
-
-__device__ __forceinline__ void bmma(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                     unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
@@ -183,215 +170,29 @@ __device__ __forceinline__ double f2d_scaled(float f, int ex, bool neg) {
                                           ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
-__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
-}
-
-__device__ __forceinline__ void ldsm4(unsigned (&r)[4], const unsigned* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-constexpr int kEmuTM = 128;                        // rows per CTA
-constexpr int kSmemA = kDig * kEmuTM * kStrideW;   // words
-constexpr int kSmemB = kDig * 64 * kStrideW;       // 64 real columns (32 complex)
-constexpr size_t kEmuSmemBytes = (size_t)(kSmemA + kSmemB) * 4 + (kEmuTM + 32) * 2 * sizeof(int);
-
-// 256 threads = 4 x 2 warps; each warp owns 32 rows x 32 real columns
-// (2 x 4 MMA tiles of 16 x 8); CTA tile 128 rows x 32 complex columns.
-__global__ void __launch_bounds__(256, 1) k_gemm_emu(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
-                                                     int d0, int d1, double2* __restrict__ arena, int64_t stride,
-                                                     const unsigned* __restrict__ words, const int* __restrict__ ints,
-                                                     int64_t wstride, int64_t istride) {
-  extern __shared__ __align__(16) unsigned smem[];
-  unsigned* As = smem;
-  unsigned* Bs = smem + kSmemA;
-  int* rsc = reinterpret_cast<int*>(Bs + kSmemB);  // [128] chunk exponent minus the row maximum
-  int* csc = rsc + kEmuTM;                         // [32]  same for the complex columns
-  int* Rm = csc + 32;                              // [128] row maxima
-  int* Sm = Rm + kEmuTM;                           // [32]  column maxima
-
-  const int di = find_desc(gd, d0, d1, blockIdx.x);
-  const GemmDesc g = gd[di];
-  const EmuDesc e = ed[di];
-  const int t = blockIdx.x - g.blk0;
-  const int row0 = (t / g.tilesN) * kEmuTM, col0 = (t % g.tilesN) * kTileN;
-  const unsigned* Wd = words + blockIdx.y * wstride;
-  const int* Id = ints + blockIdx.y * istride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gq = lane >> 2, tq = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 16;  // row / complex column offsets of the warp
-  const int nch = e.Kp / kChunk;
-
-  if (tid < kEmuTM) {
-    int m = -4000;
-    for (int c = 0; c < nch; ++c) m = max(m, Id[e.aexp + (int64_t)c * e.Mp + row0 + tid]);
-    Rm[tid] = m;
-  } else if (tid < kEmuTM + 32) {
-    int m = -4000;
-    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid - kEmuTM]);
-    Sm[tid - kEmuTM] = m;
-  }
-
-  float h[2][4][4], mi[2][4][4], lo[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) h[i][j][r] = mi[i][j][r] = lo[i][j][r] = 0.f;
-
-  // ldmatrix lane addressing: A rows (lane & 15), k half (lane >> 4);
-  // B' rows n_r = 8j + (lane & 7) + 8 ((lane >> 4) & 1), k half ((lane >> 3) & 1)
-  const int a_row = lane & 15, a_kw = (lane >> 4) * 4;
-  const int b_row = (lane & 7) + ((lane >> 4) & 1) * 8, b_kw = ((lane >> 3) & 1) * 4;
-
-  for (int c = 0; c < nch; ++c) {
-    for (int q = tid; q < kDig * kEmuTM * 8; q += 256) {
-      const int p = q / (kEmuTM * 8), r = (q / 8) % kEmuTM, piece = q % 8;
-      cp16(As + (p * kEmuTM + r) * kStrideW + piece * 4,
-           Wd + e.adig + (int64_t)p * e.Mp * e.Kp + (int64_t)(row0 + r) * e.Kp + c * kChunk + piece * 4);
-    }
-    for (int q = tid; q < kDig * 64 * 8; q += 256) {
-      const int p = q / (64 * 8), r = (q / 8) % 64, piece = q % 8;
-      cp16(Bs + (p * 64 + r) * kStrideW + piece * 4,
-           Wd + e.bdig + (int64_t)p * 2 * e.Np * e.Kp + (int64_t)(2 * col0 + r) * e.Kp + c * kChunk + piece * 4);
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-    __syncthreads();  // row / column maxima visible before the scale factors
-    if (tid < kEmuTM) rsc[tid] = Id[e.aexp + (int64_t)c * e.Mp + row0 + tid] - Rm[tid];
-    else if (tid < kEmuTM + 32) csc[tid - kEmuTM] = Id[e.bexp + (int64_t)c * e.Np + col0 + tid - kEmuTM] - Sm[tid - kEmuTM];
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncthreads();
-
-    float scl[2][4][2];  // 2^{(e_i - R_i) + (f_n - S_n) - 16} per owned (row pair, column)
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-          scl[i][j][rr] = pow2f(rsc[wm + 16 * i + gq + 8 * rr] + csc[wn + 4 * j + tq] - 16);
-
-#pragma unroll 1
-    for (int L = 0; L < kLevels; ++L) {
-      float acc[2][4][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-#pragma unroll 2
-      for (int p = 0; p <= L; ++p) {
-        const unsigned* Ap = As + (p * kEmuTM + wm + a_row) * kStrideW + a_kw;
-        const unsigned* Bq = Bs + ((L - p) * 64 + 2 * wn + b_row) * kStrideW + b_kw;
-#pragma unroll
-        for (int ks = 0; ks < kChunk / 8; ++ks) {
-          unsigned a[2][4], b[4][2];
-          ldsm4(a[0], Ap + ks * 8);
-          ldsm4(a[1], Ap + 16 * kStrideW + ks * 8);
-          unsigned t4[4];
-          ldsm4(t4, Bq + ks * 8);
-          b[0][0] = t4[0]; b[0][1] = t4[1]; b[1][0] = t4[2]; b[1][1] = t4[3];
-          ldsm4(t4, Bq + 16 * kStrideW + ks * 8);
-          b[2][0] = t4[0]; b[2][1] = t4[1]; b[3][0] = t4[2]; b[3][1] = t4[3];
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bmma(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
-        }
-      }
-      // fold: levels 0, 1 into (h, mi, lo); levels >= 2 are below 2^-32 of the
-      // leading level and go straight into (mi, lo)
-      const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const float x = acc[i][j][r] * (scl[i][j][r >> 1] * cL);
-            float s, e1, s2, e2;
-            if (L < 2) {
-              two_sum(h[i][j][r], x, s, e1);
-              h[i][j][r] = s;
-              two_sum(mi[i][j][r], e1, s2, e2);
-            } else {
-              two_sum(mi[i][j][r], x, s2, e2);
-            }
-            mi[i][j][r] = s2;
-            lo[i][j][r] += e2;
-          }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          float s, e1, s2, e2;
-          two_sum(h[i][j][r], mi[i][j][r], s, e1);
-          two_sum(e1, lo[i][j][r], s2, e2);
-          h[i][j][r] = s;
-          mi[i][j][r] = s2;
-          lo[i][j][r] = e2;
-        }
-    __syncthreads();
-  }
-
-  // epilogue: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value.
-  // Two exact float -> double conversions by bit manipulation, then at most
-  // two FP64 additions per real output.
-  double2* C = arena + blockIdx.y * stride + g.c;
-  const bool neg = g.neg != 0;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int rl = wm + 16 * i + gq + rr * 8, cl = wn + 4 * j + tq;
-        const int r = row0 + rl, cc = col0 + cl;
-        if (r >= g.M || cc >= g.N) continue;
-        if (g.rmask.hit(r) || g.cmask.hit(cc)) continue;
-        const int ex = Rm[rl] + Sm[cl];
-        double vv[2];
-#pragma unroll
-        for (int part = 0; part < 2; ++part) {
-          const int q = 2 * rr + part;
-          float s, e1;
-          two_sum(h[i][j][q], mi[i][j][q], s, e1);
-          vv[part] = f2d_scaled(s, ex, neg) + f2d_scaled(e1 + lo[i][j][q], ex, neg);
-        }
-        double2 v = make_double2(vv[0], vv[1]);
-        double2* pc = C + (int64_t)r * g.ldc + cc;
-        if (g.beta) v = cadd(v, *pc);
-        *pc = v;
-      }
-}
-
 // ---------------------------------------------------------------------------
-// Tensor-core (tcgen05) digit GEMM.  Same digits, levels, fold and epilogue
-// as k_gemm_emu; the 28 digit products of a chunk are 112 asynchronous
-// 128 x 64 x 16 BF16 MMAs issued by one thread, accumulated in tensor memory
-// (one 64-column FP32 accumulator per level, 448 of the SM's 512 columns),
-// with operands brought into shared memory by bulk copies of the pre-tiled
-// digit planes.  CTA tile 128 rows x 32 complex columns, 256 threads: thread
-// (w, l) folds row 32 (w % 4) + l, real columns 32 (w / 4) .. + 31.
-// Every wait on an mbarrier gives up after a bounded time, records
-// CL_ERR_TIMEOUT and leaves through the normal teardown (TMEM freed).
-constexpr int kTcA = 4096 * 4;  // bytes of one A digit tile (128 rows x 64 real k)
-constexpr int kTcB = 2048 * 4;  // bytes of one B' digit tile (64 real columns x 64 real k)
-constexpr uint32_t kTcCols = 512;
-constexpr int kTcCtl = 2048;    // control block: mbarriers, TMEM address, exponents
-constexpr size_t kTcSmemBytes = (size_t)kDig * (kTcA + kTcB) + kTcCtl;
+// Digit GEMM on tcgen05.  CTA tile: 128 rows x 16 complex columns (32 real
+// columns of B'), 128 threads, two CTAs per SM so that one CTA's fold and
+// epilogue overlap the other's MMAs and copies.  Per chunk, in two halves of
+// 32 real k: bulk copies of the 7 A digit half-tiles and the B' half-block
+// into shared memory, then 14 asynchronous BF16 MMAs issued by one thread
+// (A digit p times B' digits 0 .. 6-p, 128 x 32(7-p) x 16) into seven
+// 32-column FP32 accumulators in tensor memory (one per level p + q; 224 of
+// the CTA's 256 columns).  The CTA's four warps then read the
+// levels back (thread = row) and fold them into triple-float.  Every wait on
+// an mbarrier gives up after a bounded time, records CL_ERR_TIMEOUT, waits
+// once more for what it had in flight and leaves through the normal teardown
+// (tensor memory freed).
+constexpr int kAHalf = 8192;     // bytes: 128 rows x 32 real k, BF16 (two 16-k slabs)
+constexpr int kBHalf = 2048;     // bytes per digit: 32 real columns x 32 real k
+constexpr uint32_t kTcCols = 256;
+constexpr int kTcCtl = 2048;     // control block: mbarriers, TMEM address, exponents
+constexpr size_t kTcSmemBytes = (size_t)kDig * (kAHalf + kBHalf) + kTcCtl;
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28;
+// M = 128, N = 32 (7 - p) for A digit p (a multiple of 16, <= 224)
+constexpr uint32_t kTcIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
+__host__ __device__ constexpr uint32_t tc_idesc(int p) { return kTcIdescBase | ((uint32_t)(4 * (kDig - p)) << 17); }
 constexpr unsigned long long kWaitNs = 500000000ull;  // 0.5 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -437,11 +238,12 @@ __device__ __forceinline__ unsigned long long umma_desc(uint32_t saddr) {
   return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | ((unsigned long long)(128 >> 4) << 16) |
          ((unsigned long long)(256 >> 4) << 32) | (1ull << 46);
 }
-__device__ __forceinline__ void umma_bf16(uint32_t dtmem, unsigned long long ad, unsigned long long bd, uint32_t acc) {
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, unsigned long long ad, unsigned long long bd, uint32_t idesc,
+                                          uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -454,33 +256,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(256, 1)
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 2)
     k_gemm_emu_tc(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1,
                   double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
                   const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_tc[];
-  unsigned char* sA = smem_tc;
-  unsigned char* sB = smem_tc + kDig * kTcA;
-  unsigned char* ctl = sB + kDig * kTcB;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);  // [0] operands landed, [1] MMAs done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 16);
-  int* abort_flag = reinterpret_cast<int*>(ctl + 20);
+  unsigned char* sA = smem_tc;                  // [7][kAHalf]
+  unsigned char* sB = smem_tc + kDig * kAHalf;  // [7][kBHalf]
+  unsigned char* ctl = sB + kDig * kBHalf;
+  // mbarriers: [0] operands landed, [1] MMAs of the first half done, [2] MMAs of the chunk done
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 32);
+  int* abort_flag = reinterpret_cast<int*>(ctl + 36);
   int* Rm = reinterpret_cast<int*>(ctl + 64);  // [128] row maxima of the chunk exponents
-  int* Sm = Rm + 128;                          // [32]  column maxima
-  int* rsc = Sm + 32;                          // [128] chunk exponent minus the row maximum
-  int* csc = rsc + 128;                        // [32]  same for the columns
+  int* Sm = Rm + 128;                          // [16]  column maxima
+  int* rsc = Sm + kTileCx;                     // [128] chunk exponent minus the row maximum
+  int* csc = rsc + 128;                        // [16]  same for the columns
 
   const int di = find_desc(gd, d0, d1, blockIdx.x);
   const GemmDesc g = gd[di];
   const EmuDesc e = ed[di];
   const int t = blockIdx.x - g.blk0;
   const int rb = t / g.tilesN, nb = t % g.tilesN;
-  const int row0 = rb * 128, col0 = nb * 32;
+  const int row0 = rb * 128, col0 = nb * kTileCx;
   const unsigned* Wd = words + blockIdx.y * wstride;
   const int* Id = ints + blockIdx.y * istride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int nch = e.Kp / kChunk;
-  const uint32_t s_full = smem_u32(&bars[0]), s_done = smem_u32(&bars[1]);
+  const uint32_t s_full = smem_u32(&bars[0]), s_h0 = smem_u32(&bars[1]), s_done = smem_u32(&bars[2]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -490,86 +301,119 @@ __global__ void __launch_bounds__(256, 1)
   }
   if (tid == 32) {
     mbar_init(s_full, 1);
+    mbar_init(s_h0, 1);
     mbar_init(s_done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < 128) {
+  {
     int m = -4000;
     for (int c = 0; c < nch; ++c) m = max(m, Id[e.aexp + (int64_t)c * e.Mp + row0 + tid]);
     Rm[tid] = m;
-  } else if (tid < 160) {
-    int m = -4000;
-    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid - 128]);
-    Sm[tid - 128] = m;
   }
+  if (tid < kTileCx) {
+    int m = -4000;
+    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid]);
+    Sm[tid] = m;
+  }
+  // exponents of the next chunk, loaded one chunk ahead
+  int ra = nch > 0 ? Id[e.aexp + row0 + tid] : 0;
+  int cb = (tid < kTileCx && nch > 0) ? Id[e.bexp + col0 + tid] : 0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  auto issue_copies = [&](int c) {
-    mbar_expect_tx(s_full, (unsigned)(kDig * (kTcA + kTcB)));
+  // bulk copies of half `hf` of chunk c (thread 0)
+  auto issue = [&](int c, int hf) {
+    mbar_expect_tx(s_full, (unsigned)(kDig * (kAHalf + kBHalf)));
+    const int64_t ablk = (int64_t)rb * nch + c, bblk = (int64_t)nb * nch + c;
 #pragma unroll 1
-    for (int p = 0; p < kDig; ++p) {
-      const unsigned* srcA = Wd + e.adig + (((int64_t)p * (e.Mp / 128) + rb) * nch + c) * 4096;
-      const unsigned* srcB = Wd + e.bdig + (((int64_t)p * (e.Np / 32) + nb) * nch + c) * 2048;
-      bulk_g2s(smem_u32(sA + p * kTcA), srcA, kTcA, s_full);
-      bulk_g2s(smem_u32(sB + p * kTcB), srcB, kTcB, s_full);
-    }
+    for (int p = 0; p < kDig; ++p)
+      bulk_g2s(smem_u32(sA + p * kAHalf), Wd + e.adig + (ablk * kDig + p) * 4096 + hf * 2048, kAHalf, s_full);
+    bulk_g2s(smem_u32(sB), Wd + e.bdig + bblk * 7168 + hf * 3584, kDig * kBHalf, s_full);
+  };
+  // the 14 MMAs of one half (thread 0): A digit p times B' digits 0 .. 6-p
+  // (N = 32 (7 - p)) into levels p .. 6 at TMEM columns 32 p ..
+  auto mmas = [&](int hf) {
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll 1
+    for (int p = 0; p < kDig; ++p)
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb)
+        umma_bf16(tmem + 32 * p, umma_desc(a0 + p * kAHalf + kb * 4096), umma_desc(b0 + kb * (kDig * 1024)),
+                  tc_idesc(p), (hf | p | kb) != 0 ? 1u : 0u);
   };
 
-  const int qd = warp & 3, hc = warp >> 2;
-  const int rl = qd * 32 + lane;  // tile row of this thread
   float h[32], mi[32], lo[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) h[i] = mi[i] = lo[i] = 0.f;
 
-  if (tid == 0 && nch > 0) issue_copies(0);  // K = 0: no operands, C = beta C
+  unsigned fph = 0;  // phase of the operands barrier (thread 0)
+  if (tid == 0 && nch > 0) issue(0, 0);  // K = 0: no operands, C = beta C
   bool ok = true;
 #pragma unroll 1
   for (int c = 0; c < nch; ++c) {
-    if (tid < 128) rsc[tid] = Id[e.aexp + (int64_t)c * e.Mp + row0 + tid] - Rm[tid];
-    else if (tid < 160) csc[tid - 128] = Id[e.bexp + (int64_t)c * e.Np + col0 + tid - 128] - Sm[tid - 128];
+    rsc[tid] = ra - Rm[tid];
+    if (tid < kTileCx) csc[tid] = cb - Sm[tid];
+    if (c + 1 < nch) {
+      ra = Id[e.aexp + (int64_t)(c + 1) * e.Mp + row0 + tid];
+      if (tid < kTileCx) cb = Id[e.bexp + (int64_t)(c + 1) * e.Np + col0 + tid];
+    }
     __syncthreads();
     if (tid == 0) {
-      if (mbar_wait(s_full, c & 1)) {
+      // stage that gave up: 1 first-half operands, 2 first-half MMAs, 3 second-half operands
+      int fail = 0;
+      if (!mbar_wait(s_full, fph)) {
+        fail = 1;
+        mbar_wait(s_full, fph);  // copies in flight: wait once more
+      }
+      fph ^= 1;
+      if (!fail) {
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-#pragma unroll 1
-        for (int L = 0; L < kLevels; ++L)
-#pragma unroll 1
-          for (int p = 0; p <= L; ++p)
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb)
-              umma_bf16(tmem + 64 * L, umma_desc(a0 + p * kTcA + kb * 4096),
-                        umma_desc(b0 + (L - p) * kTcB + kb * 2048), (p > 0 || kb > 0) ? 1u : 0u);
+        mmas(0);
+        umma_commit(s_h0);
+        if (!mbar_wait(s_h0, c & 1)) {
+          fail = 2;
+          mbar_wait(s_h0, c & 1);
+        }
+      }
+      if (!fail) {
+        issue(c, 1);  // the first half's operands are consumed
+        if (!mbar_wait(s_full, fph)) {
+          fail = 3;
+          mbar_wait(s_full, fph);
+        }
+        fph ^= 1;
+      }
+      if (!fail) {
+        tc_fence_after();
+        mmas(1);
         umma_commit(s_done);
       } else {
         *abort_flag = 1;
-        set_status(status, CL_ERR_TIMEOUT, -1, c);
-        mbar_wait(s_full, c & 1);  // copies still in flight: wait once more
-        mbar_arrive(s_done);       // no MMA issued: release the other threads
+        set_status(status, CL_ERR_TIMEOUT, -fail, c);
+        mbar_arrive(s_done);  // no second-half MMAs: release the other threads
       }
     }
     const bool got = mbar_wait(s_done, c & 1);
     tc_fence_after();
-    if (!got) set_status(status, CL_ERR_TIMEOUT, -2, c);
+    if (!got) set_status(status, CL_ERR_TIMEOUT, -4, c);
     if (__syncthreads_or(!got || *abort_flag)) {
       ok = false;
       if (tid == 0 && !*abort_flag) mbar_wait(s_done, c & 1);  // MMAs may still run: wait once more
       break;
     }
-    if (tid == 0 && c + 1 < nch) issue_copies(c + 1);  // operands of chunk c consumed
+    if (tid == 0 && c + 1 < nch) issue(c + 1, 0);  // overlaps the fold below
 
-    float sc[16];  // 2^{(e_i - R_i) + (f_n - S_n) - 16} for this row and the 16 complex columns
-    const int rs = rsc[rl] - 16;
+    float sc[kTileCx];  // 2^{(e_i - R_i) + (f_n - S_n) - 16} for this row and the 16 complex columns
+    const int rs = rsc[tid] - 16;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sc[j] = pow2f(rs + csc[hc * 16 + j]);
+    for (int j = 0; j < kTileCx; ++j) sc[j] = pow2f(rs + csc[j]);
 #pragma unroll 1
     for (int L = 0; L < kLevels; ++L) {
       uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + 64 * L + 32 * hc, v);
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * L, v);
       const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
@@ -606,15 +450,22 @@ __global__ void __launch_bounds__(256, 1)
   }
   if (!ok) return;
 
-  double2* C = arena + blockIdx.y * stride + g.c;
-  const bool neg = g.neg != 0;
-  const int r = row0 + rl;
+  // epilogue: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value.  The
+  // C row segment is loaded first (16 independent loads), then written.
+  const int r = row0 + tid;
   if (r >= g.M || g.rmask.hit(r)) return;
+  double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)r * g.ldc + col0;
+  const bool neg = g.neg != 0;
+  double2 cv[kTileCx];
+  if (g.beta) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int cl = hc * 16 + j, cc = col0 + cl;
+    for (int j = 0; j < kTileCx; ++j) cv[j] = col0 + j < g.N ? crow[j] : make_double2(0, 0);
+  }
+#pragma unroll
+  for (int j = 0; j < kTileCx; ++j) {
+    const int cc = col0 + j;
     if (cc >= g.N || g.cmask.hit(cc)) continue;
-    const int ex = Rm[rl] + Sm[cl];
+    const int ex = Rm[tid] + Sm[j];
     double vv[2];
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
@@ -624,36 +475,315 @@ __global__ void __launch_bounds__(256, 1)
       vv[part] = f2d_scaled(s, ex, neg) + f2d_scaled(e1 + lo[q], ex, neg);
     }
     double2 v = make_double2(vv[0], vv[1]);
-    double2* pc = C + (int64_t)r * g.ldc + cc;
-    if (g.beta) v = cadd(v, *pc);
-    *pc = v;
+    if (g.beta) v = cadd(v, cv[j]);
+    crow[j] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent digit GEMM for launches whose problems all have K <= 32 (one
+// exponent chunk: the sweep updates of the factorisation and the panel
+// products).  One CTA per SM takes a contiguous range of output tiles (128
+// rows x 16 complex columns) of the launch; warp-specialised, 192 threads:
+//   warp 0 lane 0  producer: bulk copies of the current row block's A digits
+//                  (112 KB, kept while consecutive tiles share the block) and
+//                  of each tile's B' digits into a two-stage ring (28 KB);
+//   warp 1 lane 0  MMA issuer: per tile 28 tcgen05 MMAs (per A digit p and
+//                  16-k slab, one 128 x 32(7-p) x 16 product with B' digits
+//                  0 .. 6-p) into one of two accumulator sets in tensor memory
+//                  (7 levels x 32 columns at TMEM columns 0 and 256), so the
+//                  MMAs of tile i+1 run while tile i is folded and written;
+//   warps 2-9      fold (thread = row) and FP64 epilogue in two groups of four
+//                  warps taking alternate tiles (accumulator set = tile
+//                  parity), so one group's FP32 fold overlaps the other's
+//                  FP64 write-back; the C row segment is prefetched into L1.
+// With one chunk the row / column exponents are the chunk's own, the fold
+// scale is 2^{-16-8L} and the output exponent e_row + f_col.
+constexpr int kPA = 16384;  // bytes: one A digit tile, 128 rows x 64 real k
+constexpr int kPB = 4096;   // bytes: one B' digit tile, 32 real columns x 64 real k
+constexpr int kPCtl = 1024;
+constexpr size_t kPSmemBytes = (size_t)kDig * kPA + 2 * (size_t)kDig * kPB + kPCtl;
+constexpr uint32_t kPCols = 512;
+
+// tile t of the launch -> problem, row block and 16-column tile
+struct TileRef {
+  int di, rb, j;
+};
+__device__ __forceinline__ TileRef tile_ref(const GemmDesc* __restrict__ gd, int d0, int d1, int t) {
+  TileRef r;
+  r.di = find_desc(gd, d0, d1, t);
+  const int rel = t - gd[r.di].blk0, tn = gd[r.di].tilesN;
+  r.rb = rel / tn;
+  r.j = rel - r.rb * tn;
+  return r;
+}
+
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, unsigned parity, const volatile int* abort_flag) {
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\tselp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort_flag || gtimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__global__ void __launch_bounds__(320, 1)
+    k_gemm_emu_persist(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
+                       double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
+                       const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_p[];
+  unsigned char* sA = smem_p;                   // [7][kPA]
+  unsigned char* sB = smem_p + kDig * kPA;      // [2 stages][7][kPB]
+  unsigned char* ctl = sB + 2 * kDig * kPB;
+  // mbarriers: [0] A landed, [1,2] B stage landed, [3,4] B stage consumed,
+  //            [5,6] accumulator set full, [7,8] accumulator set drained
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 96);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 100);
+  const uint32_t bar0 = smem_u32(bars);
+  auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
+  const uint32_t b_afull = bar0;
+
+  const int G = gridDim.x;
+  const int t0 = (int)((int64_t)total * blockIdx.x / G), t1 = (int)((int64_t)total * (blockIdx.x + 1) / G);
+  const int n = t1 - t0;
+  const unsigned* Wd = words + blockIdx.y * wstride;
+  const int* Id = ints + blockIdx.y * istride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kPCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int i = 0; i < 7; ++i) mbar_init(bar(i), 1);
+    mbar_init(bar(7), 128);  // one 4-warp epilogue group per accumulator set
+    mbar_init(bar(8), 128);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- producer
+      int prev = -1, issued = 0, a_loads = 0;
+      bool good = true;
+      for (int i = 0; i < n && good && !*abort_flag; ++i) {
+        const TileRef tr = tile_ref(gd, d0, d1, t0 + i);
+        const EmuDesc& e = ed[tr.di];
+        const int key = tr.di * 65536 + tr.rb;
+        if (key != prev) {
+          // the MMAs of the previous tile read the old A block: wait for them
+          if (i > 0 && !mbar_wait_ab(bar(3 + ((i - 1) & 1)), ((i - 1) >> 1) & 1, abort_flag)) {
+            good = false;
+            break;
+          }
+          mbar_expect_tx(b_afull, (unsigned)(kDig * kPA));
+          for (int p = 0; p < kDig; ++p)
+            bulk_g2s(smem_u32(sA + p * kPA), Wd + e.adig + ((int64_t)tr.rb * kDig + p) * 4096, kPA, b_afull);
+          ++a_loads;
+          prev = key;
+        }
+        const int s = i & 1, u = i >> 1;
+        if (i >= 2 && !mbar_wait_ab(bar(3 + s), (u - 1) & 1, abort_flag)) {
+          good = false;
+          break;
+        }
+        mbar_expect_tx(bar(1 + s), (unsigned)(kDig * kPB));
+        bulk_g2s(smem_u32(sB + s * kDig * kPB), Wd + e.bdig + (int64_t)tr.j * 7168, kDig * kPB, bar(1 + s));
+        issued = i + 1;
+      }
+      if (!good) {
+        *abort_flag = 1;
+        set_status(status, CL_ERR_TIMEOUT, -5, t0);
+      }
+      if (*abort_flag) {  // copies still in flight: the last two stages and the A block, bounded
+        for (int i = max(0, issued - 2); i < issued; ++i) mbar_wait(bar(1 + (i & 1)), (i >> 1) & 1);
+        if (a_loads > 0) mbar_wait(b_afull, (a_loads - 1) & 1);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      int prev = -1, a_use = 0, last = -1;
+      bool good = true;
+      const uint32_t a0 = smem_u32(sA);
+      for (int i = 0; i < n && good && !*abort_flag; ++i) {
+        const TileRef tr = tile_ref(gd, d0, d1, t0 + i);
+        const int key = tr.di * 65536 + tr.rb;
+        if (key != prev) {
+          if (!mbar_wait_ab(b_afull, a_use & 1, abort_flag)) {
+            good = false;
+            break;
+          }
+          ++a_use;
+          prev = key;
+        }
+        const int s = i & 1, u = i >> 1;
+        if (!mbar_wait_ab(bar(1 + s), u & 1, abort_flag) ||
+            (i >= 2 && !mbar_wait_ab(bar(7 + s), (u - 1) & 1, abort_flag))) {
+          good = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(sB + s * kDig * kPB), d = tmem + 256u * s;
+#pragma unroll 1
+        for (int p = 0; p < kDig; ++p)
+#pragma unroll
+          for (int kb = 0; kb < 4; ++kb)
+            umma_bf16(d + 32 * p, umma_desc(a0 + p * kPA + kb * 4096), umma_desc(b0 + kb * (kDig * 1024)), tc_idesc(p),
+                      (p | kb) != 0 ? 1u : 0u);
+        umma_commit(bar(3 + s));
+        umma_commit(bar(5 + s));
+        last = i;
+      }
+      if (!good) {
+        *abort_flag = 1;
+        set_status(status, CL_ERR_TIMEOUT, -6, t0);
+      }
+      if (*abort_flag && last >= 0) mbar_wait(bar(5 + (last & 1)), (last >> 1) & 1);  // MMAs in flight
+    }
+    __syncwarp();
+  } else {  // ---- fold and epilogue: warps 2-5 take even tiles, 6-9 odd; thread = row
+    const int grp = (warp - 2) >> 2, q4 = warp & 3, rl = q4 * 32 + lane;
+    int prev = -1, erow = 0;
+    for (int i = grp; i < n; i += 2) {
+      __syncwarp();
+      if (__any_sync(0xffffffffu, *abort_flag)) break;
+      const TileRef tr = tile_ref(gd, d0, d1, t0 + i);
+      const GemmDesc g = gd[tr.di];
+      const int64_t bexp = ed[tr.di].bexp;
+      const int key = tr.di * 65536 + tr.rb;
+      if (key != prev) {
+        erow = Id[ed[tr.di].aexp + tr.rb * 128 + rl];
+        prev = key;
+      }
+      const int r = tr.rb * 128 + rl, col0 = tr.j * kTileCx;
+      const bool row_ok = r < g.M && !g.rmask.hit(r);
+      const bool neg = g.neg != 0;
+      double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)r * g.ldc + col0;
+      if (row_ok && g.beta) {  // C row segment (256 bytes) into L1 while the MMAs run
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow));
+        if (col0 + 8 < g.N) asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + 8));
+      }
+      const int s = i & 1, u = i >> 1;
+      const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (!*abort_flag) set_status(status, CL_ERR_TIMEOUT, -7, t0);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      // two halves of 8 complex columns (16 TMEM columns per level)
+#pragma unroll 1
+      for (int hh = 0; hh < 2; ++hh) {
+        float h[16], mi[16], lo[16];
+#pragma unroll 1
+        for (int L = 0; L < kLevels; ++L) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + 32 * L + 16 * hh, v);
+          const float sL = __int_as_float((127 - 16 - 8 * L) << 23);  // 2^{-16-8L}
+          if (L == 0) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              h[k] = __uint_as_float(v[k]) * sL;
+              mi[k] = lo[k] = 0.f;
+            }
+          } else if (L == 1) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) two_sum(h[k], __uint_as_float(v[k]) * sL, h[k], mi[k]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              float s2, e2;
+              two_sum(mi[k], __uint_as_float(v[k]) * sL, s2, e2);
+              mi[k] = s2;
+              lo[k] += e2;
+            }
+          }
+        }
+        if (hh == 1) {
+          tc_fence_before();
+          mbar_arrive(bar(7 + s));  // accumulator set s may be overwritten
+        }
+        if (!row_ok) continue;
+        const int c8 = col0 + 8 * hh;
+        int fe[8];
+        {
+          const int4* fp = reinterpret_cast<const int4*>(Id + bexp + c8);
+          const int4 x0 = fp[0], x1 = fp[1];
+          fe[0] = x0.x, fe[1] = x0.y, fe[2] = x0.z, fe[3] = x0.w;
+          fe[4] = x1.x, fe[5] = x1.y, fe[6] = x1.z, fe[7] = x1.w;
+        }
+        double2 cv[8];  // C row segment: all loads issued before any store
+        if (g.beta) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[8 * hh + jj] : make_double2(0, 0);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int cc = c8 + jj;
+          if (cc >= g.N || g.cmask.hit(cc)) continue;
+          const int ex = erow + fe[jj];
+          double vv[2];
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            const int k = 2 * jj + part;
+            float s1, e1;
+            two_sum(h[k], mi[k], s1, e1);
+            vv[part] = f2d_scaled(s1, ex, neg) + f2d_scaled(e1 + lo[k], ex, neg);
+          }
+          double2 v = make_double2(vv[0], vv[1]);
+          if (g.beta) v = cadd(v, cv[jj]);
+          crow[8 * hh + jj] = v;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPCols) : "memory");
   }
 }
 
 }  // namespace
 
-size_t emu_smem_bytes() { return kEmuSmemBytes; }
-
 // opt the GEMM kernel in to > 48 KB of dynamic shared memory on the current
 // device (done when a plan is set up, outside any stream capture)
 cudaError_t emu_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmuSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm_emu_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+  return cudaFuncSetAttribute(k_gemm_emu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
 }
 
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool tc, cudaStream_t st) {
+                       int* status, bool single_chunk, int num_sms, cudaStream_t st) {
   const dim3 gs((unsigned)((items + 7) / 8), (unsigned)batch);
-  const dim3 gg((unsigned)blocks, (unsigned)batch);
-  if (tc) {
-    k_emu_split<true><<<gs, 256, 0, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride, items);
-    k_gemm_emu_tc<<<gg, 256, kTcSmemBytes, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride,
-                                                 status);
+  k_emu_split<<<gs, 256, 0, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride, items);
+  if (single_chunk) {
+    // blocks = output tiles of the launch; one persistent CTA per SM
+    const dim3 gp((unsigned)std::min(blocks, std::max(num_sms, 1)), (unsigned)batch);
+    k_gemm_emu_persist<<<gp, 320, kPSmemBytes, st>>>(gd, ed, d0, d1, blocks, arena, stride, words, ints, wstride,
+                                                     istride, status);
   } else {
-    k_emu_split<false><<<gs, 256, 0, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride, items);
-    k_gemm_emu<<<gg, 256, kEmuSmemBytes, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride);
+    const dim3 gg((unsigned)blocks, (unsigned)batch);
+    k_gemm_emu_tc<<<gg, 128, kTcSmemBytes, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride,
+                                                 status);
   }
   return cudaGetLastError();
 }
@@ -661,7 +791,8 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
   const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
   return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.batch, arena, p.arena_elems,
-                    p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, p.emu_tc, st);
+                    p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, p.num_sms,
+                    st);
 }
 
 }  // namespace cl
@@ -693,7 +824,7 @@ bool zgemm_layout(int M, int N, int K, ZgemmLayout& z) {
   const int64_t ints = e.bexp + nch * e.Np;
   e.it0 = 0;
   e.items = (int)(e.Mp * nch + e.Np * nch);
-  z.blocks = (e.Mp / 128) * (e.Np / 32);
+  z.blocks = (e.Mp / 128) * (e.Np / 16);
   z.desc_off = 0;
   z.words_off = 1024;
   z.ints_off = z.words_off + (size_t)words * 4;
@@ -731,12 +862,14 @@ extern "C" int cl_zgemm_emu(int M, int N, int K, const double* A, int lda, const
   z.g.neg = neg ? 1 : 0;
   z.g.beta = beta ? 1 : 0;
   z.g.blk0 = 0;
-  z.g.tilesN = z.e.Np / 32;
-  static thread_local int prepared_dev = -1;
+  z.g.tilesN = z.e.Np / 16;
+  static thread_local int prepared_dev = -1, sms = 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CL_ERR_CUDA;
   if (prepared_dev != dev) {
-    if (cl::emu_prepare() != cudaSuccess) return CL_ERR_CUDA;
+    if (cl::emu_prepare() != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return CL_ERR_CUDA;
     prepared_dev = dev;
   }
   unsigned char* wb = static_cast<unsigned char*>(work);
@@ -749,6 +882,6 @@ extern "C" int cl_zgemm_emu(int M, int N, int K, const double* A, int lda, const
   e = cl::launch_emu(reinterpret_cast<const cl::GemmDesc*>(wb), reinterpret_cast<const cl::EmuDesc*>(wb + 128), 0, 1,
                      z.e.items, z.blocks, 1, reinterpret_cast<double2*>(const_cast<double*>(A)), 0,
                      reinterpret_cast<unsigned*>(wb + z.words_off), reinterpret_cast<int*>(wb + z.ints_off), 0, 0,
-                     status, true, stream);
+                     status, z.e.Kp == 32, sms, stream);
   return e == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }

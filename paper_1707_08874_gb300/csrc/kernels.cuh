@@ -17,10 +17,12 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t
 // FP64-accurate GEMM on the BF16 tensor cores (split pass + digit GEMM)
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 cudaError_t emu_prepare();
-// split pass + digit GEMM over descriptors [d0, d1) (tc: tcgen05 kernel and tiled digit layout)
+// split pass + tcgen05 digit GEMM over descriptors [d0, d1); blocks = output
+// tiles (128 x 16 complex); single_chunk (every K <= 32): persistent kernel
+// on min(blocks, num_sms) CTAs
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool tc, cudaStream_t st);
+                       int* status, bool single_chunk, int num_sms, cudaStream_t st);
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

@@ -86,16 +86,17 @@ struct GatherDesc {
 };
 
 // Split-digit workspace of one GEMM problem in the FP64-emulation path
-// (CL_FP64_EMU): digit planes of A ([7][Mp][Kp] words) and of the real
-// embedding of B, transposed ([7][2 Np][Kp] words); chunk exponents
-// ([Kp/32][Mp] and [Kp/32][Np] ints); padded sizes.  CTA tiles are
-// kEmuTileM rows x kTileN complex columns.
+// (CL_FP64_EMU): digit tiles of A (7 x Mp x Kp words) and of the real
+// embedding of B, transposed (7 x 2 Np x Kp words); chunk exponents
+// ([Kp/32][Mp] and [Kp/32][Np] ints); padded sizes.  Output tiles are
+// 128 rows x 16 complex columns.
 struct EmuDesc {
   int64_t adig, bdig;  // word offsets in the replica's word workspace
   int64_t aexp, bexp;  // int offsets in the replica's int workspace
   int Mp, Np, Kp;      // Mp % 128 == 0, Np % 32 == 0, Kp % 32 == 0 (complex)
   int it0, items;      // split-pass warp items of this problem inside its launch
 };
+
 
 enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT };
 
@@ -113,6 +114,7 @@ struct Op {
   int stream = 0;
   int wait = -1;
   bool signal = false;
+  bool single_chunk = false;  // CL_FP64_EMU GEMM with every K <= 32: persistent kernel
 };
 
 struct Plan {
@@ -120,6 +122,7 @@ struct Plan {
   int panel = kPanelFP64;
   bool has_device = false;
   int device = 0;
+  int num_sms = 0;            // multiprocessors of the device (set up with the device state)
   std::vector<SNode> nodes;   // postorder, root last
   int n_levels = 0;
   double factor_flops = 0, selinv_flops = 0;
@@ -137,7 +140,6 @@ struct Plan {
   std::vector<GatherDesc> gather;
   std::vector<EmuDesc> emu;                         // parallel to gemm (CL_FP64_EMU only)
   int64_t emu_words = 0, emu_ints = 0;              // workspace per replica
-  bool emu_tc = true;                               // tcgen05 digit GEMM (false: mma.sync)
   std::vector<Op> factor_ops, selinv_ops;
   // device memory
   void* d_arena = nullptr;       // batch * arena_elems complex (precision-dependent)

@@ -44,7 +44,7 @@ def _check(A, B, C0, got, beta, neg):
 
 
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 32, 32), (130, 33, 70), (257, 65, 1000), (64, 200, 24),
-                                   (300, 96, 31)])
+                                   (300, 96, 31), (2000, 700, 24), (24, 2112, 24)])
 def test_zgemm_emu_random(M, N, K):
     rng = np.random.default_rng(M * 1000003 + N * 101 + K)
     A, B = _rand(rng, M, K), _rand(rng, K, N)
@@ -53,11 +53,13 @@ def test_zgemm_emu_random(M, N, K):
     _check(A, B, None, got.cpu().numpy(), False, False)
 
 
+@pytest.mark.parametrize("K", [48, 32])
 @pytest.mark.parametrize("beta,neg", [(1, 0), (1, 1), (0, 1)])
-def test_zgemm_emu_beta_neg_strided(beta, neg):
-    """C = beta C -/+ A B on sub-matrices of larger row-major arrays (lda > K)."""
-    rng = np.random.default_rng(7 + 2 * beta + neg)
-    M, N, K = 150, 40, 48
+def test_zgemm_emu_beta_neg_strided(beta, neg, K):
+    """C = beta C -/+ A B on sub-matrices of larger row-major arrays (lda > K);
+    K = 32 runs the persistent single-chunk kernel, K = 48 the chunked one."""
+    rng = np.random.default_rng(7 + 2 * beta + neg + K)
+    M, N = 150, 40
     Abig, Bbig, Cbig = _rand(rng, M, K + 9), _rand(rng, K, N + 5), _rand(rng, M, N + 3)
     tA, tB, tC = (torch.from_numpy(x).cuda() for x in (Abig, Bbig, Cbig))
     got, st = _B().zgemm_emu(tA[:, :K], tB[:, :N], tC[:, :N], beta=bool(beta), neg=bool(neg))
@@ -83,11 +85,12 @@ def test_zgemm_emu_dynamic_range():
     _check(A, B, None, got.cpu().numpy(), False, False)
 
 
-def test_zgemm_emu_exact_small_integers():
+@pytest.mark.parametrize("K", [90, 20])
+def test_zgemm_emu_exact_small_integers(K):
     """Gaussian integers below 2^8: every digit product is exact, so the
     result equals the exact integer product bit for bit."""
-    rng = np.random.default_rng(3)
-    M, N, K = 140, 36, 90
+    rng = np.random.default_rng(3 + K)
+    M, N = 140, 36
     A = rng.integers(-255, 256, (M, K)) + 1j * rng.integers(-255, 256, (M, K))
     B = rng.integers(-255, 256, (K, N)) + 1j * rng.integers(-255, 256, (K, N))
     got, st = _B().zgemm_emu(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
