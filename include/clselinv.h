@@ -145,6 +145,8 @@ int cl_analyze_ex(int Ns, int Nt, int batch, int precision, int panel, cl_plan**
  * cl_plan_get_node; compute calls on it return CL_ERR_INVALID_ARG.
  */
 int cl_analyze_symbolic(int Ns, int Nt, int precision, cl_plan** plan);
+/* cl_analyze_symbolic_ex -- the same with an explicit pivot-panel width (as cl_analyze_ex). */
+int cl_analyze_symbolic_ex(int Ns, int Nt, int precision, int panel, cl_plan** plan);
 
 /*
  * cl_factor -- numeric sparse LU of D(m;mu) (Sec. 3, first half of the
@@ -315,6 +317,24 @@ int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info);
  */
 int cl_plan_get_node(const cl_plan* plan, int i, int* parent, int* level, int* n_sep,
                      int* n_bnd, int* sep, int* bnd);
+
+/*
+ * cl_plan_check_schedule -- host-side race check of the factorisation's
+ * two-stream schedule (panel chain on one stream, bulk updates on the other,
+ * ordered only by the events the schedule names).  Replays the factor ops in
+ * list order with a vector clock per op and counts, element by element of the
+ * fronts and workspace, accesses from different streams that touch one
+ * element (at least one writing) without being ordered.  Accesses are the
+ * entries that can change a result: GEMM operand rows / columns of unmasked
+ * outputs, unmasked copy entries, panel blocks, extend-add map entries.
+ *   ignore_waits  1: drop the cross-stream waits (the check then finds races)
+ *   conflicts     out: number of unordered conflicting accesses (0 = race-free)
+ *   first         out (may be NULL): description of the first one, first_len bytes
+ * Works on symbolic plans; needs ~12 bytes of host memory per arena element.
+ * Not part of the paper: a verification aid for the schedule.
+ */
+int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* conflicts, char* first,
+                           int first_len);
 
 /*
  * cl_profile_enable -- enable (1) or disable (0) per-launch timing: while

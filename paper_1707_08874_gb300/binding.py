@@ -77,7 +77,8 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
-           "cl_zgemm_emu_workspace", "cl_zgemm_emu"]
+           "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
+           "cl_analyze_symbolic_ex"]
 
 
 def lib_path() -> str:
@@ -98,6 +99,7 @@ def load(build_if_missing: bool = True):
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     L.cl_analyze.argtypes = [I, I, I, I, ctypes.POINTER(P)]
     L.cl_analyze_symbolic.argtypes = [I, I, I, ctypes.POINTER(P)]
+    L.cl_analyze_symbolic_ex.argtypes = [I, I, I, I, ctypes.POINTER(P)]
     L.cl_factor.argtypes = [P, P, D, D, P]
     L.cl_selinv_blocks.argtypes = [P, P, P, P, P]
     L.cl_fermion_drift.argtypes = [P, P, P, P, D, D, P, P]
@@ -124,6 +126,7 @@ def load(build_if_missing: bool = True):
     L.cl_group_destroy.argtypes = [P]
     L.cl_group_destroy.restype = None
     L.cl_zgemm_emu_workspace.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.cl_plan_check_schedule.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, I]
     L.cl_zgemm_emu.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, ctypes.c_size_t, P, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
@@ -226,9 +229,9 @@ class Plan:
         return cls(h, False)
 
     @classmethod
-    def analyze_symbolic(cls, Ns: int, Nt: int, precision: int = CL_FP64) -> "Plan":
+    def analyze_symbolic(cls, Ns: int, Nt: int, precision: int = CL_FP64, panel: int = 0) -> "Plan":
         h = ctypes.c_void_p()
-        _check(load().cl_analyze_symbolic(Ns, Nt, precision, ctypes.byref(h)), "cl_analyze_symbolic")
+        _check(load().cl_analyze_symbolic_ex(Ns, Nt, precision, panel, ctypes.byref(h)), "cl_analyze_symbolic_ex")
         return cls(h, True)
 
     def close(self):
@@ -247,6 +250,14 @@ class Plan:
         inf = PlanInfo()
         _check(load().cl_plan_get_info(self._h, ctypes.byref(inf)), "cl_plan_get_info")
         return inf.as_dict()
+
+    def check_schedule(self, ignore_waits: bool = False):
+        """Host race check of the two-stream factor schedule: (conflicts, first)."""
+        n = ctypes.c_longlong()
+        buf = ctypes.create_string_buffer(256)
+        _check(load().cl_plan_check_schedule(self._h, int(ignore_waits), ctypes.byref(n), buf, 256),
+               "cl_plan_check_schedule")
+        return n.value, buf.value.decode()
 
     def node(self, i: int) -> dict:
         L = load()

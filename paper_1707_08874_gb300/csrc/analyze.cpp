@@ -395,8 +395,11 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       st.blocks = blks;
       ec.d1 = (int)p.copies.size();
       ec.blocks = blke;
+      int strips_idx = -1;
       if (st.d1 > st.d0) {
         st.wait = last_copy;  // the previous bulk update and write-back touched these strips
+        st.signal = true;
+        strips_idx = (int)p.factor_ops.size();
         p.factor_ops.push_back(st);
         p.factor_ops.push_back(ec);
       }
@@ -424,6 +427,8 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       cp.blocks = blk3;
       cp.stream = 1;
       cp.signal = true;
+      // the column strip reads the old column panel that this write-back replaces
+      if (strips_idx >= 0) cp.wait = strips_idx;
       p.factor_ops.push_back(g2);
       last_copy = (int)p.factor_ops.size();
       p.factor_ops.push_back(cp);

@@ -304,6 +304,10 @@ int cl_analyze_symbolic(int Ns, int Nt, int precision, cl_plan** plan) {
   return make_plan(Ns, Nt, 1, precision, 0, plan, false);
 }
 
+int cl_analyze_symbolic_ex(int Ns, int Nt, int precision, int panel, cl_plan** plan) {
+  return make_plan(Ns, Nt, 1, precision, panel, plan, false);
+}
+
 int cl_factor(cl_plan* plan, const double* links, double m, double mu, cudaStream_t stream) {
   if (!compute_ready(plan) || !links) return CL_ERR_INVALID_ARG;
   return run(plan->p, plan->p.factor_ops, links, m, mu, nullptr, nullptr, nullptr, stream);
@@ -431,6 +435,21 @@ int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info) {
         launches += (op.kind == cl::OP_GEMM && p.precision == CL_FP64_EMU) ? 2 : 1;  // split + GEMM
   info->launches_per_eval = launches;
   info->workspace_bytes = (double)p.batch * (4.0 * p.emu_words + 4.0 * p.emu_ints);
+  return CL_OK;
+}
+
+int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* conflicts, char* first, int first_len) {
+  if (!plan || !conflicts) return CL_ERR_INVALID_ARG;
+  std::string msg;
+  try {
+    *conflicts = cl::check_factor_schedule(plan->p, ignore_waits != 0, &msg);
+  } catch (const std::bad_alloc&) {
+    return CL_ERR_OOM;
+  }
+  if (first && first_len > 0) {
+    std::strncpy(first, msg.c_str(), (size_t)first_len - 1);
+    first[first_len - 1] = 0;
+  }
   return CL_OK;
 }
 

@@ -34,7 +34,6 @@ namespace cl {
 namespace {
 
 constexpr int kDig = 7;      // base-256 digits per operand
-constexpr int kLevels = 7;   // digit pairs p + q <= 6 (0-based) -> 28 products
 constexpr int kChunk = 32;   // complex k per exponent chunk (64 real k)
 constexpr int kTileCx = 16;  // complex columns of C per CTA (32 real columns of B')
 
@@ -249,20 +248,13 @@ __device__ __forceinline__ void umma_bf16(uint32_t dtmem, unsigned long long ad,
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+// load without waiting: several loads, then one tmem_ld_wait()
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __global__ void __launch_bounds__(128, 2)
     k_gemm_emu_tc(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1,
@@ -410,24 +402,37 @@ __global__ void __launch_bounds__(128, 2)
     const int rs = rsc[tid] - 16;
 #pragma unroll
     for (int j = 0; j < kTileCx; ++j) sc[j] = pow2f(rs + csc[j]);
-#pragma unroll 1
-    for (int L = 0; L < kLevels; ++L) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * L, v);
-      const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
+    // levels in two batches of loads per half of the columns (one wait each)
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float x = __uint_as_float(v[i]) * (sc[i >> 1] * cL);
-        float s, e1, s2, e2;
-        if (L < 2) {
-          two_sum(h[i], x, s, e1);
-          h[i] = s;
-          two_sum(mi[i], e1, s2, e2);
-        } else {
-          two_sum(mi[i], x, s2, e2);
+    for (int hh = 0; hh < 2; ++hh) {
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + 16 * hh;
+#pragma unroll
+      for (int grp = 0; grp < 2; ++grp) {
+        const int L0 = grp ? 4 : 0, nl = grp ? 3 : 4;
+        uint32_t v[4][16];
+#pragma unroll
+        for (int l = 0; l < nl; ++l) tmem_ld16_issue(ta + 32 * (L0 + l), v[l]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int l = 0; l < nl; ++l) {
+          const int L = L0 + l;
+          const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int i = 16 * hh + k;
+            const float x = __uint_as_float(v[l][k]) * (sc[i >> 1] * cL);
+            float s, e1, s2, e2;
+            if (L < 2) {
+              two_sum(h[i], x, s, e1);
+              h[i] = s;
+              two_sum(mi[i], e1, s2, e2);
+            } else {
+              two_sum(mi[i], x, s2, e2);
+            }
+            mi[i] = s2;
+            lo[i] += e2;
+          }
         }
-        mi[i] = s2;
-        lo[i] += e2;
       }
     }
 #pragma unroll
@@ -689,29 +694,40 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 1
       for (int hh = 0; hh < 2; ++hh) {
         float h[16], mi[16], lo[16];
-#pragma unroll 1
-        for (int L = 0; L < kLevels; ++L) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + 32 * L + 16 * hh, v);
-          const float sL = __int_as_float((127 - 16 - 8 * L) << 23);  // 2^{-16-8L}
-          if (L == 0) {
+        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + 16 * hh;
+        {  // levels 0-3: four loads, one wait
+          uint32_t v[4][16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              h[k] = __uint_as_float(v[k]) * sL;
-              mi[k] = lo[k] = 0.f;
-            }
-          } else if (L == 1) {
+          for (int L = 0; L < 4; ++L) tmem_ld16_issue(ta + 32 * L, v[L]);
+          tmem_ld_wait();
 #pragma unroll
-            for (int k = 0; k < 16; ++k) two_sum(h[k], __uint_as_float(v[k]) * sL, h[k], mi[k]);
-          } else {
+          for (int k = 0; k < 16; ++k) {
+            h[k] = __uint_as_float(v[0][k]) * 0x1p-16f;
+            two_sum(h[k], __uint_as_float(v[1][k]) * 0x1p-24f, h[k], mi[k]);
+            lo[k] = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int L = 2; L < 4; ++L) {
               float s2, e2;
-              two_sum(mi[k], __uint_as_float(v[k]) * sL, s2, e2);
+              two_sum(mi[k], __uint_as_float(v[L][k]) * __int_as_float((127 - 16 - 8 * L) << 23), s2, e2);
               mi[k] = s2;
               lo[k] += e2;
             }
           }
+        }
+        {  // levels 4-6
+          uint32_t v[3][16];
+#pragma unroll
+          for (int L = 0; L < 3; ++L) tmem_ld16_issue(ta + 32 * (L + 4), v[L]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+#pragma unroll
+            for (int L = 0; L < 3; ++L) {
+              float s2, e2;
+              two_sum(mi[k], __uint_as_float(v[L][k]) * __int_as_float((127 - 16 - 8 * (L + 4)) << 23), s2, e2);
+              mi[k] = s2;
+              lo[k] += e2;
+            }
         }
         if (hh == 1) {
           tc_fence_before();

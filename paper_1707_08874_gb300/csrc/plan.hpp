@@ -193,5 +193,9 @@ enum Family { F_ZERO, F_ASSEMBLE, F_EXTADD, F_PANEL, F_GEMM, F_COPY, F_GATHER, F
 // host analysis (analyze.cpp); throws std::invalid_argument on invalid input.
 // panel: pivoting panel width in unknowns (multiple of 3, 3..48), 0 = default
 void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel = 0);
+// number of unordered conflicting element accesses between the two streams of
+// the factor schedule (0: race-free); ignore_waits drops the cross-stream
+// waits (the check must then find races); *first describes the first one
+long long check_factor_schedule(const Plan& p, bool ignore_waits, std::string* first);
 
 }  // namespace cl
