@@ -95,12 +95,19 @@ __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, cons
 // In-place inverse of one diagonal panel block (bp <= kMaxPanel) by
 // Gauss-Jordan elimination with partial (row) pivoting inside the panel; the
 // row interchanges are undone on the columns at the end.  Pivots are chosen by
-// max(|re|, |im|), compared through the ordered bit patterns of the absolute
-// values (integer work only).  A pivot below 1e-13 * max|block| records
-// CL_ERR_SINGULAR (supernode, column).  Threads form a 16 x 16 grid; thread
-// (ty, tx) owns rows ty + 16a and columns tx + 16b of the panel.
+// max(|re|, |im|), compared through the leading 32 bits of the ordered bit
+// pattern of the absolute value (ties: the lowest row); a pivot below
+// 1e-13 * max|block| (1e-6 for FP32 fronts) records CL_ERR_SINGULAR
+// (supernode, column).
+//
+// GB300's FP64 pipe retires ~2 lanes per cycle per SM, so every FP64 warp
+// instruction should carry 32 live lanes: the update phase walks the bp x bp
+// entries linearly (thread t takes entries t, t + 256, ...).  Per column one
+// warp picks the pivot (warp reductions), forms the reciprocal, the
+// multipliers and the scaled pivot row; two block barriers per column.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPanel = 48;
+constexpr int kPanelSlots = (kMaxPanel * kMaxPanel + 255) / 256;  // entries per thread
 
 __device__ __forceinline__ long long mag_key(double2 v) {
   const long long a = __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFll;
@@ -111,39 +118,87 @@ __device__ __forceinline__ long long mag_key(float2 v) {
   const int a = __float_as_int(v.x) & 0x7FFFFFFF, b = __float_as_int(v.y) & 0x7FFFFFFF;
   return a > b ? a : b;
 }
+// 32-bit order key of the magnitude (monotone in max(|re|, |im|))
+__device__ __forceinline__ unsigned key32(double2 v) { return (unsigned)(mag_key(v) >> 32); }
+__device__ __forceinline__ unsigned key32(float2 v) { return (unsigned)mag_key(v); }
 __device__ __forceinline__ double key_value(long long k, double) { return __longlong_as_double(k); }
 __device__ __forceinline__ double key_value(long long k, float) { return (double)__int_as_float((int)k); }
 __device__ __forceinline__ long long value_key(double v, double) { return __double_as_longlong(v); }
 __device__ __forceinline__ long long value_key(double v, float) { return __float_as_int((float)v); }
+
+// |x| truncated to single precision by integer operations (0 below the float
+// range, +inf above): FP64 operations cost ~100 cycles of latency on this part
+__device__ __forceinline__ float abs_to_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(b >> 52) - 1023 + 127;
+  if (e <= 0) return 0.f;
+  if (e >= 255) return __int_as_float(0x7F800000);
+  return __int_as_float((e << 23) | (int)((b >> 29) & 0x7FFFFF));
+}
+// a finite, normal float as a double, by integer operations (exact)
+__device__ __forceinline__ double float_to_double(float f) {
+  const unsigned u = __float_as_uint(f);
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                          ((unsigned long long)(((u >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFF) << 29)));
+}
+
+// 1 / pv = conj(pv) / |pv|^2.  FP64: a single-precision seed of 1 / |pv|^2
+// formed from float copies of the components (integer conversions, so it runs
+// beside the FP64 |pv|^2), then two Newton steps (22 -> 44 -> 88 bits).
+template <typename T, typename R>
+__device__ __forceinline__ T reciprocal(T pv) {
+  const R n2 = fma(pv.x, pv.x, pv.y * pv.y);
+  R r;
+  if (sizeof(R) == 8) {
+    const float xf = abs_to_float(pv.x), yf = abs_to_float(pv.y);
+    const float rf = __fdividef(1.0f, fmaf(xf, xf, yf * yf));
+    const bool seed_ok = rf > 1e-30f && rf < 1e30f;  // normal, far from the float range limits
+    r = seed_ok ? (R)float_to_double(rf) : (R)0;
+    const R e1 = fma(-n2, r, (R)1);
+    r = fma(r, e1, r);
+    const R e2 = fma(-n2, r, (R)1);
+    r = fma(r, e2, r);
+    if (!seed_ok || !(n2 > 0) || !isfinite(r)) r = (R)1 / n2;  // extreme / zero / NaN: plain division
+  } else {
+    r = (R)1 / n2;
+  }
+  T inv;
+  inv.x = pv.x * r;
+  inv.y = -pv.y * r;
+  return inv;
+}
 
 template <typename T, typename R>
 __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
                                                        int64_t stride, int* __restrict__ status) {
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
-  const int bp = d.bp, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int bp = d.bp, nel = bp * bp, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ T S[kMaxPanel][kMaxPanel + 1];  // physical rows; logical row i lives in S[rmap[i]]
   __shared__ T fcol[kMaxPanel], prow[kMaxPanel];
-  __shared__ int rmap[kMaxPanel], piv[kMaxPanel];
+  __shared__ int rmap[kMaxPanel], piv[kMaxPanel], qcol[kMaxPanel];
   __shared__ long long wmax[8];
   __shared__ T sinv;
   __shared__ long long sthr;
+  // this thread's entries (linear order), loaded once
+  int ei[kPanelSlots], ej[kPanelSlots];
   long long km = 0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < bp && j < bp) {
-        const T v = A[(int64_t)i * d.ld + j];
-        S[i][j] = v;
-        km = max(km, mag_key(v));
-      }
+  for (int t = 0; t < kPanelSlots; ++t) {
+    const int e = tid + 256 * t;
+    ei[t] = e < nel ? e / bp : -1;
+    ej[t] = e < nel ? e - ei[t] * bp : 0;
+    if (e < nel) {
+      const T v = A[(int64_t)ei[t] * d.ld + ej[t]];
+      S[ei[t]][ej[t]] = v;
+      km = max(km, mag_key(v));
     }
+  }
   if (tid < bp) rmap[tid] = tid;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
-  if ((tid & 31) == 0) wmax[tid >> 5] = km;
+  if (lane == 0) wmax[warp] = km;
   __syncthreads();
   if (tid == 0) {
     long long m = wmax[0];
@@ -154,104 +209,92 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   __syncthreads();
   const long long thr = sthr;
   for (int c = 0; c < bp; ++c) {
-    // (1) warp 0: pivot among logical rows c..bp-1 (ties keep the lowest),
-    //     exchange it into logical position c, reciprocal of the pivot
-    if (tid < 32) {
-      long long best = -1;
-      int bi = c;
-      for (int i = c + tid; i < bp; i += 32) {
-        const long long k = mag_key(S[rmap[i]][c]);
-        if (k > best) { best = k; bi = i; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) {
-        piv[c] = bi;
-        const int pc = rmap[bi];
-        rmap[bi] = rmap[c];
-        rmap[c] = pc;
-        if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
-        // 1/pv = conj(pv) / |pv|^2; the reciprocal of |pv|^2 from a
-        // single-precision seed refined by two Newton steps (24 -> 48 -> 96
-        // bits), a short dependent chain on the serial path of the panel
-        const T pv = S[pc][c];
-        const R n2 = pv.x * pv.x + pv.y * pv.y;
-        R r = (R)(1.0f / (float)n2);
-        if (sizeof(R) == 8) {
-          r = r * ((R)2 - n2 * r);
-          r = r * ((R)2 - n2 * r);
+    if (warp == 0) {
+      // (1) pivot among logical rows c..bp-1, lowest row on ties
+      unsigned key = 0;
+      int bi = 0x7fffffff;
+      for (int i = c + lane; i < bp; i += 32) {
+        const unsigned k = key32(S[rmap[i]][c]);
+        if (bi == 0x7fffffff || k > key) {
+          key = k;
+          bi = i;
         }
-        if (!(n2 > 0) || !isfinite(r)) r = (R)1 / n2;  // zero / overflow / NaN: plain division
-        T inv;
-        inv.x = pv.x * r;
-        inv.y = -pv.y * r;
+      }
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, bi != 0x7fffffff ? key : 0u);
+      const int pr = (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && key == kmax) ? (unsigned)bi : 0x7fffffffu);
+      const int pc = rmap[pr];
+      const T pv = S[pc][c];
+      const T inv = reciprocal<T, R>(pv);
+      __syncwarp();
+      if (lane == 0) {
+        piv[c] = pr;
+        rmap[pr] = rmap[c];
+        rmap[c] = pc;
+        const long long best = mag_key(pv);
+        if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
         sinv = inv;
       }
+      __syncwarp();
+      // (2) multipliers (column c of every logical row) and the scaled pivot row
+      for (int i = lane; i < bp; i += 32) {
+        fcol[i] = S[rmap[i]][c];
+        prow[i] = (i == c) ? inv : cmul(S[pc][i], inv);
+      }
     }
     __syncthreads();
-    // (2) multipliers (column c of every logical row) and the scaled pivot row
+    // (3) eliminate column c from every other logical row; row c <- pivot row.
+    // All loads first, then four FMAs per entry (independent across entries),
+    // then the stores.
     const T inv = sinv;
-    if (tid < bp) {
-      fcol[tid] = S[rmap[tid]][c];
-      prow[tid] = (tid == c) ? inv : cmul(S[rmap[c]][tid], inv);
-    }
-    __syncthreads();
-    // (3) eliminate column c from every other logical row; row c <- pivot row
+    T vv[kPanelSlots], ww[kPanelSlots], ff[kPanelSlots];
+    int rp[kPanelSlots];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int i = ty + 16 * a;
-      if (i >= bp) continue;
-      T* Si = S[rmap[i]];
+    for (int t = 0; t < kPanelSlots; ++t) {
+      if (ei[t] < 0) continue;
+      rp[t] = rmap[ei[t]];
+      vv[t] = S[rp[t]][ej[t]];
+      ww[t] = ej[t] == c ? inv : prow[ej[t]];
+      ff[t] = fcol[ei[t]];
+    }
+#pragma unroll
+    for (int t = 0; t < kPanelSlots; ++t) {
+      if (ei[t] < 0) continue;
+      const int i = ei[t], j = ej[t];
+      T v;
       if (i == c) {
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const int j = tx + 16 * b;
-          if (j < bp) Si[j] = prow[j];
-        }
-        continue;
+        v = ww[t];  // the scaled pivot row (inv on the diagonal)
+      } else if (j == c) {
+        v.x = -(ff[t].x * inv.x - ff[t].y * inv.y);
+        v.y = -(ff[t].x * inv.y + ff[t].y * inv.x);
+      } else {
+        v = vv[t];
+        const T f = ff[t], w = ww[t];
+        v.x = fma(-f.x, w.x, v.x);
+        v.x = fma(f.y, w.y, v.x);
+        v.y = fma(-f.x, w.y, v.y);
+        v.y = fma(-f.y, w.x, v.y);
       }
-      const T f = fcol[i];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const int j = tx + 16 * b;
-        if (j >= bp) continue;
-        if (j == c) {
-          const T v = cmul(f, inv);
-          Si[c] = T{-v.x, -v.y};
-        } else {
-          T v = Si[j];
-          const T w = prow[j];
-          v.x -= f.x * w.x - f.y * w.y;
-          v.y -= f.x * w.y + f.y * w.x;
-          Si[j] = v;
-        }
-      }
+      vv[t] = v;
     }
+#pragma unroll
+    for (int t = 0; t < kPanelSlots; ++t)
+      if (ei[t] >= 0) S[rp[t]][ej[t]] = vv[t];
     __syncthreads();
   }
-  // logical rows are in rmap order; undo the column interchanges in reverse
-  // order (they mirror the row interchanges of the pivoting) and store
-  for (int c = bp - 1; c >= 0; --c) {
-    const int p = piv[c];
-    if (p != c && tid < bp) {
-      T* Sr = S[rmap[tid]];
-      const T t = Sr[c];
-      Sr[c] = Sr[p];
-      Sr[p] = t;
+  // logical rows are in rmap order; the row interchanges are undone on the
+  // columns in reverse order: result column j = column qcol[j] of S
+  if (tid == 0) {
+    for (int j = 0; j < bp; ++j) qcol[j] = j;
+    for (int c = bp - 1; c >= 0; --c) {
+      const int p = piv[c], t = qcol[c];
+      qcol[c] = qcol[p];
+      qcol[p] = t;
     }
-    __syncthreads();
   }
+  __syncthreads();
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < bp && j < bp) A[(int64_t)i * d.ld + j] = S[rmap[i]][j];
-    }
+  for (int t = 0; t < kPanelSlots; ++t)
+    if (ei[t] >= 0) A[(int64_t)ei[t] * d.ld + ej[t]] = S[rmap[ei[t]]][qcol[ej[t]]];
 }
 
 // ---------------------------------------------------------------------------
