@@ -121,6 +121,24 @@ def oracle_sample(lu_steps=256, ncols=96):
     return 1.0 / t_eval, cores, sample, t_eval
 
 
+def lapack_sample():
+    """The paper's dense comparison (Sec. 3: the full inverse by LAPACK) on the
+    host cores: dense D of the workload (oracle) and torch.linalg.inv in
+    complex128, timed once; the drift itself is negligible beside it."""
+    import torch
+    import oracle
+    from paper_1707_08874_gb300 import inputs
+    U = inputs.random_links(NS, NT, seed=inputs.BASE_SEED)
+    t0 = time.perf_counter()
+    D = torch.from_numpy(oracle.dirac_dense(NS, NT, U, M, MU))
+    t1 = time.perf_counter()
+    torch.linalg.inv(D)
+    t2 = time.perf_counter()
+    sample = ("8^3x4 dense D (%.1f s) + torch.linalg.inv complex128 N=%d (%.1f s), one evaluation"
+              % (t1 - t0, D.shape[0], t2 - t1))
+    return 1.0 / (t2 - t0), torch.get_num_threads(), sample
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -320,9 +338,7 @@ def run_ours(args, rank, world, local):
     gemm_ms = g.get("total_ms", 0.0) / max(1, g.get("launches", 1))
     gemm_flops = g.get("flops", 0.0) / max(1, g.get("launches", 1))
     achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
-    peak = peak_gflops / 1e3
-    if prec == B.CL_FP64_EMU:
-        peak /= 28.0  # 28 BF16 digit products per FP64-equivalent product
+    peak = peak_gflops / 1e3  # FP64-equivalent for the emulated path (BF16 peak / 28, above)
     total_prof_ms = sum(v["total_ms"] for v in prof.values())
     flops_eval = info["factor_flops"] + info["selinv_flops"]
     line = {
@@ -357,6 +373,9 @@ def run_ours(args, rank, world, local):
     if not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}
+        lv, lcores, lsample = lapack_sample()
+        line["cpu_lapack"] = {"value": lv, "unit": "evals/s", "cores": lcores, "kind": "dense LAPACK inverse",
+                              "sample": lsample}
     print(json.dumps(line), flush=True)
     plan.close()
 

@@ -97,6 +97,10 @@ typedef struct cl_langevin_params {
   unsigned long long seed;   /* key of the Philox4x32-10 noise stream           */
   int n_cool;                /* gauge-cooling iterations after each update     */
   int fermions;              /* 1: K = K^g + K^f (selected inversion); 0: K^g only */
+  int renorm_det;            /* 1: after each update U <- U / det(U)^{1/3} (principal cube
+                                root), removing the drift of det U away from 1; 0: off
+                                (default, as in the paper: Sec. 4.2 keeps the links free
+                                rather than reunitarising, for consistency with mu != 0) */
 } cl_langevin_params;
 
 /*

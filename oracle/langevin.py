@@ -168,6 +168,16 @@ def link_update(U, K, eps, eta):
     return R @ U
 
 
+def renorm_det(U):
+    """Optional determinant renormalisation, off by default as in the paper
+    (Sec. 4.2 keeps the links free rather than reunitarising): U <- U /
+    det(U)^{1/3} with the principal cube root |d|^{1/3} exp(i arg(d) / 3),
+    arg in (-pi, pi]."""
+    d = np.linalg.det(U)
+    c = np.abs(d) ** (1.0 / 3.0) * np.exp(1j * np.angle(d) / 3.0)
+    return U / c[..., None, None]
+
+
 def cooling_gradient(U, Ns, Nt):
     _, dn, _ = shifts(Ns, Nt)
     Uh = np.conj(np.swapaxes(U, -1, -2))
@@ -244,6 +254,8 @@ def langevin_step(U, prm: dict, step: int, Ns: int, Nt: int, replica: int = 0):
     obs["eps"] = eps
     eta = noise(prm["seed"], step, V, replica)
     U2 = link_update(U, K, eps, eta)
+    if prm.get("renorm_det", 0):
+        U2 = renorm_det(U2)
     if prm.get("n_cool", 0) > 0:
         U2 = gauge_cool(U2, prm["n_cool"], prm["alpha_cool"], Ns, Nt)
     return U2, obs, eps

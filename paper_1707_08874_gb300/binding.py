@@ -55,7 +55,8 @@ class ProfileEntry(ctypes.Structure):
 class LangevinParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("m", ctypes.c_double), ("mu", ctypes.c_double), ("nf", ctypes.c_double),
                 ("eps_max", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha_cool", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("n_cool", ctypes.c_int), ("fermions", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("n_cool", ctypes.c_int), ("fermions", ctypes.c_int),
+                ("renorm_det", ctypes.c_int)]
 
 
 OBS_FIELDS = ["plaq_s_re", "plaq_s_im", "plaq_t_re", "plaq_t_im", "poly_re", "poly_im", "poly_inv_re",

@@ -379,6 +379,7 @@ int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm
     if (st != CL_OK) return st;
   }
   cl::LangevinArgs a{prm->eps_max, prm->kappa, 0.0, prm->seed, 0};
+  a.renorm_det = prm->renorm_det != 0;
   cudaError_t e = cl::launch_gauge_drift(p, links, p.d_Ui, prm->beta, p.d_K, ferm ? 1 : 0, stream);
   if (e == cudaSuccess) e = cl::launch_kmax(p, p.d_K, p.d_slots, stream);
   if (e == cudaSuccess)

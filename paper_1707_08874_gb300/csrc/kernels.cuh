@@ -35,6 +35,7 @@ struct LangevinArgs {
   double fixed_eps;       // > 0: use this step and `step` instead of the rule and the state
   unsigned long long seed;
   long long step;
+  int renorm_det = 0;     // 1: U <- U / det(U)^{1/3} after the update
 };
 // observables record per replica (doubles): plaq_s re,im | plaq_t re,im | poly re,im |
 // poly_inv re,im | condensate re,im | unitarity | K_max | eps | t | step | spare |

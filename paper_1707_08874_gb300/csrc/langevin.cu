@@ -249,7 +249,20 @@ __global__ void k_update(double* __restrict__ U, const double* __restrict__ K, i
   M3 u;
 #pragma unroll
   for (int i = 0; i < 9; ++i) u.e[i] = up[i];
-  const M3 v = mul_m3(R, u);
+  M3 v = mul_m3(R, u);
+  if (a.renorm_det) {
+    // U <- U / det(U)^{1/3}, principal cube root |d|^{1/3} e^{i arg(d) / 3}
+    const double2* E = v.e;
+    const double2 d = cadd(cadd(cmul(E[0], csub(cmul(E[4], E[8]), cmul(E[5], E[7]))),
+                                cmul(E[1], csub(cmul(E[5], E[6]), cmul(E[3], E[8])))),
+                           cmul(E[2], csub(cmul(E[3], E[7]), cmul(E[4], E[6]))));
+    const double rad = 1.0 / cbrt(hypot(d.x, d.y)), ang = -atan2(d.y, d.x) / 3.0;
+    double sn, cs;
+    sincos(ang, &sn, &cs);
+    const double2 f = make_double2(rad * cs, rad * sn);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v.e[i] = cmul(v.e[i], f);
+  }
 #pragma unroll
   for (int i = 0; i < 9; ++i) up[i] = v.e[i];
 }

@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--calib", type=int, default=10)
     ap.add_argument("--n-cool", type=int, default=5)
     ap.add_argument("--alpha-cool", type=float, default=0.05)
+    ap.add_argument("--renorm-det", action="store_true", help="U <- U / det(U)^(1/3) after each update")
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--seed", type=int, default=1707)
@@ -63,7 +64,8 @@ def main(argv=None):
     state = torch.from_numpy(state0).to("cuda")
     obs = torch.zeros((args.batch, B.OBS_LEN), dtype=torch.float64, device="cuda")
     prm = dict(beta=args.beta, m=args.m, mu=args.mu, nf=args.nf, eps_max=args.eps_max, kappa=args.kappa,
-               alpha_cool=args.alpha_cool, seed=args.seed, n_cool=args.n_cool, fermions=1)
+               alpha_cool=args.alpha_cool, seed=args.seed, n_cool=args.n_cool, fermions=1,
+               renorm_det=int(args.renorm_det))
     out = open(args.out, "w") if args.out else sys.stdout
     kcal = []
     t0 = time.time()

@@ -122,6 +122,26 @@ def test_langevin_steps_match_oracle(plan, links2, kappa, n_cool):
         assert _rel(got[b], ref[b]) < 1e-11
 
 
+def test_langevin_step_renorm_det(plan, links2):
+    """The optional determinant renormalisation: links scaled off SL(3,C)
+    come back to det U = 1 after one full step, matching the oracle step."""
+    B = _B()
+    prm = dict(beta=5.0, m=0.05, mu=0.25, nf=1.0, eps_max=1e-3, kappa=0.0, alpha_cool=0.05, seed=77,
+               n_cool=1, fermions=1, renorm_det=1)
+    U0 = links2 * (1.05 * np.exp(0.2j))
+    U = _dev(U0)
+    state = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    obs = torch.zeros((2, 20), dtype=torch.float64, device="cuda")
+    plan.langevin_step(U, prm, state, obs)
+    torch.cuda.synchronize()
+    assert plan.get_status()[0] == B.CL_OK
+    got = U.cpu().numpy()
+    for b in range(2):
+        ref, _, _ = L.langevin_step(U0[b].copy(), prm, 0, NS, NT, replica=b)
+        assert _rel(got[b], ref) < 1e-11
+        assert np.abs(np.linalg.det(got[b]) - 1).max() < 1e-12
+
+
 def test_pure_gauge_su3_stays_unitary():
     """beta > 0, no fermions, SU(3) start: real drift and real noise keep the
     links in SU(3) (no excursion without a complex action)."""

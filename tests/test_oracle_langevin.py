@@ -142,3 +142,17 @@ def test_observables_unit_and_gauge_invariant(links):
     b = L.observables(U2, NS, NT)
     for k in ("plaq_s", "plaq_t", "poly", "poly_inv"):
         assert abs(a[k] - b[k]) < 1e-12, k
+
+
+def test_renorm_det_pins():
+    """Determinant renormalisation: det U = 1 afterwards; SL(3,C) links are
+    left as they are; a positive real factor on U is removed exactly (the
+    principal cube root of c^3 det U is c det(U)^{1/3})."""
+    rng = np.random.default_rng(12)
+    U = inputs.random_links(4, 4, seed=31)
+    A = U * (1.3 * np.exp(0.4j))
+    R = L.renorm_det(A)
+    assert np.abs(np.linalg.det(R) - 1).max() < 1e-13
+    assert np.abs(L.renorm_det(U) - U).max() < 1e-13 * np.abs(U).max()
+    c = rng.uniform(0.5, 2.0)
+    assert np.abs(L.renorm_det(c * A) - R).max() < 1e-13 * np.abs(R).max()
