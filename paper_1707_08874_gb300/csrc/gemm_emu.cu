@@ -23,8 +23,9 @@
 // Two kernels per GEMM launch:
 //   k_emu_split    digits and exponents of A and B, written as tiles in the
 //                  order the tensor core reads shared memory;
-//   k_gemm_emu_tc  the digit products as tcgen05 MMAs with FP32 accumulators
-//                  in tensor memory, the fold and the FP64 epilogue.
+//   k_gemm_emu_persist / k_gemm_emu_chunked  the digit products as tcgen05
+//                  MMAs with FP32 accumulators in tensor memory, the fold and
+//                  the FP64 epilogue (single-chunk and chunked launches).
 #include <algorithm>
 #include <cstring>
 
@@ -170,23 +171,15 @@ __device__ __forceinline__ double f2d_scaled(float f, int ex, bool neg) {
 }
 
 // ---------------------------------------------------------------------------
-// Digit GEMM on tcgen05.  CTA tile: 128 rows x 16 complex columns (32 real
-// columns of B'), 128 threads, two CTAs per SM so that one CTA's fold and
-// epilogue overlap the other's MMAs and copies.  Per chunk, in two halves of
-// 32 real k: bulk copies of the 7 A digit half-tiles and the B' half-block
-// into shared memory, then 14 asynchronous BF16 MMAs issued by one thread
-// (A digit p times B' digits 0 .. 6-p, 128 x 32(7-p) x 16) into seven
-// 32-column FP32 accumulators in tensor memory (one per level p + q; 224 of
-// the CTA's 256 columns).  The CTA's four warps then read the
-// levels back (thread = row) and fold them into triple-float.  Every wait on
-// an mbarrier gives up after a bounded time, records CL_ERR_TIMEOUT, waits
-// once more for what it had in flight and leaves through the normal teardown
-// (tensor memory freed).
+// tcgen05 building blocks of the digit GEMMs.  Operands reach shared memory by
+// bulk copies of the pre-tiled digit planes; one thread issues BF16 MMAs into
+// FP32 accumulators in tensor memory (one 32-column accumulator per level
+// p + q, 224 columns per set); warps read the levels back with tcgen05.ld.
+// Every wait on an mbarrier gives up after a bounded time, records
+// CL_ERR_TIMEOUT, waits once more for what it had in flight and leaves through
+// the normal teardown (tensor memory freed).
 constexpr int kAHalf = 8192;     // bytes: 128 rows x 32 real k, BF16 (two 16-k slabs)
 constexpr int kBHalf = 2048;     // bytes per digit: 32 real columns x 32 real k
-constexpr uint32_t kTcCols = 256;
-constexpr int kTcCtl = 2048;     // control block: mbarriers, TMEM address, exponents
-constexpr size_t kTcSmemBytes = (size_t)kDig * (kAHalf + kBHalf) + kTcCtl;
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28;
 // M = 128, N = 32 (7 - p) for A digit p (a multiple of 16, <= 224)
@@ -255,235 +248,6 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&v)[16
                : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__global__ void __launch_bounds__(128, 2)
-    k_gemm_emu_tc(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1,
-                  double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
-                  const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
-  extern __shared__ __align__(1024) unsigned char smem_tc[];
-  unsigned char* sA = smem_tc;                  // [7][kAHalf]
-  unsigned char* sB = smem_tc + kDig * kAHalf;  // [7][kBHalf]
-  unsigned char* ctl = sB + kDig * kBHalf;
-  // mbarriers: [0] operands landed, [1] MMAs of the first half done, [2] MMAs of the chunk done
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 32);
-  int* abort_flag = reinterpret_cast<int*>(ctl + 36);
-  int* Rm = reinterpret_cast<int*>(ctl + 64);  // [128] row maxima of the chunk exponents
-  int* Sm = Rm + 128;                          // [16]  column maxima
-  int* rsc = Sm + kTileCx;                     // [128] chunk exponent minus the row maximum
-  int* csc = rsc + 128;                        // [16]  same for the columns
-
-  const int di = find_desc(gd, d0, d1, blockIdx.x);
-  const GemmDesc g = gd[di];
-  const EmuDesc e = ed[di];
-  const int t = blockIdx.x - g.blk0;
-  const int rb = t / g.tilesN, nb = t % g.tilesN;
-  const int row0 = rb * 128, col0 = nb * kTileCx;
-  const unsigned* Wd = words + blockIdx.y * wstride;
-  const int* Id = ints + blockIdx.y * istride;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int nch = e.Kp / kChunk;
-  const uint32_t s_full = smem_u32(&bars[0]), s_h0 = smem_u32(&bars[1]), s_done = smem_u32(&bars[2]);
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(kTcCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 32) {
-    mbar_init(s_full, 1);
-    mbar_init(s_h0, 1);
-    mbar_init(s_done, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  {
-    int m = -4000;
-    for (int c = 0; c < nch; ++c) m = max(m, Id[e.aexp + (int64_t)c * e.Mp + row0 + tid]);
-    Rm[tid] = m;
-  }
-  if (tid < kTileCx) {
-    int m = -4000;
-    for (int c = 0; c < nch; ++c) m = max(m, Id[e.bexp + (int64_t)c * e.Np + col0 + tid]);
-    Sm[tid] = m;
-  }
-  // exponents of the next chunk, loaded one chunk ahead
-  int ra = nch > 0 ? Id[e.aexp + row0 + tid] : 0;
-  int cb = (tid < kTileCx && nch > 0) ? Id[e.bexp + col0 + tid] : 0;
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tslot;
-
-  // bulk copies of half `hf` of chunk c (thread 0)
-  auto issue = [&](int c, int hf) {
-    mbar_expect_tx(s_full, (unsigned)(kDig * (kAHalf + kBHalf)));
-    const int64_t ablk = (int64_t)rb * nch + c, bblk = (int64_t)nb * nch + c;
-#pragma unroll 1
-    for (int p = 0; p < kDig; ++p)
-      bulk_g2s(smem_u32(sA + p * kAHalf), Wd + e.adig + (ablk * kDig + p) * 4096 + hf * 2048, kAHalf, s_full);
-    bulk_g2s(smem_u32(sB), Wd + e.bdig + bblk * 7168 + hf * 3584, kDig * kBHalf, s_full);
-  };
-  // the 14 MMAs of one half (thread 0): A digit p times B' digits 0 .. 6-p
-  // (N = 32 (7 - p)) into levels p .. 6 at TMEM columns 32 p ..
-  auto mmas = [&](int hf) {
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-#pragma unroll 1
-    for (int p = 0; p < kDig; ++p)
-#pragma unroll
-      for (int kb = 0; kb < 2; ++kb)
-        umma_bf16(tmem + 32 * p, umma_desc(a0 + p * kAHalf + kb * 4096), umma_desc(b0 + kb * (kDig * 1024)),
-                  tc_idesc(p), (hf | p | kb) != 0 ? 1u : 0u);
-  };
-
-  float h[32], mi[32], lo[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) h[i] = mi[i] = lo[i] = 0.f;
-
-  unsigned fph = 0;  // phase of the operands barrier (thread 0)
-  if (tid == 0 && nch > 0) issue(0, 0);  // K = 0: no operands, C = beta C
-  bool ok = true;
-#pragma unroll 1
-  for (int c = 0; c < nch; ++c) {
-    rsc[tid] = ra - Rm[tid];
-    if (tid < kTileCx) csc[tid] = cb - Sm[tid];
-    if (c + 1 < nch) {
-      ra = Id[e.aexp + (int64_t)(c + 1) * e.Mp + row0 + tid];
-      if (tid < kTileCx) cb = Id[e.bexp + (int64_t)(c + 1) * e.Np + col0 + tid];
-    }
-    __syncthreads();
-    if (tid == 0) {
-      // stage that gave up: 1 first-half operands, 2 first-half MMAs, 3 second-half operands
-      int fail = 0;
-      if (!mbar_wait(s_full, fph)) {
-        fail = 1;
-        mbar_wait(s_full, fph);  // copies in flight: wait once more
-      }
-      fph ^= 1;
-      if (!fail) {
-        tc_fence_after();
-        mmas(0);
-        umma_commit(s_h0);
-        if (!mbar_wait(s_h0, c & 1)) {
-          fail = 2;
-          mbar_wait(s_h0, c & 1);
-        }
-      }
-      if (!fail) {
-        issue(c, 1);  // the first half's operands are consumed
-        if (!mbar_wait(s_full, fph)) {
-          fail = 3;
-          mbar_wait(s_full, fph);
-        }
-        fph ^= 1;
-      }
-      if (!fail) {
-        tc_fence_after();
-        mmas(1);
-        umma_commit(s_done);
-      } else {
-        *abort_flag = 1;
-        set_status(status, CL_ERR_TIMEOUT, -fail, c);
-        mbar_arrive(s_done);  // no second-half MMAs: release the other threads
-      }
-    }
-    const bool got = mbar_wait(s_done, c & 1);
-    tc_fence_after();
-    if (!got) set_status(status, CL_ERR_TIMEOUT, -4, c);
-    if (__syncthreads_or(!got || *abort_flag)) {
-      ok = false;
-      if (tid == 0 && !*abort_flag) mbar_wait(s_done, c & 1);  // MMAs may still run: wait once more
-      break;
-    }
-    if (tid == 0 && c + 1 < nch) issue(c + 1, 0);  // overlaps the fold below
-
-    float sc[kTileCx];  // 2^{(e_i - R_i) + (f_n - S_n) - 16} for this row and the 16 complex columns
-    const int rs = rsc[tid] - 16;
-#pragma unroll
-    for (int j = 0; j < kTileCx; ++j) sc[j] = pow2f(rs + csc[j]);
-    // levels in two batches of loads per half of the columns (one wait each)
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + 16 * hh;
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-        const int L0 = grp ? 4 : 0, nl = grp ? 3 : 4;
-        uint32_t v[4][16];
-#pragma unroll
-        for (int l = 0; l < nl; ++l) tmem_ld16_issue(ta + 32 * (L0 + l), v[l]);
-        tmem_ld_wait();
-#pragma unroll
-        for (int l = 0; l < nl; ++l) {
-          const int L = L0 + l;
-          const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int i = 16 * hh + k;
-            const float x = __uint_as_float(v[l][k]) * (sc[i >> 1] * cL);
-            float s, e1, s2, e2;
-            if (L < 2) {
-              two_sum(h[i], x, s, e1);
-              h[i] = s;
-              two_sum(mi[i], e1, s2, e2);
-            } else {
-              two_sum(mi[i], x, s2, e2);
-            }
-            mi[i] = s2;
-            lo[i] += e2;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      float s, e1, s2, e2;
-      two_sum(h[i], mi[i], s, e1);
-      two_sum(e1, lo[i], s2, e2);
-      h[i] = s;
-      mi[i] = s2;
-      lo[i] = e2;
-    }
-    tc_fence_before();
-    __syncthreads();  // accumulators read: the next chunk's MMAs may overwrite them
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
-  }
-  if (!ok) return;
-
-  // epilogue: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value.  The
-  // C row segment is loaded first (16 independent loads), then written.
-  const int r = row0 + tid;
-  if (r >= g.M || g.rmask.hit(r)) return;
-  double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)r * g.ldc + col0;
-  const bool neg = g.neg != 0;
-  double2 cv[kTileCx];
-  if (g.beta) {
-#pragma unroll
-    for (int j = 0; j < kTileCx; ++j) cv[j] = col0 + j < g.N ? crow[j] : make_double2(0, 0);
-  }
-#pragma unroll
-  for (int j = 0; j < kTileCx; ++j) {
-    const int cc = col0 + j;
-    if (cc >= g.N || g.cmask.hit(cc)) continue;
-    const int ex = Rm[tid] + Sm[j];
-    double vv[2];
-#pragma unroll
-    for (int part = 0; part < 2; ++part) {
-      const int q = 2 * j + part;
-      float s, e1;
-      two_sum(h[q], mi[q], s, e1);
-      vv[part] = f2d_scaled(s, ex, neg) + f2d_scaled(e1 + lo[q], ex, neg);
-    }
-    double2 v = make_double2(vv[0], vv[1]);
-    if (g.beta) v = cadd(v, cv[j]);
-    crow[j] = v;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Persistent digit GEMM for launches whose problems all have K <= 32 (one
@@ -776,12 +540,266 @@ __global__ void __launch_bounds__(320, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent digit GEMM for chunked launches (some K > 32: the products of the
+// selected inversion, K up to a pivot block).  One CTA per SM over a
+// contiguous range of output tiles (128 rows x 16 complex columns); per tile
+// its chunks of 32 complex k in order, each chunk in two halves of 32 real k.
+// Warp-specialised, 320 threads:
+//   warp 0 lane 0  producer: per half, the 7 A digit half-tiles (56 KB) and
+//                  the B' half-block (14 KB) into a three-stage ring;
+//   warp 1 lane 0  MMA issuer: 14 wide MMAs per half into one of two TMEM
+//                  accumulator sets (set = chunk parity), so the MMAs of
+//                  chunk k+1 run while chunk k is folded;
+//   warps 2-9      fold: two groups of four warps, group g owning complex
+//                  columns 8g .. 8g+7 of the tile (thread = row), fold each
+//                  chunk's levels into triple-float with the chunk's row /
+//                  column exponents and write the tile after its last chunk.
+constexpr int kCStage = kDig * (kAHalf + kBHalf);  // bytes per ring stage
+constexpr int kCStages = 3;
+constexpr size_t kCSmemBytes = (size_t)kCStages * kCStage + 1024;
+
+__global__ void __launch_bounds__(320, 1)
+    k_gemm_emu_chunked(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
+                       double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
+                       const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_c[];
+  unsigned char* ctl = smem_c + kCStages * kCStage;
+  // mbarriers: [0..2] stage landed, [3..5] stage consumed, [6,7] accumulator
+  //            set full, [8,9] accumulator set drained
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 96);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 100);
+  const uint32_t bar0 = smem_u32(bars);
+  auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
+  auto stageA = [&](int s) { return smem_c + s * kCStage; };
+  auto stageB = [&](int s) { return smem_c + s * kCStage + kDig * kAHalf; };
+
+  const int G = gridDim.x;
+  const int t0 = (int)((int64_t)total * blockIdx.x / G), t1 = (int)((int64_t)total * (blockIdx.x + 1) / G);
+  const unsigned* Wd = words + blockIdx.y * wstride;
+  const int* Id = ints + blockIdx.y * istride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kPCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int i = 0; i < 8; ++i) mbar_init(bar(i), 1);
+    mbar_init(bar(8), 256);  // both fold groups drain a set
+    mbar_init(bar(9), 256);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- producer
+      int q = 0;
+      bool good = true;
+      for (int t = t0; t < t1 && good && !*abort_flag; ++t) {
+        const TileRef tr = tile_ref(gd, d0, d1, t);
+        const EmuDesc& e = ed[tr.di];
+        const int nch = e.Kp / kChunk;
+        for (int c = 0; c < nch && good; ++c)
+          for (int hf = 0; hf < 2; ++hf, ++q) {
+            const int s = q % kCStages, u = q / kCStages;
+            if (q >= kCStages && !mbar_wait_ab(bar(3 + s), (u - 1) & 1, abort_flag)) {
+              good = false;
+              break;
+            }
+            mbar_expect_tx(bar(s), (unsigned)kCStage);
+            const int64_t ablk = (int64_t)tr.rb * nch + c, bblk = (int64_t)tr.j * nch + c;
+            for (int p = 0; p < kDig; ++p)
+              bulk_g2s(smem_u32(stageA(s) + p * kAHalf), Wd + e.adig + (ablk * kDig + p) * 4096 + hf * 2048, kAHalf,
+                       bar(s));
+            bulk_g2s(smem_u32(stageB(s)), Wd + e.bdig + bblk * 7168 + hf * 3584, kDig * kBHalf, bar(s));
+          }
+      }
+      if (!good) {
+        *abort_flag = 1;
+        set_status(status, CL_ERR_TIMEOUT, -8, t0);
+      }
+      if (*abort_flag)  // copies still in flight: the last stages, bounded
+        for (int i = max(0, q - kCStages); i < q; ++i) mbar_wait(bar(i % kCStages), (i / kCStages) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      int q = 0, k = 0;
+      bool good = true;
+      for (int t = t0; t < t1 && good && !*abort_flag; ++t) {
+        const TileRef tr = tile_ref(gd, d0, d1, t);
+        const int nch = ed[tr.di].Kp / kChunk;
+        for (int c = 0; c < nch && good; ++c, ++k) {
+          const int set = k & 1, uk = k >> 1;
+          if (k >= 2 && !mbar_wait_ab(bar(8 + set), (uk - 1) & 1, abort_flag)) {
+            good = false;
+            break;
+          }
+          for (int hf = 0; hf < 2; ++hf, ++q) {
+            const int s = q % kCStages, u = q / kCStages;
+            if (!mbar_wait_ab(bar(s), u & 1, abort_flag)) {
+              good = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(stageA(s)), b0 = smem_u32(stageB(s)), d = tmem + 256u * set;
+#pragma unroll 1
+            for (int p = 0; p < kDig; ++p)
+#pragma unroll
+              for (int kb = 0; kb < 2; ++kb)
+                umma_bf16(d + 32 * p, umma_desc(a0 + p * kAHalf + kb * 4096), umma_desc(b0 + kb * (kDig * 1024)),
+                          tc_idesc(p), (hf | p | kb) != 0 ? 1u : 0u);
+            umma_commit(bar(3 + s));
+          }
+          if (!good) break;
+          umma_commit(bar(6 + set));
+        }
+      }
+      if (!good) {
+        *abort_flag = 1;
+        set_status(status, CL_ERR_TIMEOUT, -9, t0);
+      }
+      if (*abort_flag && k > 0) mbar_wait(bar(6 + ((k - 1) & 1)), ((k - 1) >> 1) & 1);  // MMAs in flight
+    }
+    __syncwarp();
+  } else {  // ---- fold and epilogue
+    const int grp = (warp - 2) >> 2, q4 = warp & 3, rl = q4 * 32 + lane;
+    int k = 0;
+    bool stop = false;
+    for (int t = t0; t < t1 && !stop; ++t) {
+      const TileRef tr = tile_ref(gd, d0, d1, t);
+      const GemmDesc g = gd[tr.di];
+      const EmuDesc e = ed[tr.di];
+      const int nch = e.Kp / kChunk;
+      const int row = tr.rb * 128 + rl, c8 = tr.j * kTileCx + 8 * grp;
+      // row / column maxima of the chunk exponents (column jj = lane jj of each warp)
+      int Rm = -4000, Sc = -4000;
+      for (int c = 0; c < nch; ++c) {
+        Rm = max(Rm, Id[e.aexp + (int64_t)c * e.Mp + row]);
+        if (lane < 8) Sc = max(Sc, Id[e.bexp + (int64_t)c * e.Np + c8 + lane]);
+      }
+      int ra = nch > 0 ? Id[e.aexp + row] : 0;
+      int cb = (lane < 8 && nch > 0) ? Id[e.bexp + c8 + lane] : 0;
+      float h[16], mi[16], lo[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) h[i] = mi[i] = lo[i] = 0.f;
+      for (int c = 0; c < nch; ++c, ++k) {
+        __syncwarp();
+        const int rsc = ra - Rm - 16, csc = cb - Sc;
+        if (c + 1 < nch) {
+          ra = Id[e.aexp + (int64_t)(c + 1) * e.Mp + row];
+          if (lane < 8) cb = Id[e.bexp + (int64_t)(c + 1) * e.Np + c8 + lane];
+        }
+        float sc[8];  // 2^{(e_i - R_i) + (f_n - S_n) - 16}
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) sc[jj] = pow2f(rsc + __shfl_sync(0xffffffffu, csc, jj));
+        const int set = k & 1, uk = k >> 1;
+        const bool got = mbar_wait_ab(bar(6 + set), uk & 1, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (!*abort_flag) set_status(status, CL_ERR_TIMEOUT, -10, t0);
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * set + 16 * grp;
+#pragma unroll
+        for (int b4 = 0; b4 < 2; ++b4) {  // levels 0-3, then 4-6
+          const int L0 = 4 * b4, nl = b4 ? 3 : 4;
+          uint32_t v[4][16];
+#pragma unroll
+          for (int l = 0; l < nl; ++l) tmem_ld16_issue(ta + 32 * (L0 + l), v[l]);
+          tmem_ld_wait();
+          if (b4) {
+            tc_fence_before();
+            mbar_arrive(bar(8 + set));  // accumulator set drained
+          }
+#pragma unroll
+          for (int l = 0; l < nl; ++l) {
+            const int L = L0 + l;
+            const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float x = __uint_as_float(v[l][i]) * (sc[i >> 1] * cL);
+              float s1, e1, s2, e2;
+              if (L < 2) {
+                two_sum(h[i], x, s1, e1);
+                h[i] = s1;
+                two_sum(mi[i], e1, s2, e2);
+              } else {
+                two_sum(mi[i], x, s2, e2);
+              }
+              mi[i] = s2;
+              lo[i] += e2;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float s1, e1, s2, e2;
+          two_sum(h[i], mi[i], s1, e1);
+          two_sum(e1, lo[i], s2, e2);
+          h[i] = s1;
+          mi[i] = s2;
+          lo[i] = e2;
+        }
+      }
+      if (stop) break;
+      // epilogue of the tile: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value.
+      // Column maxima from lanes 0-7, shuffled while every lane is present.
+      int sx[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) sx[jj] = __shfl_sync(0xffffffffu, Sc, jj);
+      if (row >= g.M || g.rmask.hit(row)) continue;
+      double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)row * g.ldc + c8;
+      const bool neg = g.neg != 0;
+      double2 cv[8];
+      if (g.beta) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[jj] : make_double2(0, 0);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int cc = c8 + jj;
+        const int ex = Rm + sx[jj];
+        if (cc >= g.N || g.cmask.hit(cc)) continue;
+        double vv[2];
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const int i = 2 * jj + part;
+          float s1, e1;
+          two_sum(h[i], mi[i], s1, e1);
+          vv[part] = f2d_scaled(s1, ex, neg) + f2d_scaled(e1 + lo[i], ex, neg);
+        }
+        double2 v = make_double2(vv[0], vv[1]);
+        if (g.beta) v = cadd(v, cv[jj]);
+        crow[jj] = v;
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPCols) : "memory");
+  }
+}
+
 }  // namespace
 
 // opt the GEMM kernel in to > 48 KB of dynamic shared memory on the current
 // device (done when a plan is set up, outside any stream capture)
 cudaError_t emu_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCSmemBytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_gemm_emu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
 }
@@ -797,9 +815,9 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
     k_gemm_emu_persist<<<gp, 320, kPSmemBytes, st>>>(gd, ed, d0, d1, blocks, arena, stride, words, ints, wstride,
                                                      istride, status);
   } else {
-    const dim3 gg((unsigned)blocks, (unsigned)batch);
-    k_gemm_emu_tc<<<gg, 128, kTcSmemBytes, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride,
-                                                 status);
+    const dim3 gp((unsigned)std::min(blocks, std::max(num_sms, 1)), (unsigned)batch);
+    k_gemm_emu_chunked<<<gp, 320, kCSmemBytes, st>>>(gd, ed, d0, d1, blocks, arena, stride, words, ints, wstride,
+                                                     istride, status);
   }
   return cudaGetLastError();
 }
