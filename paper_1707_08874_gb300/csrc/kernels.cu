@@ -256,24 +256,20 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
       ww[t] = ej[t] == c ? inv : prow[ej[t]];
       ff[t] = fcol[ei[t]];
     }
+    // One FMA sequence for every entry (a divergent branch would cost each
+    // warp both paths on the FP64 pipe): v - f w with
+    //   pivot row (i == c):     v = scaled pivot row, f = 0
+    //   pivot column (j == c):  v = 0, w = inv  (-> -f inv)
 #pragma unroll
     for (int t = 0; t < kPanelSlots; ++t) {
       if (ei[t] < 0) continue;
-      const int i = ei[t], j = ej[t];
-      T v;
-      if (i == c) {
-        v = ww[t];  // the scaled pivot row (inv on the diagonal)
-      } else if (j == c) {
-        v.x = -(ff[t].x * inv.x - ff[t].y * inv.y);
-        v.y = -(ff[t].x * inv.y + ff[t].y * inv.x);
-      } else {
-        v = vv[t];
-        const T f = ff[t], w = ww[t];
-        v.x = fma(-f.x, w.x, v.x);
-        v.x = fma(f.y, w.y, v.x);
-        v.y = fma(-f.x, w.y, v.y);
-        v.y = fma(-f.y, w.x, v.y);
-      }
+      const bool prow_i = ei[t] == c, pcol_j = ej[t] == c;
+      T v = prow_i ? ww[t] : (pcol_j ? T{0, 0} : vv[t]);
+      const T f = prow_i ? T{0, 0} : ff[t], w = ww[t];
+      v.x = fma(-f.x, w.x, v.x);
+      v.x = fma(f.y, w.y, v.x);
+      v.y = fma(-f.x, w.y, v.y);
+      v.y = fma(-f.y, w.x, v.y);
       vv[t] = v;
     }
 #pragma unroll
