@@ -100,14 +100,13 @@ __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, cons
 // 1e-13 * max|block| (1e-6 for FP32 fronts) records CL_ERR_SINGULAR
 // (supernode, column).
 //
-// GB300's FP64 pipe retires ~2 lanes per cycle per SM, so every FP64 warp
-// instruction should carry 32 live lanes: the update phase walks the bp x bp
-// entries linearly (thread t takes entries t, t + 256, ...).  Per column one
-// warp picks the pivot (warp reductions), forms the reciprocal, the
-// multipliers and the scaled pivot row; two block barriers per column.
+// A scalar FP64 warp instruction occupies a scheduler's FP64 unit for ~64
+// cycles on this part (0.5 lanes per cycle, ~1.7 per SM), so every FP64 warp
+// instruction should carry 32 live lanes and one code path: the update walks
+// the bp x bp entries linearly with one FMA sequence per entry.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPanel = 48;
-constexpr int kPanelSlots = (kMaxPanel * kMaxPanel + 255) / 256;  // entries per thread
+constexpr int kPanelSlots7 = (kMaxPanel * kMaxPanel + 223) / 224;  // update entries per thread of warps 1-7
 
 __device__ __forceinline__ long long mag_key(double2 v) {
   const long long a = __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFll;
@@ -169,6 +168,43 @@ __device__ __forceinline__ T reciprocal(T pv) {
   return inv;
 }
 
+// pivot of column c among logical rows c..bp-1 (one warp): the largest
+// magnitude key, the lowest row on ties
+template <typename T>
+__device__ __forceinline__ int pivot_row(const T (*S)[kMaxPanel + 1], const int* rmap, int c, int bp, int lane) {
+  unsigned key = 0;
+  int bi = 0x7fffffff;
+  for (int i = c + lane; i < bp; i += 32) {
+    const unsigned k = key32(S[rmap[i]][c]);
+    if (bi == 0x7fffffff || k > key) {
+      key = k;
+      bi = i;
+    }
+  }
+  const unsigned kmax = __reduce_max_sync(0xffffffffu, bi != 0x7fffffff ? key : 0u);
+  return (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && key == kmax) ? (unsigned)bi : 0x7fffffffu);
+}
+
+// entry update v - f w of Gauss-Jordan step c, one FMA sequence for every
+// entry (a divergent branch would cost each warp both paths on the FP64
+// pipe): pivot row (i == c): v = scaled pivot row, f = 0; pivot column
+// (j == c): v = 0, w = inv (-> -f inv)
+template <typename T>
+__device__ __forceinline__ T gj_entry(T v, T f, T w, bool prow_i, bool pcol_j) {
+  T r = prow_i ? w : (pcol_j ? T{0, 0} : v);
+  if (prow_i) f = T{0, 0};
+  r.x = fma(-f.x, w.x, r.x);
+  r.x = fma(f.y, w.y, r.x);
+  r.y = fma(-f.x, w.y, r.y);
+  r.y = fma(-f.y, w.x, r.y);
+  return r;
+}
+
+// Column look-ahead: while warps 1-7 apply step c to every entry outside
+// column c+1, warp 0 applies it to column c+1, picks that column's pivot and
+// forms its reciprocal, so the serial pivot chain of step c+1 overlaps the
+// bulk of step c.  Per column: warp 0 records the interchange and forms the
+// multipliers and the scaled pivot row, barrier, update, barrier.
 template <typename T, typename R>
 __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
                                                        int64_t stride, int* __restrict__ status) {
@@ -181,19 +217,12 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   __shared__ long long wmax[8];
   __shared__ T sinv;
   __shared__ long long sthr;
-  // this thread's entries (linear order), loaded once
-  int ei[kPanelSlots], ej[kPanelSlots];
   long long km = 0;
-#pragma unroll
-  for (int t = 0; t < kPanelSlots; ++t) {
-    const int e = tid + 256 * t;
-    ei[t] = e < nel ? e / bp : -1;
-    ej[t] = e < nel ? e - ei[t] * bp : 0;
-    if (e < nel) {
-      const T v = A[(int64_t)ei[t] * d.ld + ej[t]];
-      S[ei[t]][ej[t]] = v;
-      km = max(km, mag_key(v));
-    }
+  for (int e = tid; e < nel; e += 256) {
+    const int i = e / bp, j = e - i * bp;
+    const T v = A[(int64_t)i * d.ld + j];
+    S[i][j] = v;
+    km = max(km, mag_key(v));
   }
   if (tid < bp) rmap[tid] = tid;
 #pragma unroll
@@ -208,23 +237,25 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   }
   __syncthreads();
   const long long thr = sthr;
+  // update entries of warps 1-7 (thread u takes entries u, u + 224, ...)
+  const int u = tid - 32;
+  int ei[kPanelSlots7], ej[kPanelSlots7];
+#pragma unroll
+  for (int t = 0; t < kPanelSlots7; ++t) {
+    const int e = u + 224 * t;
+    ei[t] = (u >= 0 && e < nel) ? e / bp : -1;
+    ej[t] = ei[t] >= 0 ? e - ei[t] * bp : 0;
+  }
+  int pr = 0;
+  T inv{0, 0};
+  if (warp == 0) {
+    pr = pivot_row(S, rmap, 0, bp, lane);
+    inv = reciprocal<T, R>(S[rmap[pr]][0]);
+  }
   for (int c = 0; c < bp; ++c) {
     if (warp == 0) {
-      // (1) pivot among logical rows c..bp-1, lowest row on ties
-      unsigned key = 0;
-      int bi = 0x7fffffff;
-      for (int i = c + lane; i < bp; i += 32) {
-        const unsigned k = key32(S[rmap[i]][c]);
-        if (bi == 0x7fffffff || k > key) {
-          key = k;
-          bi = i;
-        }
-      }
-      const unsigned kmax = __reduce_max_sync(0xffffffffu, bi != 0x7fffffff ? key : 0u);
-      const int pr = (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && key == kmax) ? (unsigned)bi : 0x7fffffffu);
       const int pc = rmap[pr];
       const T pv = S[pc][c];
-      const T inv = reciprocal<T, R>(pv);
       __syncwarp();
       if (lane == 0) {
         piv[c] = pr;
@@ -235,46 +266,48 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
         sinv = inv;
       }
       __syncwarp();
-      // (2) multipliers (column c of every logical row) and the scaled pivot row
+      // multipliers (column c of every logical row) and the scaled pivot row
       for (int i = lane; i < bp; i += 32) {
         fcol[i] = S[rmap[i]][c];
         prow[i] = (i == c) ? inv : cmul(S[pc][i], inv);
       }
     }
     __syncthreads();
-    // (3) eliminate column c from every other logical row; row c <- pivot row.
-    // All loads first, then four FMAs per entry (independent across entries),
-    // then the stores.
-    const T inv = sinv;
-    T vv[kPanelSlots], ww[kPanelSlots], ff[kPanelSlots];
-    int rp[kPanelSlots];
+    const int cn = c + 1;
+    if (warp == 0) {
+      if (cn < bp) {
+        // step c on column c+1, then that column's pivot and reciprocal
+        const T w = prow[cn];
+        for (int i = lane; i < bp; i += 32) {
+          const int r = rmap[i];
+          S[r][cn] = gj_entry(S[r][cn], fcol[i], w, i == c, false);
+        }
+        __syncwarp();
+        pr = pivot_row(S, rmap, cn, bp, lane);
+        inv = reciprocal<T, R>(S[rmap[pr]][cn]);
+      }
+    } else {
+      // step c on every other entry: all loads, then the FMAs, then the stores
+      const T invc = sinv;
+      T vv[kPanelSlots7], ww[kPanelSlots7], ff[kPanelSlots7];
+      int rp[kPanelSlots7];
 #pragma unroll
-    for (int t = 0; t < kPanelSlots; ++t) {
-      if (ei[t] < 0) continue;
-      rp[t] = rmap[ei[t]];
-      vv[t] = S[rp[t]][ej[t]];
-      ww[t] = ej[t] == c ? inv : prow[ej[t]];
-      ff[t] = fcol[ei[t]];
+      for (int t = 0; t < kPanelSlots7; ++t) {
+        if (ei[t] < 0 || ej[t] == cn) continue;
+        rp[t] = rmap[ei[t]];
+        vv[t] = S[rp[t]][ej[t]];
+        ww[t] = ej[t] == c ? invc : prow[ej[t]];
+        ff[t] = fcol[ei[t]];
+      }
+#pragma unroll
+      for (int t = 0; t < kPanelSlots7; ++t) {
+        if (ei[t] < 0 || ej[t] == cn) continue;
+        vv[t] = gj_entry(vv[t], ff[t], ww[t], ei[t] == c, ej[t] == c);
+      }
+#pragma unroll
+      for (int t = 0; t < kPanelSlots7; ++t)
+        if (ei[t] >= 0 && ej[t] != cn) S[rp[t]][ej[t]] = vv[t];
     }
-    // One FMA sequence for every entry (a divergent branch would cost each
-    // warp both paths on the FP64 pipe): v - f w with
-    //   pivot row (i == c):     v = scaled pivot row, f = 0
-    //   pivot column (j == c):  v = 0, w = inv  (-> -f inv)
-#pragma unroll
-    for (int t = 0; t < kPanelSlots; ++t) {
-      if (ei[t] < 0) continue;
-      const bool prow_i = ei[t] == c, pcol_j = ej[t] == c;
-      T v = prow_i ? ww[t] : (pcol_j ? T{0, 0} : vv[t]);
-      const T f = prow_i ? T{0, 0} : ff[t], w = ww[t];
-      v.x = fma(-f.x, w.x, v.x);
-      v.x = fma(f.y, w.y, v.x);
-      v.y = fma(-f.x, w.y, v.y);
-      v.y = fma(-f.y, w.x, v.y);
-      vv[t] = v;
-    }
-#pragma unroll
-    for (int t = 0; t < kPanelSlots; ++t)
-      if (ei[t] >= 0) S[rp[t]][ej[t]] = vv[t];
     __syncthreads();
   }
   // logical rows are in rmap order; the row interchanges are undone on the
@@ -288,9 +321,10 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int t = 0; t < kPanelSlots; ++t)
-    if (ei[t] >= 0) A[(int64_t)ei[t] * d.ld + ej[t]] = S[rmap[ei[t]]][qcol[ej[t]]];
+  for (int e = tid; e < nel; e += 256) {
+    const int i = e / bp, j = e - i * bp;
+    A[(int64_t)i * d.ld + j] = S[rmap[i]][qcol[j]];
+  }
 }
 
 // ---------------------------------------------------------------------------
