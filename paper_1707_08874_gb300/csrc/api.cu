@@ -114,6 +114,8 @@ int setup_device(Plan& p) {
     p.streams[0] = s0;
     if ((e = cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, lo)) != cudaSuccess) return cuda_status(e);
     p.streams[1] = s1;
+    p.prio_lo = lo;
+    p.prio_hi = hi;
     cudaEvent_t ev = nullptr;
     for (void** slot : {&p.fork_event, &p.join_events[0], &p.join_events[1]}) {
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);

@@ -806,27 +806,24 @@ cudaError_t emu_prepare() {
 
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool single_chunk, int num_sms, cudaStream_t st) {
+                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, int prio) {
   const dim3 gs((unsigned)((items + 7) / 8), (unsigned)batch);
-  k_emu_split<<<gs, 256, 0, st>>>(gd, ed, d0, d1, arena, stride, words, ints, wstride, istride, items);
-  if (single_chunk) {
-    // blocks = output tiles of the launch; one persistent CTA per SM
-    const dim3 gp((unsigned)std::min(blocks, std::max(num_sms, 1)), (unsigned)batch);
-    k_gemm_emu_persist<<<gp, 320, kPSmemBytes, st>>>(gd, ed, d0, d1, blocks, arena, stride, words, ints, wstride,
-                                                     istride, status);
-  } else {
-    const dim3 gp((unsigned)std::min(blocks, std::max(num_sms, 1)), (unsigned)batch);
-    k_gemm_emu_chunked<<<gp, 320, kCSmemBytes, st>>>(gd, ed, d0, d1, blocks, arena, stride, words, ints, wstride,
-                                                     istride, status);
-  }
-  return cudaGetLastError();
+  cudaError_t e = launch_k(k_emu_split, gs, dim3(256), 0, st, prio, gd, ed, d0, d1, (const double2*)arena, stride,
+                           words, ints, wstride, istride, items);
+  if (e != cudaSuccess) return e;
+  const dim3 gp((unsigned)std::min(blocks, std::max(max_ctas, 1)), (unsigned)batch);
+  if (single_chunk)  // blocks = output tiles of the launch; persistent CTAs over ranges of tiles
+    return launch_k(k_gemm_emu_persist, gp, dim3(320), kPSmemBytes, st, prio, gd, ed, d0, d1, blocks, arena, stride,
+                    (const unsigned*)words, (const int*)ints, wstride, istride, status);
+  return launch_k(k_gemm_emu_chunked, gp, dim3(320), kCSmemBytes, st, prio, gd, ed, d0, d1, blocks, arena, stride,
+                  (const unsigned*)words, (const int*)ints, wstride, istride, status);
 }
 
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
   const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
   return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.batch, arena, p.arena_elems,
                     p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, p.num_sms,
-                    st);
+                    st, op_priority(p, op));
 }
 
 }  // namespace cl

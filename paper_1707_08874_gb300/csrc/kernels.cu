@@ -437,24 +437,23 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
   const int64_t stride = p.arena_elems;
   const dim3 grid1((unsigned)op.blocks, (unsigned)p.batch);
   const LatticeGeo g{p.Ns, p.Nt, p.V};
+  const int prio = op_priority(p, op);
   switch (op.kind) {
     case OP_ZERO:
       return cudaMemset2DAsync(arena, (size_t)stride * sizeof(T), 0, (size_t)p.pool_elems * sizeof(T),
                                (size_t)p.batch, st);
     case OP_ASSEMBLE:
-      k_assemble<T><<<grid1, 128, 0, st>>>(links, arena, stride, p.d_off, p.d_ld, g, m, mu);
-      break;
+      return launch_k(k_assemble<T>, grid1, dim3(128), 0, st, prio, links, arena, stride, p.d_off, p.d_ld, g, m, mu);
     case OP_EXTADD:
-      k_extend_add<T><<<grid1, 256, 0, st>>>(p.d_extadd, op.d0, op.d1, p.d_maps, arena, stride);
-      break;
+      return launch_k(k_extend_add<T>, grid1, dim3(256), 0, st, prio, p.d_extadd, op.d0, op.d1, p.d_maps, arena,
+                      stride);
     case OP_PANEL:
-      k_panel_inverse<T, R><<<grid1, 256, 0, st>>>(p.d_panels, op.d0, arena, stride, p.d_status);
-      break;
+      return launch_k(k_panel_inverse<T, R>, grid1, dim3(256), 0, st, prio, p.d_panels, op.d0, arena, stride,
+                      p.d_status);
     case OP_GEMM:
       return launch_gemm(p, op, arena, st);
     case OP_COPY:
-      k_copy<T><<<grid1, 256, 0, st>>>(p.d_copies, op.d0, op.d1, arena, stride);
-      break;
+      return launch_k(k_copy<T>, grid1, dim3(256), 0, st, prio, p.d_copies, op.d0, op.d1, arena, stride);
     case OP_GATHER:
       k_gather<T><<<grid1, 256, 0, st>>>(p.d_gather, op.d0, op.d1, p.d_maps, arena, stride);
       break;

@@ -6,6 +6,33 @@
 
 namespace cl {
 
+// Scheduling priority of an op's launches.  With the two-stream
+// factorisation the panel chain (stream 0) runs at the device's highest
+// priority and the bulk updates (stream 1) at its lowest; the priority is
+// given as a launch attribute, which stream capture records in the graph's
+// kernel nodes (a stream's own priority does not carry into a graph).
+constexpr int kNoPrio = 0x7fffffff;
+inline int op_priority(const Plan& p, const Op& op) {
+  return p.streams[1] ? (op.stream ? p.prio_lo : p.prio_hi) : kNoPrio;
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int prio,
+                     Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr{};
+  if (prio != kNoPrio) {
+    attr.id = cudaLaunchAttributePriority;
+    attr.val.priority = prio;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // one scheduled operation of the factorisation / selected inversion
 template <typename T, typename R>
 cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links, double m, double mu,
@@ -18,11 +45,11 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 cudaError_t emu_prepare();
 // split pass + tcgen05 digit GEMM over descriptors [d0, d1); blocks = output
-// tiles (128 x 16 complex); single_chunk (every K <= 32): persistent kernel
-// on min(blocks, num_sms) CTAs
+// tiles (128 x 16 complex); persistent kernels (single_chunk: every K <= 32)
+// on min(blocks, max_ctas) CTAs, each a contiguous range of tiles
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool single_chunk, int num_sms, cudaStream_t st);
+                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, int prio = kNoPrio);
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

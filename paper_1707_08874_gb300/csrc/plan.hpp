@@ -185,6 +185,7 @@ struct Plan {
   std::vector<void*> op_events;  // per factor op (nullptr when it does not signal)
   void* fork_event = nullptr;
   void* join_events[2] = {nullptr, nullptr};
+  int prio_lo = 0, prio_hi = 0;  // the device's lowest / highest stream priority
 };
 
 // kernel families for profiling records
