@@ -478,20 +478,21 @@ __global__ void __launch_bounds__(320, 1)
             }
           }
         }
-        {  // levels 4-6
+        {  // levels 4-6, at most 2^-32 of the leading level: summed in FP32
+           // (rounding below 2^-53 of it), then one error-free addition
           uint32_t v[3][16];
 #pragma unroll
           for (int L = 0; L < 3; ++L) tmem_ld16_issue(ta + 32 * (L + 4), v[L]);
           tmem_ld_wait();
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-#pragma unroll
-            for (int L = 0; L < 3; ++L) {
-              float s2, e2;
-              two_sum(mi[k], __uint_as_float(v[L][k]) * __int_as_float((127 - 16 - 8 * (L + 4)) << 23), s2, e2);
-              mi[k] = s2;
-              lo[k] += e2;
-            }
+          for (int k = 0; k < 16; ++k) {
+            const float x = fmaf(__uint_as_float(v[2][k]), 0x1p-64f,
+                                 fmaf(__uint_as_float(v[1][k]), 0x1p-56f, __uint_as_float(v[0][k]) * 0x1p-48f));
+            float s2, e2;
+            two_sum(mi[k], x, s2, e2);
+            mi[k] = s2;
+            lo[k] += e2;
+          }
         }
         if (hh == 1) {
           tc_fence_before();
@@ -722,23 +723,35 @@ __global__ void __launch_bounds__(320, 1)
             tc_fence_before();
             mbar_arrive(bar(8 + set));  // accumulator set drained
           }
-#pragma unroll
-          for (int l = 0; l < nl; ++l) {
-            const int L = L0 + l;
-            const float cL = __int_as_float((127 - 8 * L) << 23);  // 2^{-8L}
+          if (b4) {  // levels 4-6 (<= 2^-32 of the leading level): FP32 sum, one error-free addition
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const float x = __uint_as_float(v[l][i]) * (sc[i >> 1] * cL);
-              float s1, e1, s2, e2;
-              if (L < 2) {
-                two_sum(h[i], x, s1, e1);
-                h[i] = s1;
-                two_sum(mi[i], e1, s2, e2);
-              } else {
-                two_sum(mi[i], x, s2, e2);
-              }
+              const float c = sc[i >> 1];
+              const float x = fmaf(__uint_as_float(v[2][i]), c * 0x1p-48f,
+                                   fmaf(__uint_as_float(v[1][i]), c * 0x1p-40f, __uint_as_float(v[0][i]) * (c * 0x1p-32f)));
+              float s2, e2;
+              two_sum(mi[i], x, s2, e2);
               mi[i] = s2;
               lo[i] += e2;
+            }
+          } else {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const float cL = __int_as_float((127 - 8 * l) << 23);  // 2^{-8L}
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const float x = __uint_as_float(v[l][i]) * (sc[i >> 1] * cL);
+                float s1, e1, s2, e2;
+                if (l < 2) {
+                  two_sum(h[i], x, s1, e1);
+                  h[i] = s1;
+                  two_sum(mi[i], e1, s2, e2);
+                } else {
+                  two_sum(mi[i], x, s2, e2);
+                }
+                mi[i] = s2;
+                lo[i] += e2;
+              }
             }
           }
         }
