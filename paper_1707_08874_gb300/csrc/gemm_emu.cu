@@ -263,9 +263,10 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 //                  (7 levels x 32 columns at TMEM columns 0 and 256), so the
 //                  MMAs of tile i+1 run while tile i is folded and written;
 //   warps 2-9      fold (thread = row) and FP64 epilogue in two groups of four
-//                  warps taking alternate tiles (accumulator set = tile
-//                  parity), so one group's FP32 fold overlaps the other's
-//                  FP64 write-back; the C row segment is prefetched into L1.
+//                  warps, each owning half of every tile's columns, so a
+//                  tile's fold and write-back take half as long as with one
+//                  group per tile (the panel chain's small launches have one
+//                  tile per CTA); the C row segment is prefetched into L1.
 // With one chunk the row / column exponents are the chunk's own, the fold
 // scale is 2^{-16-8L} and the output exponent e_row + f_col.
 constexpr int kPA = 16384;  // bytes: one A digit tile, 128 rows x 64 real k
@@ -334,8 +335,8 @@ __global__ void __launch_bounds__(320, 1)
   }
   if (tid == 32) {
     for (int i = 0; i < 7; ++i) mbar_init(bar(i), 1);
-    mbar_init(bar(7), 128);  // one 4-warp epilogue group per accumulator set
-    mbar_init(bar(8), 128);
+    mbar_init(bar(7), 256);  // both fold groups drain an accumulator set
+    mbar_init(bar(8), 256);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -424,10 +425,10 @@ __global__ void __launch_bounds__(320, 1)
       if (*abort_flag && last >= 0) mbar_wait(bar(5 + (last & 1)), (last >> 1) & 1);  // MMAs in flight
     }
     __syncwarp();
-  } else {  // ---- fold and epilogue: warps 2-5 take even tiles, 6-9 odd; thread = row
+  } else {  // ---- fold and epilogue: thread = row; group g (warps 2-5, 6-9) owns complex columns 8g .. 8g+7
     const int grp = (warp - 2) >> 2, q4 = warp & 3, rl = q4 * 32 + lane;
     int prev = -1, erow = 0;
-    for (int i = grp; i < n; i += 2) {
+    for (int i = 0; i < n; ++i) {
       __syncwarp();
       if (__any_sync(0xffffffffu, *abort_flag)) break;
       const TileRef tr = tile_ref(gd, d0, d1, t0 + i);
@@ -442,10 +443,8 @@ __global__ void __launch_bounds__(320, 1)
       const bool row_ok = r < g.M && !g.rmask.hit(r);
       const bool neg = g.neg != 0;
       double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)r * g.ldc + col0;
-      if (row_ok && g.beta) {  // C row segment (256 bytes) into L1 while the MMAs run
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow));
-        if (col0 + 8 < g.N) asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + 8));
-      }
+      if (row_ok && g.beta && col0 + 8 * grp < g.N)  // this group's C row segment into L1 while the MMAs run
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + 8 * grp));
       const int s = i & 1, u = i >> 1;
       const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
@@ -454,9 +453,8 @@ __global__ void __launch_bounds__(320, 1)
         break;
       }
       tc_fence_after();
-      // two halves of 8 complex columns (16 TMEM columns per level)
-#pragma unroll 1
-      for (int hh = 0; hh < 2; ++hh) {
+      {  // this group's 8 complex columns (16 TMEM columns per level)
+        const int hh = grp;
         float h[16], mi[16], lo[16];
         const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + 16 * hh;
         {  // levels 0-3: four loads, one wait
@@ -494,10 +492,8 @@ __global__ void __launch_bounds__(320, 1)
             lo[k] += e2;
           }
         }
-        if (hh == 1) {
-          tc_fence_before();
-          mbar_arrive(bar(7 + s));  // accumulator set s may be overwritten
-        }
+        tc_fence_before();
+        mbar_arrive(bar(7 + s));  // this group is done with accumulator set s
         if (!row_ok) continue;
         const int c8 = col0 + 8 * hh;
         int fe[8];
