@@ -37,7 +37,10 @@ METRIC = "fermion-drift evals/sec on 8^3x4 (FP64 vs mixed, stated drift error); 
 NS, NT, M, MU = 8, 4, 0.05, 0.25
 # DRAM bytes per launch of the dominant kernel from an ncu capture of this
 # workload (profiles/gemm_fp64_8x4.md); None until captured for the current kernel.
-NCU_TRAFFIC = {}
+# DRAM bytes per digit-GEMM launch (dram__bytes_read + dram__bytes_write,
+# averaged over the 323 GEMM launches of one 8^3x4 evaluation, ncu, cold
+# cache); valid for the kernels it was taken on, keyed by (precision, batch)
+NCU_TRAFFIC = {("fp64_emu", 1): 60.55e6}
 
 
 def measured_bf16_tflops():
