@@ -68,6 +68,7 @@ int setup_device(Plan& p) {
   if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) != cudaSuccess) return CL_ERR_CUDA;
   size_t total = 0;
   cudaError_t e;
+  if ((e = cl::panel_prepare()) != cudaSuccess) return cuda_status(e);
   const size_t arena = (size_t)p.arena_elems * p.batch * elem_bytes(p);
   if ((e = cudaMalloc(&p.d_arena, arena)) != cudaSuccess) return cuda_status(e);
   total += arena;

@@ -103,10 +103,11 @@ __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, cons
 // A scalar FP64 warp instruction occupies a scheduler's FP64 unit for ~64
 // cycles on this part (0.5 lanes per cycle, ~1.7 per SM), so every FP64 warp
 // instruction should carry 32 live lanes and one code path: the update walks
-// the bp x bp entries linearly with one FMA sequence per entry.
+// the bp x bp entries linearly with one FMA sequence per entry, and the
+// kernel is instantiated per maximum panel width (24, 48) so that its update
+// loop holds only the slots that the width can fill.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPanel = 48;
-constexpr int kPanelSlots7 = (kMaxPanel * kMaxPanel + 223) / 224;  // update entries per thread of warps 1-7
 
 __device__ __forceinline__ long long mag_key(double2 v) {
   const long long a = __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFll;
@@ -168,14 +169,18 @@ __device__ __forceinline__ T reciprocal(T pv) {
   return inv;
 }
 
-// pivot of column c among logical rows c..bp-1 (one warp): the largest
-// magnitude key, the lowest row on ties
-template <typename T>
-__device__ __forceinline__ int pivot_row(const T (*S)[kMaxPanel + 1], const int* rmap, int c, int bp, int lane) {
+// pivot among logical rows c0..bp-1 of a column whose entry of logical row
+// lane + 32 h the calling warp holds in v[h]: the largest magnitude key, the
+// lowest row on ties
+template <typename T, int H>
+__device__ __forceinline__ int pivot_row(const T (&v)[H], int c0, int bp, int lane) {
   unsigned key = 0;
   int bi = 0x7fffffff;
-  for (int i = c + lane; i < bp; i += 32) {
-    const unsigned k = key32(S[rmap[i]][c]);
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const int i = lane + 32 * h;
+    if (i < c0 || i >= bp) continue;
+    const unsigned k = key32(v[h]);
     if (bi == 0x7fffffff || k > key) {
       key = k;
       bi = i;
@@ -200,31 +205,44 @@ __device__ __forceinline__ T gj_entry(T v, T f, T w, bool prow_i, bool pcol_j) {
   return r;
 }
 
+// logical rows a and b exchanged
+__device__ __forceinline__ int swap_index(int i, int a, int b) { return i == a ? b : (i == b ? a : i); }
+
+template <typename T>
+constexpr size_t panel_smem_bytes(int mp) {
+  return 2 * (size_t)mp * (mp + 1) * sizeof(T);
+}
+
+// The block lives in two shared-memory copies: step c reads copy c & 1 and
+// writes the other, so one barrier per column suffices and warp 0 can read
+// the pre-step values of any row while warps 1-7 write the step's results.
 // Column look-ahead: while warps 1-7 apply step c to every entry outside
-// column c+1, warp 0 applies it to column c+1, picks that column's pivot and
-// forms its reciprocal, so the serial pivot chain of step c+1 overlaps the
-// bulk of step c.  Per column: warp 0 records the interchange and forms the
-// multipliers and the scaled pivot row, barrier, update, barrier.
-template <typename T, typename R>
+// column c+1, warp 0 applies it to column c+1, picks that column's pivot,
+// applies step c to the pivot row, forms the reciprocal, and leaves step
+// c+1's row map, multipliers and scaled pivot row for the next column.
+// The update warps are ranked so that warp 4, which shares a scheduler with
+// warp 0, takes the last (least filled) entries.
+template <typename T, typename R, int MP>
 __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
                                                        int64_t stride, int* __restrict__ status) {
+  constexpr int kSlots = (MP * MP + 223) / 224;  // update entries per thread of warps 1-7
+  constexpr int H = (MP + 31) / 32;              // column entries per lane of warp 0
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  T(*S)[MP][MP + 1] = reinterpret_cast<T(*)[MP][MP + 1]>(panel_smem);  // S[2]; logical row i in S[.][rmap[.][i]]
+  __shared__ T fcol[2][MP], prow[2][MP], sinv[2];
+  __shared__ int rmap[2][MP], piv[MP], qcol[MP];
+  __shared__ long long wmax[8];
+  __shared__ long long sthr;
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
   const int bp = d.bp, nel = bp * bp, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ T S[kMaxPanel][kMaxPanel + 1];  // physical rows; logical row i lives in S[rmap[i]]
-  __shared__ T fcol[kMaxPanel], prow[kMaxPanel];
-  __shared__ int rmap[kMaxPanel], piv[kMaxPanel], qcol[kMaxPanel];
-  __shared__ long long wmax[8];
-  __shared__ T sinv;
-  __shared__ long long sthr;
   long long km = 0;
   for (int e = tid; e < nel; e += 256) {
     const int i = e / bp, j = e - i * bp;
     const T v = A[(int64_t)i * d.ld + j];
-    S[i][j] = v;
+    S[0][i][j] = v;
     km = max(km, mag_key(v));
   }
-  if (tid < bp) rmap[tid] = tid;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
   if (lane == 0) wmax[warp] = km;
@@ -237,76 +255,120 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   }
   __syncthreads();
   const long long thr = sthr;
-  // update entries of warps 1-7 (thread u takes entries u, u + 224, ...)
-  const int u = tid - 32;
-  int ei[kPanelSlots7], ej[kPanelSlots7];
-#pragma unroll
-  for (int t = 0; t < kPanelSlots7; ++t) {
-    const int e = u + 224 * t;
-    ei[t] = (u >= 0 && e < nel) ? e / bp : -1;
-    ej[t] = ei[t] >= 0 ? e - ei[t] * bp : 0;
-  }
-  int pr = 0;
-  T inv{0, 0};
+  // step 0's pivot, row map, multipliers and scaled pivot row
   if (warp == 0) {
-    pr = pivot_row(S, rmap, 0, bp, lane);
-    inv = reciprocal<T, R>(S[rmap[pr]][0]);
-  }
-  for (int c = 0; c < bp; ++c) {
-    if (warp == 0) {
-      const int pc = rmap[pr];
-      const T pv = S[pc][c];
-      __syncwarp();
-      if (lane == 0) {
-        piv[c] = pr;
-        rmap[pr] = rmap[c];
-        rmap[c] = pc;
-        const long long best = mag_key(pv);
-        if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + c);
-        sinv = inv;
-      }
-      __syncwarp();
-      // multipliers (column c of every logical row) and the scaled pivot row
-      for (int i = lane; i < bp; i += 32) {
-        fcol[i] = S[rmap[i]][c];
-        prow[i] = (i == c) ? inv : cmul(S[pc][i], inv);
+    T v[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = lane + 32 * h;
+      v[h] = i < bp ? S[0][i][0] : T{0, 0};
+    }
+    const int pr = pivot_row(v, 0, bp, lane);
+    const T pv = S[0][pr][0];
+    const T inv = reciprocal<T, R>(pv);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = lane + 32 * h;
+      if (i < bp) {
+        const int s = swap_index(i, 0, pr);
+        rmap[0][i] = s;
+        fcol[0][i] = S[0][s][0];
+        prow[0][i] = i == 0 ? inv : cmul(S[0][pr][i], inv);
       }
     }
-    __syncthreads();
-    const int cn = c + 1;
+    if (lane == 0) {
+      piv[0] = pr;
+      sinv[0] = inv;
+      const long long best = mag_key(pv);
+      if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0);
+    }
+  }
+  // update entries of warps 1-7: the thread of rank q takes entries q, q + 224, ...
+  const int rank = warp == 0 ? 0 : (warp < 4 ? warp - 1 : (warp == 4 ? 6 : warp - 2));
+  const int u = rank * 32 + lane;
+  int ei[kSlots], ej[kSlots];
+#pragma unroll
+  for (int t = 0; t < kSlots; ++t) {
+    const int e = u + 224 * t;
+    ei[t] = (warp != 0 && e < nel) ? e / bp : -1;
+    ej[t] = ei[t] >= 0 ? e - ei[t] * bp : 0;
+  }
+  __syncthreads();
+  for (int c = 0; c < bp; ++c) {
+    const int cur = c & 1, nxt = cur ^ 1, cn = c + 1;
     if (warp == 0) {
       if (cn < bp) {
-        // step c on column c+1, then that column's pivot and reciprocal
-        const T w = prow[cn];
-        for (int i = lane; i < bp; i += 32) {
-          const int r = rmap[i];
-          S[r][cn] = gj_entry(S[r][cn], fcol[i], w, i == c, false);
+        // step c on column c+1 (logical row lane + 32 h in v[h])
+        const T wc = prow[cur][cn];
+        T v[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const int i = lane + 32 * h;
+          v[h] = T{0, 0};
+          if (i < bp) {
+            const int r = rmap[cur][i];
+            v[h] = gj_entry(S[cur][r][cn], fcol[cur][i], wc, i == c, false);
+            S[nxt][r][cn] = v[h];
+          }
         }
-        __syncwarp();
-        pr = pivot_row(S, rmap, cn, bp, lane);
-        inv = reciprocal<T, R>(S[rmap[pr]][cn]);
+        const int pr = pivot_row(v, cn, bp, lane);
+        T mine = v[0];
+#pragma unroll
+        for (int h = 1; h < H; ++h)
+          if ((pr >> 5) == h) mine = v[h];
+        T pv;
+        pv.x = __shfl_sync(0xffffffffu, mine.x, pr & 31);
+        pv.y = __shfl_sync(0xffffffffu, mine.y, pr & 31);
+        // step c on the pivot row (logical row pr > c), outside column c+1
+        const int rp = rmap[cur][pr];
+        const T fp = fcol[cur][pr], invc = sinv[cur];
+        T row[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const int j = lane + 32 * h;
+          row[h] = T{0, 0};
+          if (j < bp && j != cn) row[h] = gj_entry(S[cur][rp][j], fp, j == c ? invc : prow[cur][j], false, j == c);
+        }
+        const T inv = reciprocal<T, R>(pv);
+        // step c+1: logical rows c+1 and pr exchanged
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const int j = lane + 32 * h;
+          if (j < bp) {
+            rmap[nxt][j] = rmap[cur][swap_index(j, cn, pr)];
+            prow[nxt][j] = j == cn ? inv : cmul(row[h], inv);
+            fcol[nxt][swap_index(j, cn, pr)] = v[h];
+          }
+        }
+        if (lane == 0) {
+          piv[cn] = pr;
+          sinv[nxt] = inv;
+          const long long best = mag_key(pv);
+          if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + cn);
+        }
       }
     } else {
-      // step c on every other entry: all loads, then the FMAs, then the stores
-      const T invc = sinv;
-      T vv[kPanelSlots7], ww[kPanelSlots7], ff[kPanelSlots7];
-      int rp[kPanelSlots7];
+      // step c on every entry outside column c+1: all loads, the FMAs, the stores
+      const T invc = sinv[cur];
+      T vv[kSlots], ww[kSlots], ff[kSlots];
+      int rp[kSlots];
 #pragma unroll
-      for (int t = 0; t < kPanelSlots7; ++t) {
-        if (ei[t] < 0 || ej[t] == cn) continue;
-        rp[t] = rmap[ei[t]];
-        vv[t] = S[rp[t]][ej[t]];
-        ww[t] = ej[t] == c ? invc : prow[ej[t]];
-        ff[t] = fcol[ei[t]];
+      for (int t = 0; t < kSlots; ++t) {
+        if (rank * 32 + 224 * t >= nel) continue;  // warp-uniform: no live entry in this slot
+        const int i = ei[t] >= 0 ? ei[t] : 0, j = ej[t];
+        rp[t] = rmap[cur][i];
+        vv[t] = S[cur][rp[t]][j];
+        ww[t] = j == c ? invc : prow[cur][j];
+        ff[t] = fcol[cur][i];
       }
 #pragma unroll
-      for (int t = 0; t < kPanelSlots7; ++t) {
-        if (ei[t] < 0 || ej[t] == cn) continue;
+      for (int t = 0; t < kSlots; ++t) {
+        if (rank * 32 + 224 * t >= nel) continue;
         vv[t] = gj_entry(vv[t], ff[t], ww[t], ei[t] == c, ej[t] == c);
       }
 #pragma unroll
-      for (int t = 0; t < kPanelSlots7; ++t)
-        if (ei[t] >= 0 && ej[t] != cn) S[rp[t]][ej[t]] = vv[t];
+      for (int t = 0; t < kSlots; ++t)
+        if (rank * 32 + 224 * t < nel && ei[t] >= 0 && ej[t] != cn) S[nxt][rp[t]][ej[t]] = vv[t];
     }
     __syncthreads();
   }
@@ -321,10 +383,28 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
     }
   }
   __syncthreads();
+  const int fin = bp & 1, fmap = (bp - 1) & 1;
   for (int e = tid; e < nel; e += 256) {
     const int i = e / bp, j = e - i * bp;
-    A[(int64_t)i * d.ld + j] = S[rmap[i]][qcol[j]];
+    A[(int64_t)i * d.ld + j] = S[fin][rmap[fmap][i]][qcol[j]];
   }
+}
+
+// opt the panel kernels in to their dynamic shared memory on the current
+// device (75 KB for 48-wide FP64 blocks; done before any launch or capture)
+cudaError_t panel_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)panel_smem_bytes<double2>(48));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)panel_smem_bytes<double2>(24));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)panel_smem_bytes<float2>(48));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)panel_smem_bytes<float2>(24));
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -448,8 +528,11 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
       return launch_k(k_extend_add<T>, grid1, dim3(256), 0, st, prio, p.d_extadd, op.d0, op.d1, p.d_maps, arena,
                       stride);
     case OP_PANEL:
-      return launch_k(k_panel_inverse<T, R>, grid1, dim3(256), 0, st, prio, p.d_panels, op.d0, arena, stride,
-                      p.d_status);
+      if (p.panel <= 24)
+        return launch_k(k_panel_inverse<T, R, 24>, grid1, dim3(256), panel_smem_bytes<T>(24), st, prio, p.d_panels,
+                        op.d0, arena, stride, p.d_status);
+      return launch_k(k_panel_inverse<T, R, kMaxPanel>, grid1, dim3(256), panel_smem_bytes<T>(kMaxPanel), st, prio,
+                      p.d_panels, op.d0, arena, stride, p.d_status);
     case OP_GEMM:
       return launch_gemm(p, op, arena, st);
     case OP_COPY:

@@ -44,6 +44,7 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t
 // FP64-accurate GEMM on the BF16 tensor cores (split pass + digit GEMM)
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 cudaError_t emu_prepare();
+cudaError_t panel_prepare();
 // split pass + tcgen05 digit GEMM over descriptors [d0, d1); blocks = output
 // tiles (128 x 16 complex); persistent kernels (single_chunk: every K <= 32)
 // on min(blocks, max_ctas) CTAs, each a contiguous range of tiles

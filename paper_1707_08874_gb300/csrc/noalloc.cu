@@ -87,6 +87,7 @@ extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double
   unsigned char* base = nullptr;
   int st = scratch_address(&base);
   if (st != CL_OK) return st;
+  if (cl::panel_prepare() != cudaSuccess) return CL_ERR_CUDA;
   p.d_status = reinterpret_cast<int*>(base);
   p.d_arena = base + 256;
   size_t o = 256 + arena_bytes;
