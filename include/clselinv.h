@@ -137,7 +137,7 @@ int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan);
 /*
  * cl_analyze_ex -- cl_analyze with an explicit pivoting-panel width
  * (unknowns, a multiple of 3 in 3..48; 0 = the precision's default: 48 for
- * CL_FP64 / CL_MIXED_FP32, 24 for CL_FP64_EMU).  Narrower panels shorten the
+ * CL_FP64, 30 for CL_FP64_EMU / CL_MIXED_FP32).  Narrower panels shorten the
  * serial chain of FP64 panel inverses, wider ones make fewer, larger GEMMs;
  * the autotuner in the Python package picks it per shape by timing.
  */

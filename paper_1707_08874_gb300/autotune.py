@@ -14,7 +14,7 @@ import os
 from . import binding as B
 from . import inputs
 
-CANDIDATES = (12, 24, 48)
+CANDIDATES = (12, 24, 30, 48)
 
 
 def cache_path() -> str:

@@ -104,7 +104,7 @@ __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, cons
 // cycles on this part (0.5 lanes per cycle, ~1.7 per SM), so every FP64 warp
 // instruction should carry 32 live lanes and one code path: the update walks
 // the bp x bp entries linearly with one FMA sequence per entry, and the
-// kernel is instantiated per maximum panel width (24, 48) so that its update
+// kernel is instantiated per maximum panel width (24, 32, 48) so that its update
 // loop holds only the slots that the width can fill.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPanel = 48;
@@ -393,17 +393,14 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
 // opt the panel kernels in to their dynamic shared memory on the current
 // device (75 KB for 48-wide FP64 blocks; done before any launch or capture)
 cudaError_t panel_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)panel_smem_bytes<double2>(48));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)panel_smem_bytes<double2>(24));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)panel_smem_bytes<float2>(48));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)panel_smem_bytes<float2>(24));
+  cudaError_t e = cudaSuccess;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 48>, a, (int)panel_smem_bytes<double2>(48));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 32>, a, (int)panel_smem_bytes<double2>(32));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 24>, a, (int)panel_smem_bytes<double2>(24));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 48>, a, (int)panel_smem_bytes<float2>(48));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 32>, a, (int)panel_smem_bytes<float2>(32));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 24>, a, (int)panel_smem_bytes<float2>(24));
   return e;
 }
 
@@ -530,6 +527,9 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
     case OP_PANEL:
       if (p.panel <= 24)
         return launch_k(k_panel_inverse<T, R, 24>, grid1, dim3(256), panel_smem_bytes<T>(24), st, prio, p.d_panels,
+                        op.d0, arena, stride, p.d_status);
+      if (p.panel <= 32)
+        return launch_k(k_panel_inverse<T, R, 32>, grid1, dim3(256), panel_smem_bytes<T>(32), st, prio, p.d_panels,
                         op.d0, arena, stride, p.d_status);
       return launch_k(k_panel_inverse<T, R, kMaxPanel>, grid1, dim3(256), panel_smem_bytes<T>(kMaxPanel), st, prio,
                       p.d_panels, op.d0, arena, stride, p.d_status);

@@ -14,11 +14,15 @@ namespace cl {
 constexpr int kTileM = 64;
 constexpr int kTileN = 32;
 constexpr int kEmuTileM = 128;
-// Sites per leaf of the nested dissection and pivoting panel (unknowns) by precision.
+// Sites per leaf of the nested dissection and pivoting panel (unknowns) by
+// precision.  30 unknowns (10 sites) is the widest panel whose products stay
+// single-chunk digit GEMMs (K <= 32 complex); measured on GB300 at 8^3x4 it
+// beats 24 and 48 for the emulated-FP64 and FP32 fronts, while the FP64-pipe
+// bound native fronts prefer 48.
 constexpr int kLeafSites = 8;
 constexpr int kPanelFP64 = 48;
-constexpr int kPanelFP32 = 48;
-constexpr int kPanelEmu = 24;
+constexpr int kPanelFP32 = 30;
+constexpr int kPanelEmu = 30;
 
 struct SNode {
   std::vector<int> sep;       // sites eliminated at this supernode (front order)

@@ -78,6 +78,33 @@ def test_fp64_parity_small(ns, nt, seed, prec):
     plan.close()
 
 
+
+_REF64 = {}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("panel", [12, 27, 30, 48])
+def test_fp64_parity_panel_widths(panel, prec):
+    """Every width instantiation of the panel inverse (24-, 32- and 48-wide
+    blocks); 27 and 30 leave a ragged last panel in most supernodes, 30 is the
+    widest panel whose products stay single-chunk digit GEMMs."""
+    B = _binding()
+    U = inputs.random_links(6, 4, seed=1707)
+    if not _REF64:
+        _REF64["ref"] = oracle.drift_eval(6, 4, U, M, MU)
+        _REF64["tol"] = _tol(oracle.dirac_dense(6, 4, U, M, MU))
+    ref, (tol, kappa) = _REF64["ref"], _REF64["tol"]
+    plan = B.Plan.analyze_ex(6, 4, 1, _prec(B, prec), panel)
+    assert plan.info["panel"] == panel
+    got, st = _run(plan, U)
+    assert st == B.CL_OK
+    for key in ("Gdiag", "Gfwd", "Gbwd"):
+        err = _blockwise(got[key][0], ref[key])
+        assert err < tol, (key, err, tol, kappa)
+    kerr = np.abs(got["Kf"][0] - ref["Kf"]).max() / np.abs(ref["Kf"]).max()
+    assert kerr < tol, (kerr, tol, kappa)
+    plan.close()
+
 def test_fp64_free_field_and_su3():
     """U = 1 (free field) and SU(3) links at mu = 0 (real drift)."""
     B = _binding()

@@ -21,7 +21,8 @@ def lib():
 CASES = [(4, 4, B.CL_FP64, 12), (4, 4, B.CL_FP64, 24), (4, 4, B.CL_FP64, 48),
          (4, 4, B.CL_FP64_EMU, 12), (4, 4, B.CL_FP64_EMU, 24), (4, 4, B.CL_FP64_EMU, 48),
          (4, 4, B.CL_MIXED_FP32, 48), (6, 4, B.CL_FP64, 48), (6, 4, B.CL_FP64_EMU, 24),
-         (4, 6, B.CL_FP64_EMU, 24), (4, 8, B.CL_FP64, 24), (6, 6, B.CL_FP64_EMU, 48)]
+         (4, 6, B.CL_FP64_EMU, 24), (4, 8, B.CL_FP64, 24), (6, 6, B.CL_FP64_EMU, 48),
+         (4, 4, B.CL_FP64_EMU, 30), (6, 4, B.CL_FP64_EMU, 30), (6, 4, B.CL_FP64, 27), (8, 4, B.CL_FP64_EMU, 30)]
 
 
 @pytest.mark.parametrize("ns,nt,prec,panel", CASES)
