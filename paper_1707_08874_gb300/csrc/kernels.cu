@@ -143,26 +143,41 @@ __device__ __forceinline__ double float_to_double(float f) {
                                           ((unsigned long long)(u & 0x7FFFFF) << 29)));
 }
 
-// 1 / pv = conj(pv) / |pv|^2.  FP64: a single-precision seed of 1 / |pv|^2
-// formed from float copies of the components (integer conversions, so it runs
-// beside the FP64 |pv|^2), then two Newton steps (22 -> 44 -> 88 bits).
+// 1 / pv = conj(pv) / |pv|^2, branch-free.  FP64: a single-precision seed
+// r0 of 1 / |pv|^2 formed from float copies of the components (integer
+// conversions, beside the FP64 |pv|^2), e = 1 - |pv|^2 r0 (|e| < 2^-19) and
+// conj(pv) r0 (1 + e + e^2), the series of 1 / (1 - e) cut below 2^-57:
+// five dependent FP64 levels (a dependent FP64 operation costs ~200 cycles on
+// this part).  FP32: a fast reciprocal and one Newton step.  ok = false where
+// the seed is unusable (zero, tiny, huge or non-finite pv); recip_exact then
+// gives the plain quotient.
 template <typename T, typename R>
-__device__ __forceinline__ T reciprocal(T pv) {
-  const R n2 = fma(pv.x, pv.x, pv.y * pv.y);
-  R r;
+__device__ __forceinline__ T recip_fast(T pv, bool& ok) {
+  T inv;
   if (sizeof(R) == 8) {
     const float xf = abs_to_float(pv.x), yf = abs_to_float(pv.y);
     const float rf = __fdividef(1.0f, fmaf(xf, xf, yf * yf));
-    const bool seed_ok = rf > 1e-30f && rf < 1e30f;  // normal, far from the float range limits
-    r = seed_ok ? (R)float_to_double(rf) : (R)0;
-    const R e1 = fma(-n2, r, (R)1);
-    r = fma(r, e1, r);
-    const R e2 = fma(-n2, r, (R)1);
-    r = fma(r, e2, r);
-    if (!seed_ok || !(n2 > 0) || !isfinite(r)) r = (R)1 / n2;  // extreme / zero / NaN: plain division
+    ok = rf > 1e-30f && rf < 1e30f;  // normal, far from the float range limits
+    const R r0 = ok ? (R)float_to_double(rf) : (R)0;
+    const R n2 = fma(pv.x, pv.x, pv.y * pv.y);
+    const R yx = pv.x * r0, yy = -pv.y * r0;
+    const R e = fma(-n2, r0, (R)1);
+    const R g = fma(e, e, e);
+    inv.x = fma(yx, g, yx);
+    inv.y = fma(yy, g, yy);
   } else {
-    r = (R)1 / n2;
+    const R n2 = fma(pv.x, pv.x, pv.y * pv.y);
+    ok = n2 > (R)1e-30 && n2 < (R)1e30;
+    R r = __fdividef(1.0f, (float)n2);
+    r = fma(r, fma(-n2, r, (R)1), r);
+    inv.x = pv.x * r;
+    inv.y = -pv.y * r;
   }
+  return inv;
+}
+template <typename T, typename R>
+__device__ __noinline__ T recip_exact(T pv) {
+  const R r = (R)1 / fma(pv.x, pv.x, pv.y * pv.y);
   T inv;
   inv.x = pv.x * r;
   inv.y = -pv.y * r;
@@ -213,31 +228,43 @@ constexpr size_t panel_smem_bytes(int mp) {
   return 2 * (size_t)mp * (mp + 1) * sizeof(T);
 }
 
+__host__ __device__ constexpr int bit_count(unsigned m) { return m ? (int)(m & 1u) + bit_count(m >> 1) : 0; }
+
+// Update-warp sets: warp w runs on scheduler w % 4.  The pivot chain of warp
+// 0 is a string of dependent FP64 operations, so the update warps stay off
+// scheduler 0 (measured on one 24- / 30-wide FP64 block: 43 / 61 us with
+// twelve update warps on schedulers 1-3, 47 / 67 us with seven warps over all
+// four).
+constexpr unsigned kUpdNoSched0 = 0xEEEEu;
+
 // The block lives in two shared-memory copies: step c reads copy c & 1 and
 // writes the other, so one barrier per column suffices and warp 0 can read
-// the pre-step values of any row while warps 1-7 write the step's results.
-// Column look-ahead: while warps 1-7 apply step c to every entry outside
-// column c+1, warp 0 applies it to column c+1, picks that column's pivot,
-// applies step c to the pivot row, forms the reciprocal, and leaves step
-// c+1's row map, multipliers and scaled pivot row for the next column.
-// The update warps are ranked so that warp 4, which shares a scheduler with
-// warp 0, takes the last (least filled) entries.
-template <typename T, typename R, int MP>
-__global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
-                                                       int64_t stride, int* __restrict__ status) {
-  constexpr int kSlots = (MP * MP + 223) / 224;  // update entries per thread of warps 1-7
-  constexpr int H = (MP + 31) / 32;              // column entries per lane of warp 0
+// the pre-step values of any row while the update warps write the step's
+// results.  Column look-ahead: while the update warps apply step c to every
+// entry outside column c+1, warp 0 applies it to column c+1, every lane forms
+// the reciprocal of its own candidate pivots while the pivot is chosen, warp
+// 0 applies step c to the pivot row and leaves step c+1's row map,
+// multipliers and scaled pivot row for the next column.  The row
+// interchanges are undone at the end by reading the columns through the
+// inverse of the final row map.
+template <typename T, typename R, int MP, int NT, unsigned UMASK>
+__global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
+                                                      int64_t stride, int* __restrict__ status) {
+  constexpr int NU = bit_count(UMASK);                   // update warps
+  constexpr int kSlots = (MP * MP + 32 * NU - 1) / (32 * NU);  // update entries per update thread
+  constexpr int H = (MP + 31) / 32;                      // column entries per lane of warp 0
+  constexpr int NW = NT / 32;
+  static_assert((UMASK & 1u) == 0 && (UMASK >> NW) == 0, "update warps: 1 .. NT/32 - 1");
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T(*S)[MP][MP + 1] = reinterpret_cast<T(*)[MP][MP + 1]>(panel_smem);  // S[2]; logical row i in S[.][rmap[.][i]]
   __shared__ T fcol[2][MP], prow[2][MP], sinv[2];
-  __shared__ int rmap[2][MP], piv[MP], qcol[MP];
-  __shared__ long long wmax[8];
-  __shared__ long long sthr;
+  __shared__ int rmap[2][MP], qcol[MP];
+  __shared__ long long wmax[NW], pkey[MP];
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
   const int bp = d.bp, nel = bp * bp, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   long long km = 0;
-  for (int e = tid; e < nel; e += 256) {
+  for (int e = tid; e < nel; e += NT) {
     const int i = e / bp, j = e - i * bp;
     const T v = A[(int64_t)i * d.ld + j];
     S[0][i][j] = v;
@@ -247,14 +274,6 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
   for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
   if (lane == 0) wmax[warp] = km;
   __syncthreads();
-  if (tid == 0) {
-    long long m = wmax[0];
-    for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
-    const double rel = sizeof(R) == 8 ? 1e-13 : 1e-6;  // singular-pivot threshold by precision
-    sthr = value_key(rel * key_value(m, R(0)), R(0));
-  }
-  __syncthreads();
-  const long long thr = sthr;
   // step 0's pivot, row map, multipliers and scaled pivot row
   if (warp == 0) {
     T v[H];
@@ -265,7 +284,9 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
     }
     const int pr = pivot_row(v, 0, bp, lane);
     const T pv = S[0][pr][0];
-    const T inv = reciprocal<T, R>(pv);
+    bool ok;
+    T inv = recip_fast<T, R>(pv, ok);
+    if (!ok) inv = recip_exact<T, R>(pv);  // pv is the same in every lane: warp-uniform
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       const int i = lane + 32 * h;
@@ -277,20 +298,19 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
       }
     }
     if (lane == 0) {
-      piv[0] = pr;
       sinv[0] = inv;
-      const long long best = mag_key(pv);
-      if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0);
+      pkey[0] = mag_key(pv);
     }
   }
-  // update entries of warps 1-7: the thread of rank q takes entries q, q + 224, ...
-  const int rank = warp == 0 ? 0 : (warp < 4 ? warp - 1 : (warp == 4 ? 6 : warp - 2));
+  // update entries: the thread of rank q among the update warps takes entries q, q + 32 NU, ...
+  const bool upd = (UMASK >> warp) & 1u;
+  const int rank = __popc(UMASK & ((1u << warp) - 1u));
   const int u = rank * 32 + lane;
   int ei[kSlots], ej[kSlots];
 #pragma unroll
   for (int t = 0; t < kSlots; ++t) {
-    const int e = u + 224 * t;
-    ei[t] = (warp != 0 && e < nel) ? e / bp : -1;
+    const int e = u + 32 * NU * t;
+    ei[t] = (upd && e < nel) ? e / bp : -1;
     ej[t] = ei[t] >= 0 ? e - ei[t] * bp : 0;
   }
   __syncthreads();
@@ -311,14 +331,12 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
             S[nxt][r][cn] = v[h];
           }
         }
-        const int pr = pivot_row(v, cn, bp, lane);
-        T mine = v[0];
+        // every lane's candidate reciprocal, beside the pivot search
+        T rv[H];
+        bool rok[H];
 #pragma unroll
-        for (int h = 1; h < H; ++h)
-          if ((pr >> 5) == h) mine = v[h];
-        T pv;
-        pv.x = __shfl_sync(0xffffffffu, mine.x, pr & 31);
-        pv.y = __shfl_sync(0xffffffffu, mine.y, pr & 31);
+        for (int h = 0; h < H; ++h) rv[h] = recip_fast<T, R>(v[h], rok[h]);
+        const int pr = pivot_row(v, cn, bp, lane);
         // step c on the pivot row (logical row pr > c), outside column c+1
         const int rp = rmap[cur][pr];
         const T fp = fcol[cur][pr], invc = sinv[cur];
@@ -329,7 +347,17 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
           row[h] = T{0, 0};
           if (j < bp && j != cn) row[h] = gj_entry(S[cur][rp][j], fp, j == c ? invc : prow[cur][j], false, j == c);
         }
-        const T inv = reciprocal<T, R>(pv);
+        T mine = v[0], minv = rv[0];
+        bool mok = rok[0];
+#pragma unroll
+        for (int h = 1; h < H; ++h)
+          if ((pr >> 5) == h) mine = v[h], minv = rv[h], mok = rok[h];
+        T pv, inv;
+        pv.x = __shfl_sync(0xffffffffu, mine.x, pr & 31);
+        pv.y = __shfl_sync(0xffffffffu, mine.y, pr & 31);
+        inv.x = __shfl_sync(0xffffffffu, minv.x, pr & 31);
+        inv.y = __shfl_sync(0xffffffffu, minv.y, pr & 31);
+        if (!__shfl_sync(0xffffffffu, mok, pr & 31)) inv = recip_exact<T, R>(pv);  // warp-uniform, rare
         // step c+1: logical rows c+1 and pr exchanged
 #pragma unroll
         for (int h = 0; h < H; ++h) {
@@ -341,20 +369,18 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
           }
         }
         if (lane == 0) {
-          piv[cn] = pr;
           sinv[nxt] = inv;
-          const long long best = mag_key(pv);
-          if (best < thr || best == 0) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + cn);
+          pkey[cn] = mag_key(pv);
         }
       }
-    } else {
+    } else if (upd) {
       // step c on every entry outside column c+1: all loads, the FMAs, the stores
       const T invc = sinv[cur];
       T vv[kSlots], ww[kSlots], ff[kSlots];
       int rp[kSlots];
 #pragma unroll
       for (int t = 0; t < kSlots; ++t) {
-        if (rank * 32 + 224 * t >= nel) continue;  // warp-uniform: no live entry in this slot
+        if (rank * 32 + 32 * NU * t >= nel) continue;  // warp-uniform: no live entry in this slot
         const int i = ei[t] >= 0 ? ei[t] : 0, j = ej[t];
         rp[t] = rmap[cur][i];
         vv[t] = S[cur][rp[t]][j];
@@ -363,44 +389,68 @@ __global__ void __launch_bounds__(256) k_panel_inverse(const PanelDesc* __restri
       }
 #pragma unroll
       for (int t = 0; t < kSlots; ++t) {
-        if (rank * 32 + 224 * t >= nel) continue;
+        if (rank * 32 + 32 * NU * t >= nel) continue;
         vv[t] = gj_entry(vv[t], ff[t], ww[t], ei[t] == c, ej[t] == c);
       }
 #pragma unroll
       for (int t = 0; t < kSlots; ++t)
-        if (rank * 32 + 224 * t < nel && ei[t] >= 0 && ej[t] != cn) S[nxt][rp[t]][ej[t]] = vv[t];
+        if (rank * 32 + 32 * NU * t < nel && ei[t] >= 0 && ej[t] != cn) S[nxt][rp[t]][ej[t]] = vv[t];
     }
     __syncthreads();
   }
-  // logical rows are in rmap order; the row interchanges are undone on the
-  // columns in reverse order: result column j = column qcol[j] of S
-  if (tid == 0) {
-    for (int j = 0; j < bp; ++j) qcol[j] = j;
-    for (int c = bp - 1; c >= 0; --c) {
-      const int p = piv[c], t = qcol[c];
-      qcol[c] = qcol[p];
-      qcol[p] = t;
-    }
+  // result column j = column qcol[j] of the logical rows, qcol = inverse of
+  // the final row map; pivots below 1e-13 max|block| (1e-6 for FP32) reported
+  const int fin = bp & 1, fmap = (bp - 1) & 1;
+  if (tid < bp) qcol[rmap[fmap][tid]] = tid;
+  if (warp == 1) {
+    long long m = wmax[0];
+    for (int w = 1; w < NW; ++w) m = max(m, wmax[w]);
+    const double rel = sizeof(R) == 8 ? 1e-13 : 1e-6;
+    const long long thr = value_key(rel * key_value(m, R(0)), R(0));
+    int bad = 0x7fffffff;
+    for (int c = lane; c < bp; c += 32)
+      if (pkey[c] < thr || pkey[c] == 0) bad = min(bad, c);
+    bad = __reduce_min_sync(0xffffffffu, bad);
+    if (lane == 0 && bad != 0x7fffffff) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + bad);
   }
   __syncthreads();
-  const int fin = bp & 1, fmap = (bp - 1) & 1;
-  for (int e = tid; e < nel; e += 256) {
+  for (int e = tid; e < nel; e += NT) {
     const int i = e / bp, j = e - i * bp;
     A[(int64_t)i * d.ld + j] = S[fin][rmap[fmap][i]][qcol[j]];
   }
+}
+
+// the instantiation for a plan's panel width (blocks of 24, 32 or 48) and
+// its block size: twelve update warps off scheduler 0 (512 threads), except
+// 48-wide FP64 blocks, whose update-bound sweep runs best (and without
+// register spills) on 256 threads with update warps 1-7 (measured, one block:
+// 215 us against 219 us)
+constexpr unsigned kUpdAll7 = 0xFEu;
+template <typename T, typename R>
+struct PanelLaunch {
+  void (*k)(const PanelDesc*, int, T*, int64_t, int*);
+  int threads, block;
+};
+template <typename T, typename R>
+PanelLaunch<T, R> panel_kernel(int panel) {
+  if (panel <= 24) return {k_panel_inverse<T, R, 24, 512, kUpdNoSched0>, 512, 24};
+  if (panel <= 32) return {k_panel_inverse<T, R, 32, 512, kUpdNoSched0>, 512, 32};
+  if (sizeof(R) == 8) return {k_panel_inverse<T, R, kMaxPanel, 256, kUpdAll7>, 256, kMaxPanel};
+  return {k_panel_inverse<T, R, kMaxPanel, 512, kUpdNoSched0>, 512, kMaxPanel};
 }
 
 // opt the panel kernels in to their dynamic shared memory on the current
 // device (75 KB for 48-wide FP64 blocks; done before any launch or capture)
 cudaError_t panel_prepare() {
   cudaError_t e = cudaSuccess;
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 48>, a, (int)panel_smem_bytes<double2>(48));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 32>, a, (int)panel_smem_bytes<double2>(32));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<double2, double, 24>, a, (int)panel_smem_bytes<double2>(24));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 48>, a, (int)panel_smem_bytes<float2>(48));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 32>, a, (int)panel_smem_bytes<float2>(32));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_inverse<float2, float, 24>, a, (int)panel_smem_bytes<float2>(24));
+  for (int w : {24, 32, kMaxPanel}) {
+    const PanelLaunch<double2, double> pd = panel_kernel<double2, double>(w);
+    const PanelLaunch<float2, float> pf = panel_kernel<float2, float>(w);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(pd.k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem_bytes<double2>(w));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(pf.k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem_bytes<float2>(w));
+  }
   return e;
 }
 
@@ -524,15 +574,11 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
     case OP_EXTADD:
       return launch_k(k_extend_add<T>, grid1, dim3(256), 0, st, prio, p.d_extadd, op.d0, op.d1, p.d_maps, arena,
                       stride);
-    case OP_PANEL:
-      if (p.panel <= 24)
-        return launch_k(k_panel_inverse<T, R, 24>, grid1, dim3(256), panel_smem_bytes<T>(24), st, prio, p.d_panels,
-                        op.d0, arena, stride, p.d_status);
-      if (p.panel <= 32)
-        return launch_k(k_panel_inverse<T, R, 32>, grid1, dim3(256), panel_smem_bytes<T>(32), st, prio, p.d_panels,
-                        op.d0, arena, stride, p.d_status);
-      return launch_k(k_panel_inverse<T, R, kMaxPanel>, grid1, dim3(256), panel_smem_bytes<T>(kMaxPanel), st, prio,
-                      p.d_panels, op.d0, arena, stride, p.d_status);
+    case OP_PANEL: {
+      const PanelLaunch<T, R> pl = panel_kernel<T, R>(p.panel);
+      return launch_k(pl.k, grid1, dim3(pl.threads), panel_smem_bytes<T>(pl.block), st, prio, p.d_panels, op.d0, arena,
+                      stride, p.d_status);
+    }
     case OP_GEMM:
       return launch_gemm(p, op, arena, st);
     case OP_COPY:
