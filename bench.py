@@ -35,12 +35,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fermion-drift evals/sec on 8^3x4 (FP64 vs mixed, stated drift error); front TFLOP/s vs peak"
 NS, NT, M, MU = 8, 4, 0.05, 0.25
-# DRAM bytes per launch of the dominant kernel from an ncu capture of this
-# workload (profiles/gemm_fp64_8x4.md); None until captured for the current kernel.
 # DRAM bytes per digit-GEMM launch (dram__bytes_read + dram__bytes_write,
-# averaged over the 323 GEMM launches of one 8^3x4 evaluation, ncu, cold
-# cache); valid for the kernels it was taken on, keyed by (precision, batch)
-NCU_TRAFFIC = {("fp64_emu", 1): 60.55e6}
+# averaged over the 269 GEMM launches of one 8^3x4 evaluation with
+# 30-unknown panels, ncu, cold cache; profiles/gemm_emu_tcgen05_8x4.md);
+# valid for the kernels it was taken on, keyed by (precision, batch, panel)
+NCU_TRAFFIC = {("fp64_emu", 1, 30): 65.27e6}
 
 
 def measured_bf16_tflops():
@@ -95,7 +94,7 @@ def dist_env():
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of one 8^3 x 4 evaluation)
 # ---------------------------------------------------------------------------
-def oracle_sample(lu_steps=256, ncols=96):
+def oracle_sample(lu_steps=2560, ncols=2048):
     """Time a bounded sample of the oracle's dense evaluation and scale it to
     one full evaluation by exact operation counts: the dense D, the first
     `lu_steps` of the N-step right-looking LU (step k costs (N-k)^2 updates)
@@ -382,7 +381,7 @@ def run_ours(args, rank, world, local):
                                      B.CL_FP64_EMU: "%s / 28 digit products (FP64-equivalent ceiling of the "
                                                     "tcgen05 digit GEMM)" % peak_note,
                                      B.CL_MIXED_FP32: "FP32 FMA throughput measured live on this GPU"}[prec],
-                     "traffic": NCU_TRAFFIC.get((args.precision, bsz)),
+                     "traffic": NCU_TRAFFIC.get((args.precision, bsz, panel)),
                      "gemm_share_of_kernel_time": g.get("total_ms", 0.0) / total_prof_ms if total_prof_ms else None},
         "front_tflops": flops_eval * bsz / (ms / 1e3) / 1e12,
         "flops_per_eval": flops_eval,
