@@ -1,3 +1,4 @@
+#include <cstdlib>
 // C ABI of the library (declared in clselinv.h): plan creation, device memory
 // of the plan, and the stream-ordered compute calls.
 #include <cstring>
@@ -66,6 +67,8 @@ size_t elem_bytes(const Plan& p) { return p.precision == CL_MIXED_FP32 ? sizeof(
 int setup_device(Plan& p) {
   cudaGetDevice(&p.device);
   if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) != cudaSuccess) return CL_ERR_CUDA;
+  if (const char* cs = std::getenv("CLSELINV_CHAIN_SMS"))  // SMs kept free of bulk GEMM CTAs (tuning)
+    p.chain_sms = std::min(std::max(std::atoi(cs), 0), p.num_sms - 1);
   size_t total = 0;
   cudaError_t e;
   if ((e = cl::panel_prepare()) != cudaSuccess) return cuda_status(e);

@@ -828,11 +828,16 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
                   (const unsigned*)words, (const int*)ints, wstride, istride, status);
 }
 
+// A persistent bulk CTA (320 threads x 168 registers) leaves too few
+// registers on its SM for a panel-inverse CTA, so a bulk launch over every SM
+// would hold the next panel until the whole bulk update ends: bulk launches
+// (stream 1) leave p.chain_sms SMs to the panel chain.
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
   const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
+  const int ctas = op.stream ? std::max(1, p.num_sms - p.chain_sms) : p.num_sms;
   return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.batch, arena, p.arena_elems,
-                    p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, p.num_sms,
-                    st, op_priority(p, op));
+                    p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, ctas, st,
+                    op_priority(p, op));
 }
 
 }  // namespace cl

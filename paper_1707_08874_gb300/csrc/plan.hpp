@@ -127,6 +127,7 @@ struct Plan {
   bool has_device = false;
   int device = 0;
   int num_sms = 0;            // multiprocessors of the device (set up with the device state)
+  int chain_sms = 2;          // SMs the bulk digit GEMMs leave to the panel chain (two-stream plans)
   std::vector<SNode> nodes;   // postorder, root last
   int n_levels = 0;
   double factor_flops = 0, selinv_flops = 0;
