@@ -231,10 +231,19 @@ int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double
             double* Gf, double* Gb, cudaStream_t st) {
   T* arena = static_cast<T*>(p.d_arena);
   const bool two = &ops == &p.factor_ops && p.streams[1] != nullptr;
+  // an op's first kernel may launch programmatically (overlapping its
+  // predecessor's tail) only when it directly follows a kernel of this op list
+  // on its stream, with no event wait in between
+  // (never in a profiled run, whose per-kernel events would then overlap)
+  auto launches_kernel = [](const cl::Op& op) { return op.kind != cl::OP_ZERO && op.blocks > 0; };
   if (!two) {
+    bool fresh = true;
     for (const auto& op : ops) {
-      const int r = launch_one<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, st);
+      cl::Op o = op;
+      o.pdl = !fresh && !p.profiling;
+      const int r = launch_one<T, R>(p, o, arena, links, m, mu, Gd, Gf, Gb, st);
       if (r != CL_OK) return r;
+      fresh = !launches_kernel(op);
     }
     return CL_OK;
   }
@@ -242,12 +251,16 @@ int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double
   cudaError_t e = cudaEventRecord((cudaEvent_t)p.fork_event, st);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], (cudaEvent_t)p.fork_event, 0);
   if (e != cudaSuccess) return cuda_status(e);
+  bool fresh[2] = {true, true};
   for (size_t i = 0; i < ops.size(); ++i) {
     const cl::Op& op = ops[i];
     cudaStream_t s = ss[op.stream];
     if (op.wait >= 0 && (e = cudaStreamWaitEvent(s, (cudaEvent_t)p.op_events[op.wait], 0)) != cudaSuccess)
       return cuda_status(e);
-    const int r = launch_one<T, R>(p, op, arena, links, m, mu, Gd, Gf, Gb, s);
+    cl::Op o = op;
+    o.pdl = !fresh[op.stream] && op.wait < 0 && !p.profiling;
+    fresh[op.stream] = !launches_kernel(op);
+    const int r = launch_one<T, R>(p, o, arena, links, m, mu, Gd, Gf, Gb, s);
     if (r != CL_OK) return r;
     if (op.signal && (e = cudaEventRecord((cudaEvent_t)p.op_events[i], s)) != cudaSuccess) return cuda_status(e);
   }

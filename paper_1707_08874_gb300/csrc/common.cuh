@@ -12,6 +12,16 @@ template <typename R> struct Cx;
 template <> struct Cx<double> { using T = double2; };
 template <> struct Cx<float> { using T = float2; };
 
+// Programmatic dependent launch.  Every kernel of the factorisation and the
+// selected inversion starts here: it waits until the grids it depends on
+// have completed and their writes are visible (a no-op for a kernel launched
+// without the attribute), then lets its own successor in the stream start
+// launching, so the successor's launch overlaps this kernel's run.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

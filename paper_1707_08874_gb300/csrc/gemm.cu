@@ -29,6 +29,7 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
 // 16 complex columns = 4 x 4 MMA tiles of 8 x 8 reals.
 __global__ void __launch_bounds__(128) k_gemm_f64(const GemmDesc* __restrict__ ds, int d0, int d1,
                                                   double2* __restrict__ arena, int64_t stride) {
+  pdl_enter();
   const int di = find_desc(ds, d0, d1, blockIdx.x);
   const GemmDesc d = ds[di];
   const int t = blockIdx.x - d.blk0;
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(128) k_gemm_f64(const GemmDesc* __restrict__ d
 constexpr int TK32 = 16;
 __global__ void __launch_bounds__(256) k_gemm_f32(const GemmDesc* __restrict__ ds, int d0, int d1,
                                                   float2* __restrict__ arena, int64_t stride) {
+  pdl_enter();
   const int di = find_desc(ds, d0, d1, blockIdx.x);
   const GemmDesc d = ds[di];
   const int t = blockIdx.x - d.blk0;
@@ -174,13 +176,13 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const GemmDesc* __restrict__ d
 cudaError_t launch_gemm(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
   if (p.precision == CL_FP64_EMU) return launch_gemm_emu(p, op, arena, st);
   const dim3 grid((unsigned)op.blocks, (unsigned)p.batch);
-  return launch_k(k_gemm_f64, grid, dim3(128), 0, st, op_priority(p, op), p.d_gemm, op.d0, op.d1, arena,
+  return launch_k(k_gemm_f64, grid, dim3(128), 0, st, op_launch(p, op), p.d_gemm, op.d0, op.d1, arena,
                   p.arena_elems);
 }
 
 cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t st) {
   const dim3 grid((unsigned)op.blocks, (unsigned)p.batch);
-  return launch_k(k_gemm_f32, grid, dim3(256), 0, st, op_priority(p, op), p.d_gemm, op.d0, op.d1, arena,
+  return launch_k(k_gemm_f32, grid, dim3(256), 0, st, op_launch(p, op), p.d_gemm, op.d0, op.d1, arena,
                   p.arena_elems);
 }
 

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ 
                                                    int64_t stride, unsigned* __restrict__ words,
                                                    int* __restrict__ ints, int64_t wstride, int64_t istride,
                                                    int total) {
+  pdl_enter();
   const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (item >= total) return;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(320, 1)
     k_gemm_emu_persist(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
                        double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
                        const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem_p[];
   unsigned char* sA = smem_p;                   // [7][kPA]
   unsigned char* sB = smem_p + kDig * kPA;      // [2 stages][7][kPB]
@@ -560,6 +562,7 @@ __global__ void __launch_bounds__(320, 1)
     k_gemm_emu_chunked(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
                        double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
                        const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem_c[];
   unsigned char* ctl = smem_c + kCStages * kCStage;
   // mbarriers: [0..2] stage landed, [3..5] stage consumed, [6,7] accumulator
@@ -815,16 +818,17 @@ cudaError_t emu_prepare() {
 
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, int prio) {
+                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, LaunchOpt lo) {
   const dim3 gs((unsigned)((items + 7) / 8), (unsigned)batch);
-  cudaError_t e = launch_k(k_emu_split, gs, dim3(256), 0, st, prio, gd, ed, d0, d1, (const double2*)arena, stride,
+  cudaError_t e = launch_k(k_emu_split, gs, dim3(256), 0, st, lo, gd, ed, d0, d1, (const double2*)arena, stride,
                            words, ints, wstride, istride, items);
   if (e != cudaSuccess) return e;
+  const LaunchOpt lg{lo.prio, pdl_enabled()};  // follows the split pass in the same stream
   const dim3 gp((unsigned)std::min(blocks, std::max(max_ctas, 1)), (unsigned)batch);
   if (single_chunk)  // blocks = output tiles of the launch; persistent CTAs over ranges of tiles
-    return launch_k(k_gemm_emu_persist, gp, dim3(320), kPSmemBytes, st, prio, gd, ed, d0, d1, blocks, arena, stride,
+    return launch_k(k_gemm_emu_persist, gp, dim3(320), kPSmemBytes, st, lg, gd, ed, d0, d1, blocks, arena, stride,
                     (const unsigned*)words, (const int*)ints, wstride, istride, status);
-  return launch_k(k_gemm_emu_chunked, gp, dim3(320), kCSmemBytes, st, prio, gd, ed, d0, d1, blocks, arena, stride,
+  return launch_k(k_gemm_emu_chunked, gp, dim3(320), kCSmemBytes, st, lg, gd, ed, d0, d1, blocks, arena, stride,
                   (const unsigned*)words, (const int*)ints, wstride, istride, status);
 }
 
@@ -837,7 +841,7 @@ cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStr
   const int ctas = op.stream ? std::max(1, p.num_sms - p.chain_sms) : p.num_sms;
   return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.batch, arena, p.arena_elems,
                     p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, ctas, st,
-                    op_priority(p, op));
+                    op_launch(p, op));
 }
 
 }  // namespace cl

@@ -14,6 +14,7 @@ template <typename T>
 __global__ void k_assemble(const double* __restrict__ links, T* __restrict__ arena, int64_t stride,
                            const int64_t* __restrict__ off, const int* __restrict__ ld, LatticeGeo g,
                            double m, double mu) {
+  pdl_enter();
   const int link = blockIdx.x * blockDim.x + threadIdx.x;
   if (link >= 4 * g.V) return;
   const int rep = blockIdx.y;
@@ -51,6 +52,7 @@ __global__ void k_assemble(const double* __restrict__ links, T* __restrict__ are
 template <typename T>
 __global__ void k_extend_add(const ExtAddDesc* __restrict__ ds, int d0, int d1, const int* __restrict__ maps,
                              T* __restrict__ arena, int64_t stride) {
+  pdl_enter();
   const int di = find_desc(ds, d0, d1, blockIdx.x);
   const ExtAddDesc d = ds[di];
   const int64_t e = (int64_t)(blockIdx.x - d.blk0) * 256 + threadIdx.x;
@@ -80,6 +82,7 @@ __global__ void k_extend_add(const ExtAddDesc* __restrict__ ds, int d0, int d1, 
 template <typename T>
 __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, const int* __restrict__ maps,
                          T* __restrict__ arena, int64_t stride) {
+  pdl_enter();
   const int di = find_desc(ds, d0, d1, blockIdx.x);
   const GatherDesc d = ds[di];
   const int r = 3 * d.rs;
@@ -250,6 +253,7 @@ constexpr unsigned kUpdNoSched0 = 0xEEEEu;
 template <typename T, typename R, int MP, int NT, unsigned UMASK>
 __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
                                                       int64_t stride, int* __restrict__ status) {
+  pdl_enter();
   constexpr int NU = bit_count(UMASK);                   // update warps
   constexpr int kSlots = (MP * MP + 32 * NU - 1) / (32 * NU);  // update entries per update thread
   constexpr int H = (MP + 31) / 32;                      // column entries per lane of warp 0
@@ -459,6 +463,7 @@ cudaError_t panel_prepare() {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_copy(const CopyDesc* __restrict__ ds, int d0, int d1, T* __restrict__ arena, int64_t stride) {
+  pdl_enter();
   const int di = find_desc(ds, d0, d1, blockIdx.x);
   const CopyDesc d = ds[di];
   const int64_t e = (int64_t)(blockIdx.x - d.blk0) * 256 + threadIdx.x;
@@ -477,6 +482,7 @@ template <typename T>
 __global__ void k_extract(const T* __restrict__ arena, int64_t stride, const int64_t* __restrict__ off,
                           const int* __restrict__ ld, int V, double* __restrict__ Gdiag, double* __restrict__ Gfwd,
                           double* __restrict__ Gbwd) {
+  pdl_enter();
   const int link = blockIdx.x * blockDim.x + threadIdx.x;
   if (link >= 4 * V) return;
   const int rep = blockIdx.y;
@@ -516,6 +522,7 @@ __global__ void k_extract(const T* __restrict__ arena, int64_t stride, const int
 __global__ void k_drift(const double* __restrict__ links, const double* __restrict__ Gfwd,
                         const double* __restrict__ Gbwd, LatticeGeo g, double mu, double nf,
                         double* __restrict__ Kf, int* __restrict__ status) {
+  pdl_enter();
   const int link = blockIdx.x * blockDim.x + threadIdx.x;
   if (link >= 4 * g.V) return;
   const int64_t o = (int64_t)blockIdx.y * 4 * g.V + link;
@@ -564,7 +571,7 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
   const int64_t stride = p.arena_elems;
   const dim3 grid1((unsigned)op.blocks, (unsigned)p.batch);
   const LatticeGeo g{p.Ns, p.Nt, p.V};
-  const int prio = op_priority(p, op);
+  const LaunchOpt prio = op_launch(p, op);
   switch (op.kind) {
     case OP_ZERO:
       return cudaMemset2DAsync(arena, (size_t)stride * sizeof(T), 0, (size_t)p.pool_elems * sizeof(T),

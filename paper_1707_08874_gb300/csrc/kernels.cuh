@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace cl {
@@ -15,21 +17,45 @@ constexpr int kNoPrio = 0x7fffffff;
 inline int op_priority(const Plan& p, const Op& op) {
   return p.streams[1] ? (op.stream ? p.prio_lo : p.prio_hi) : kNoPrio;
 }
+// Programmatic dependent launch of the front kernels (each opens with
+// pdl_enter): on unless CLSELINV_PDL=0.
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("CLSELINV_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+// launch options of one kernel: priority, and whether it may start launching
+// while its predecessor in the stream still runs (only where that
+// predecessor is a kernel of the same op list and no event wait lies between)
+struct LaunchOpt {
+  int prio = kNoPrio;
+  bool pdl = false;
+};
+inline LaunchOpt op_launch(const Plan& p, const Op& op) { return {op_priority(p, op), op.pdl && pdl_enabled()}; }
 template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int prio,
+cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, LaunchOpt o,
                      Args... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr{};
-  if (prio != kNoPrio) {
-    attr.id = cudaLaunchAttributePriority;
-    attr.val.priority = prio;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+  cudaLaunchAttribute attr[2]{};
+  unsigned n = 0;
+  if (o.prio != kNoPrio) {
+    attr[n].id = cudaLaunchAttributePriority;
+    attr[n].val.priority = o.prio;
+    ++n;
   }
+  if (o.pdl) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  cfg.attrs = n ? attr : nullptr;
+  cfg.numAttrs = n;
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
@@ -50,7 +76,7 @@ cudaError_t panel_prepare();
 // on min(blocks, max_ctas) CTAs, each a contiguous range of tiles
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, int prio = kNoPrio);
+                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, LaunchOpt lo = LaunchOpt{});
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

@@ -119,6 +119,7 @@ struct Op {
   int wait = -1;
   bool signal = false;
   bool single_chunk = false;  // CL_FP64_EMU GEMM with every K <= 32: persistent kernel
+  bool pdl = false;           // set at launch: the op's first kernel follows a kernel of its stream directly
 };
 
 struct Plan {
