@@ -285,11 +285,15 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
 
   const Mask2 none{0, 0, 0, 0};
   auto add_gemm = [&](int blk, int64_t a, int lda, int64_t bb, int ldb, int64_t c, int ldc, int M, int N,
-                      int K, int neg, int beta, Mask2 rm, Mask2 cm) {
-    GemmDesc d{a, bb, c, lda, ldb, ldc, M, N, K, neg, beta, rm, cm, blk, (N + kTileN - 1) / kTileN};
+                      int K, int neg, int beta, Mask2 rm, Mask2 cm, int trans = 0) {
+    GemmDesc d{a, bb, c, lda, ldb, ldc, M, N, K, neg, beta, rm, cm, blk, (N + kTileN - 1) / kTileN, trans};
     p.gemm.push_back(d);
     return (int)tiles(M, N);
   };
+  // The digit GEMMs tile C in 128-row blocks: a product with few rows (the
+  // TR panel products, b x nf) is issued transposed (nf x b) there, with
+  // every operand read and C written through the transposed strides.
+  const bool tr_short = precision == CL_FP64_EMU;
   auto add_copy = [&](int blk, int64_t src, int lds, int64_t dst, int ldd, int rows, int cols, Mask2 rm,
                       Mask2 cm) {
     CopyDesc d{src, dst, lds, ldd, rows, cols, rm, cm, blk};
@@ -356,8 +360,12 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
         p.panels.push_back(PanelDesc{n.off + (int64_t)c0 * n.nf + c0, n.nf, bp, i, c0});
         if (n.nf == bp) continue;  // nothing outside the panel
         // TR = Y * R_old (bp x nf), TC = -C_old * Y (nf x bp)
-        blk1 += add_gemm(blk1, n.off + (int64_t)c0 * n.nf + c0, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, tR_of(n),
-                         n.nf, bp, n.nf, bp, 0, 0, none, none);
+        if (tr_short)  // TR^T = R_old^T Y^T
+          blk1 += add_gemm(blk1, n.off + (int64_t)c0 * n.nf, n.nf, n.off + (int64_t)c0 * n.nf + c0, n.nf, tR_of(n),
+                           n.nf, n.nf, bp, bp, 0, 0, none, none, 7);
+        else
+          blk1 += add_gemm(blk1, n.off + (int64_t)c0 * n.nf + c0, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, tR_of(n),
+                           n.nf, bp, n.nf, bp, 0, 0, none, none);
         blk1 += add_gemm(blk1, n.off + c0, n.nf, n.off + (int64_t)c0 * n.nf + c0, n.nf, tC_of(n), bp, n.nf, bp, bp,
                          1, 0, none, none);
       }
@@ -382,8 +390,12 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
         const int b1 = std::min(b, n.k - c1);
         const int64_t tR = tR_of(n), tC = tC_of(n);
         // row strip: A[c1.., j] -= C_old[c1.., :] TR[:, j], j outside panel p
-        blks += add_gemm(blks, n.off + (int64_t)c1 * n.nf + c0, n.nf, tR, n.nf, n.off + (int64_t)c1 * n.nf, n.nf, b1,
-                         n.nf, bp, 1, 1, none, Mask2{c0, c0 + bp, 0, 0});
+        if (tr_short)  // (A[c1.., :])^T -= TR^T C_old[c1.., :]^T
+          blks += add_gemm(blks, tR, n.nf, n.off + (int64_t)c1 * n.nf + c0, n.nf, n.off + (int64_t)c1 * n.nf, n.nf,
+                           n.nf, b1, bp, 1, 1, Mask2{c0, c0 + bp, 0, 0}, none, 7);
+        else
+          blks += add_gemm(blks, n.off + (int64_t)c1 * n.nf + c0, n.nf, tR, n.nf, n.off + (int64_t)c1 * n.nf, n.nf,
+                           b1, n.nf, bp, 1, 1, none, Mask2{c0, c0 + bp, 0, 0});
         // column strip: A[r, c1..] -= C_old[r, :] TR[:, c1..], r outside panels p and p+1
         blks += add_gemm(blks, n.off + c0, n.nf, tR + c1, n.nf, n.off + c1, n.nf, n.nf, b1, bp, 1, 1,
                          Mask2{c0, c0 + bp, c1, c1 + b1}, none);

@@ -124,9 +124,11 @@ __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ 
   const int k = c * kChunk + lane;
   double2 v = make_double2(0, 0);
   if (isA) {
-    if (line < g.M && k < g.K) v = base[g.a + (int64_t)line * g.lda + k];
+    if (line < g.M && k < g.K)
+      v = base[g.a + ((g.trans & 1) ? (int64_t)k * g.lda + line : (int64_t)line * g.lda + k)];
   } else {
-    if (line < g.N && k < g.K) v = base[g.b + (int64_t)k * g.ldb + line];
+    if (line < g.N && k < g.K)
+      v = base[g.b + ((g.trans & 2) ? (int64_t)line * g.ldb + k : (int64_t)k * g.ldb + line)];
   }
   int ex = max(exp_of(v.x), exp_of(v.y));
 #pragma unroll
@@ -444,8 +446,10 @@ __global__ void __launch_bounds__(320, 1)
       const int r = tr.rb * 128 + rl, col0 = tr.j * kTileCx;
       const bool row_ok = r < g.M && !g.rmask.hit(r);
       const bool neg = g.neg != 0;
-      double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)r * g.ldc + col0;
-      if (row_ok && g.beta && col0 + 8 * grp < g.N)  // this group's C row segment into L1 while the MMAs run
+      const bool ctr = (g.trans & 4) != 0;  // C stored transposed: column stride ldc
+      const int64_t cs = ctr ? g.ldc : 1;
+      double2* crow = arena + blockIdx.y * stride + g.c + (ctr ? (int64_t)r : (int64_t)r * g.ldc) + col0 * cs;
+      if (row_ok && g.beta && !ctr && col0 + 8 * grp < g.N)  // this group's C row segment into L1 while the MMAs run
         asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + 8 * grp));
       const int s = i & 1, u = i >> 1;
       const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag);
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(320, 1)
         double2 cv[8];  // C row segment: all loads issued before any store
         if (g.beta) {
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[8 * hh + jj] : make_double2(0, 0);
+          for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[(8 * hh + jj) * cs] : make_double2(0, 0);
         }
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(320, 1)
           }
           double2 v = make_double2(vv[0], vv[1]);
           if (g.beta) v = cadd(v, cv[jj]);
-          crow[8 * hh + jj] = v;
+          crow[(8 * hh + jj) * cs] = v;
         }
       }
     }
@@ -771,12 +775,14 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) sx[jj] = __shfl_sync(0xffffffffu, Sc, jj);
       if (row >= g.M || g.rmask.hit(row)) continue;
-      double2* crow = arena + blockIdx.y * stride + g.c + (int64_t)row * g.ldc + c8;
+      const bool ctr = (g.trans & 4) != 0;  // C stored transposed: column stride ldc
+      const int64_t cs = ctr ? g.ldc : 1;
+      double2* crow = arena + blockIdx.y * stride + g.c + (ctr ? (int64_t)row : (int64_t)row * g.ldc) + c8 * cs;
       const bool neg = g.neg != 0;
       double2 cv[8];
       if (g.beta) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[jj] : make_double2(0, 0);
+        for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[jj * cs] : make_double2(0, 0);
       }
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
@@ -793,7 +799,7 @@ __global__ void __launch_bounds__(320, 1)
         }
         double2 v = make_double2(vv[0], vv[1]);
         if (g.beta) v = cadd(v, cv[jj]);
-        crow[jj] = v;
+        crow[jj * cs] = v;
       }
     }
   }

@@ -50,6 +50,9 @@ struct GemmDesc {
   int neg, beta;
   Mask2 rmask, cmask;
   int blk0, tilesN;  // first CTA of this problem inside its launch; tiles along N
+  // operands stored transposed (digit-GEMM path only): bit 0 A(i, k) at
+  // a + k lda + i, bit 1 B(k, j) at b + j ldb + k, bit 2 C(i, j) at c + j ldc + i
+  int trans = 0;
 };
 
 // In-place inverse of the diagonal panel block A[pp] (bp x bp, leading dim ld).

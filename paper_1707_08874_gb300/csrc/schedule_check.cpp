@@ -112,14 +112,17 @@ void footprint(const Plan& p, const Op& op, R&& visit_read, W&& visit_write) {
         for (int c = 0; c < g.N; ++c)
           if (!g.cmask.hit(c)) cols.push_back(c);
         if (rows.empty() || cols.empty()) continue;
+        auto ai = [&g](int r, int k) { return g.a + ((g.trans & 1) ? (int64_t)k * g.lda + r : (int64_t)r * g.lda + k); };
+        auto bi = [&g](int k, int c) { return g.b + ((g.trans & 2) ? (int64_t)c * g.ldb + k : (int64_t)k * g.ldb + c); };
+        auto ci = [&g](int r, int c) { return g.c + ((g.trans & 4) ? (int64_t)c * g.ldc + r : (int64_t)r * g.ldc + c); };
         for (int r : rows)
-          for (int k = 0; k < g.K; ++k) visit_read(g.a + (int64_t)r * g.lda + k);
+          for (int k = 0; k < g.K; ++k) visit_read(ai(r, k));
         for (int k = 0; k < g.K; ++k)
-          for (int c : cols) visit_read(g.b + (int64_t)k * g.ldb + c);
+          for (int c : cols) visit_read(bi(k, c));
         for (int r : rows)
           for (int c : cols) {
-            if (g.beta) visit_read(g.c + (int64_t)r * g.ldc + c);
-            visit_write(g.c + (int64_t)r * g.ldc + c);
+            if (g.beta) visit_read(ci(r, c));
+            visit_write(ci(r, c));
           }
       }
       break;
