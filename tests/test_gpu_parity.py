@@ -150,6 +150,24 @@ def test_fp64_repeatable_bitwise(prec):
     plan.close()
 
 
+def test_free_chain_sms_bitwise(monkeypatch):
+    """The SMs the bulk digit GEMMs leave to the panel chain only change which
+    persistent CTA computes which output tile: bitwise identical results."""
+    B = _binding()
+    U = inputs.random_links(6, 4, seed=9)
+    outs = []
+    for free in ("0", "2", "24"):
+        monkeypatch.setenv("CLSELINV_CHAIN_SMS", free)
+        plan = B.Plan.analyze(6, 4, 1, B.CL_FP64_EMU)
+        got, st = _run(plan, U)
+        assert st == B.CL_OK
+        outs.append(got)
+        plan.close()
+    for got in outs[1:]:
+        for key in ("Gdiag", "Gfwd", "Gbwd", "Kf"):
+            assert np.array_equal(got[key], outs[0][key]), key
+
+
 def test_nonfinite_status():
     """A NaN link is reported through the status word, not a fault."""
     B = _binding()
