@@ -250,13 +250,20 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&v)[16
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t (&v)[16]) { tmem_ld16_issue(taddr, v); }
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t (&v)[8]) { tmem_ld8_issue(taddr, v); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Persistent digit GEMM for launches whose problems all have K <= 32 (one
 // exponent chunk: the sweep updates of the factorisation and the panel
 // products).  One CTA per SM takes a contiguous range of output tiles (128
-// rows x 16 complex columns) of the launch; warp-specialised, 192 threads:
+// rows x 16 complex columns) of the launch; warp-specialised, 64 + 128 NG threads:
 //   warp 0 lane 0  producer: bulk copies of the current row block's A digits
 //                  (112 KB, kept while consecutive tiles share the block) and
 //                  of each tile's B' digits into a two-stage ring (28 KB);
@@ -265,9 +272,12 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 //                  0 .. 6-p) into one of two accumulator sets in tensor memory
 //                  (7 levels x 32 columns at TMEM columns 0 and 256), so the
 //                  MMAs of tile i+1 run while tile i is folded and written;
-//   warps 2-9      fold (thread = row) and FP64 epilogue in two groups of four
-//                  warps, each owning half of every tile's columns, so a
-//                  tile's fold and write-back take half as long as with one
+//   warps 2-17     fold (thread = row) and FP64 epilogue in NG = 4 groups of
+//                  four warps (2 with CLSELINV_FOLD_GROUPS=2), each owning
+//                  16/NG of every tile's complex columns: four warps per
+//                  scheduler hide the latency of the fold's dependent FP32
+//                  chains and of the write-back's FP64 additions, and a
+//                  tile's fold and write-back take 1/NG as long as with one
 //                  group per tile (the panel chain's small launches have one
 //                  tile per CTA); the C row segment is prefetched into L1.
 // With one chunk the row / column exponents are the chunk's own, the fold
@@ -306,7 +316,8 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, unsigned parity, cons
   }
 }
 
-__global__ void __launch_bounds__(320, 1)
+template <int NG>  // fold groups of four warps
+__global__ void __launch_bounds__(64 + 128 * NG, 1)
     k_gemm_emu_persist(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
                        double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
                        const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
@@ -339,8 +350,8 @@ __global__ void __launch_bounds__(320, 1)
   }
   if (tid == 32) {
     for (int i = 0; i < 7; ++i) mbar_init(bar(i), 1);
-    mbar_init(bar(7), 256);  // both fold groups drain an accumulator set
-    mbar_init(bar(8), 256);
+    mbar_init(bar(7), 128 * NG);  // every fold group drains an accumulator set
+    mbar_init(bar(8), 128 * NG);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -429,7 +440,8 @@ __global__ void __launch_bounds__(320, 1)
       if (*abort_flag && last >= 0) mbar_wait(bar(5 + (last & 1)), (last >> 1) & 1);  // MMAs in flight
     }
     __syncwarp();
-  } else {  // ---- fold and epilogue: thread = row; group g (warps 2-5, 6-9) owns complex columns 8g .. 8g+7
+  } else {  // ---- fold and epilogue: thread = row; group g (warps 2+4g .. 5+4g) owns complex columns CC g .. CC g + CC-1
+    constexpr int CR = 32 / NG, CC = CR / 2;  // real / complex columns of a group
     const int grp = (warp - 2) >> 2, q4 = warp & 3, rl = q4 * 32 + lane;
     int prev = -1, erow = 0;
     for (int i = 0; i < n; ++i) {
@@ -449,8 +461,8 @@ __global__ void __launch_bounds__(320, 1)
       const bool ctr = (g.trans & 4) != 0;  // C stored transposed: column stride ldc
       const int64_t cs = ctr ? g.ldc : 1;
       double2* crow = arena + blockIdx.y * stride + g.c + (ctr ? (int64_t)r : (int64_t)r * g.ldc) + col0 * cs;
-      if (row_ok && g.beta && !ctr && col0 + 8 * grp < g.N)  // this group's C row segment into L1 while the MMAs run
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + 8 * grp));
+      if (row_ok && g.beta && !ctr && col0 + CC * grp < g.N)  // this group's C row segment into L1 while the MMAs run
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + CC * grp));
       const int s = i & 1, u = i >> 1;
       const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
@@ -459,17 +471,17 @@ __global__ void __launch_bounds__(320, 1)
         break;
       }
       tc_fence_after();
-      {  // this group's 8 complex columns (16 TMEM columns per level)
+      {  // this group's CC complex columns (CR TMEM columns per level)
         const int hh = grp;
-        float h[16], mi[16], lo[16];
-        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + 16 * hh;
+        float h[CR], mi[CR], lo[CR];
+        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + CR * hh;
         {  // levels 0-3: four loads, one wait
-          uint32_t v[4][16];
+          uint32_t v[4][CR];
 #pragma unroll
-          for (int L = 0; L < 4; ++L) tmem_ld16_issue(ta + 32 * L, v[L]);
+          for (int L = 0; L < 4; ++L) tmem_ld_issue(ta + 32 * L, v[L]);
           tmem_ld_wait();
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
+          for (int k = 0; k < CR; ++k) {
             h[k] = __uint_as_float(v[0][k]) * 0x1p-16f;
             two_sum(h[k], __uint_as_float(v[1][k]) * 0x1p-24f, h[k], mi[k]);
             lo[k] = 0.f;
@@ -484,12 +496,12 @@ __global__ void __launch_bounds__(320, 1)
         }
         {  // levels 4-6, at most 2^-32 of the leading level: summed in FP32
            // (rounding below 2^-53 of it), then one error-free addition
-          uint32_t v[3][16];
+          uint32_t v[3][CR];
 #pragma unroll
-          for (int L = 0; L < 3; ++L) tmem_ld16_issue(ta + 32 * (L + 4), v[L]);
+          for (int L = 0; L < 3; ++L) tmem_ld_issue(ta + 32 * (L + 4), v[L]);
           tmem_ld_wait();
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
+          for (int k = 0; k < CR; ++k) {
             const float x = fmaf(__uint_as_float(v[2][k]), 0x1p-64f,
                                  fmaf(__uint_as_float(v[1][k]), 0x1p-56f, __uint_as_float(v[0][k]) * 0x1p-48f));
             float s2, e2;
@@ -501,21 +513,23 @@ __global__ void __launch_bounds__(320, 1)
         tc_fence_before();
         mbar_arrive(bar(7 + s));  // this group is done with accumulator set s
         if (!row_ok) continue;
-        const int c8 = col0 + 8 * hh;
-        int fe[8];
+        const int c8 = col0 + CC * hh;
+        int fe[CC];
         {
           const int4* fp = reinterpret_cast<const int4*>(Id + bexp + c8);
-          const int4 x0 = fp[0], x1 = fp[1];
-          fe[0] = x0.x, fe[1] = x0.y, fe[2] = x0.z, fe[3] = x0.w;
-          fe[4] = x1.x, fe[5] = x1.y, fe[6] = x1.z, fe[7] = x1.w;
+#pragma unroll
+          for (int q = 0; q < CC / 4; ++q) {
+            const int4 x = fp[q];
+            fe[4 * q] = x.x, fe[4 * q + 1] = x.y, fe[4 * q + 2] = x.z, fe[4 * q + 3] = x.w;
+          }
         }
-        double2 cv[8];  // C row segment: all loads issued before any store
+        double2 cv[CC];  // C row segment: all loads issued before any store
         if (g.beta) {
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[(8 * hh + jj) * cs] : make_double2(0, 0);
+          for (int jj = 0; jj < CC; ++jj) cv[jj] = c8 + jj < g.N ? crow[(CC * hh + jj) * cs] : make_double2(0, 0);
         }
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
+        for (int jj = 0; jj < CC; ++jj) {
           const int cc = c8 + jj;
           if (cc >= g.N || g.cmask.hit(cc)) continue;
           const int ex = erow + fe[jj];
@@ -529,7 +543,7 @@ __global__ void __launch_bounds__(320, 1)
           }
           double2 v = make_double2(vv[0], vv[1]);
           if (g.beta) v = cadd(v, cv[jj]);
-          crow[(8 * hh + jj) * cs] = v;
+          crow[(CC * hh + jj) * cs] = v;
         }
       }
     }
@@ -548,21 +562,25 @@ __global__ void __launch_bounds__(320, 1)
 // selected inversion, K up to a pivot block).  One CTA per SM over a
 // contiguous range of output tiles (128 rows x 16 complex columns); per tile
 // its chunks of 32 complex k in order, each chunk in two halves of 32 real k.
-// Warp-specialised, 320 threads:
+// Warp-specialised, 64 + 128 NG threads:
 //   warp 0 lane 0  producer: per half, the 7 A digit half-tiles (56 KB) and
 //                  the B' half-block (14 KB) into a three-stage ring;
 //   warp 1 lane 0  MMA issuer: 14 wide MMAs per half into one of two TMEM
 //                  accumulator sets (set = chunk parity), so the MMAs of
 //                  chunk k+1 run while chunk k is folded;
-//   warps 2-9      fold: two groups of four warps, group g owning complex
+//   warps 2-9      fold: NG = 2 groups of four warps, group g owning complex
 //                  columns 8g .. 8g+7 of the tile (thread = row), fold each
 //                  chunk's levels into triple-float with the chunk's row /
-//                  column exponents and write the tile after its last chunk.
+//                  column exponents and write the tile after its last chunk
+//                  (four groups, 96 registers with spills, measured ~1%
+//                  slower on the selected inversion).
 constexpr int kCStage = kDig * (kAHalf + kBHalf);  // bytes per ring stage
+constexpr int kChunkedGroups = 2;  // fold groups of the chunked kernel
 constexpr int kCStages = 3;
 constexpr size_t kCSmemBytes = (size_t)kCStages * kCStage + 1024;
 
-__global__ void __launch_bounds__(320, 1)
+template <int NG>  // fold groups of four warps
+__global__ void __launch_bounds__(64 + 128 * NG, 1)
     k_gemm_emu_chunked(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
                        double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
                        const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
@@ -593,8 +611,8 @@ __global__ void __launch_bounds__(320, 1)
   }
   if (tid == 32) {
     for (int i = 0; i < 8; ++i) mbar_init(bar(i), 1);
-    mbar_init(bar(8), 256);  // both fold groups drain a set
-    mbar_init(bar(9), 256);
+    mbar_init(bar(8), 128 * NG);  // every fold group drains a set
+    mbar_init(bar(9), 128 * NG);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -674,7 +692,8 @@ __global__ void __launch_bounds__(320, 1)
       if (*abort_flag && k > 0) mbar_wait(bar(6 + ((k - 1) & 1)), ((k - 1) >> 1) & 1);  // MMAs in flight
     }
     __syncwarp();
-  } else {  // ---- fold and epilogue
+  } else {  // ---- fold and epilogue: group g owns complex columns CC g .. CC g + CC-1 of the tile
+    constexpr int CR = 32 / NG, CC = CR / 2;  // real / complex columns of a group
     const int grp = (warp - 2) >> 2, q4 = warp & 3, rl = q4 * 32 + lane;
     int k = 0;
     bool stop = false;
@@ -683,28 +702,28 @@ __global__ void __launch_bounds__(320, 1)
       const GemmDesc g = gd[tr.di];
       const EmuDesc e = ed[tr.di];
       const int nch = e.Kp / kChunk;
-      const int row = tr.rb * 128 + rl, c8 = tr.j * kTileCx + 8 * grp;
+      const int row = tr.rb * 128 + rl, c8 = tr.j * kTileCx + CC * grp;
       // row / column maxima of the chunk exponents (column jj = lane jj of each warp)
       int Rm = -4000, Sc = -4000;
       for (int c = 0; c < nch; ++c) {
         Rm = max(Rm, Id[e.aexp + (int64_t)c * e.Mp + row]);
-        if (lane < 8) Sc = max(Sc, Id[e.bexp + (int64_t)c * e.Np + c8 + lane]);
+        if (lane < CC) Sc = max(Sc, Id[e.bexp + (int64_t)c * e.Np + c8 + lane]);
       }
       int ra = nch > 0 ? Id[e.aexp + row] : 0;
-      int cb = (lane < 8 && nch > 0) ? Id[e.bexp + c8 + lane] : 0;
-      float h[16], mi[16], lo[16];
+      int cb = (lane < CC && nch > 0) ? Id[e.bexp + c8 + lane] : 0;
+      float h[CR], mi[CR], lo[CR];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) h[i] = mi[i] = lo[i] = 0.f;
+      for (int i = 0; i < CR; ++i) h[i] = mi[i] = lo[i] = 0.f;
       for (int c = 0; c < nch; ++c, ++k) {
         __syncwarp();
         const int rsc = ra - Rm - 16, csc = cb - Sc;
         if (c + 1 < nch) {
           ra = Id[e.aexp + (int64_t)(c + 1) * e.Mp + row];
-          if (lane < 8) cb = Id[e.bexp + (int64_t)(c + 1) * e.Np + c8 + lane];
+          if (lane < CC) cb = Id[e.bexp + (int64_t)(c + 1) * e.Np + c8 + lane];
         }
-        float sc[8];  // 2^{(e_i - R_i) + (f_n - S_n) - 16}
+        float sc[CC];  // 2^{(e_i - R_i) + (f_n - S_n) - 16}
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) sc[jj] = pow2f(rsc + __shfl_sync(0xffffffffu, csc, jj));
+        for (int jj = 0; jj < CC; ++jj) sc[jj] = pow2f(rsc + __shfl_sync(0xffffffffu, csc, jj));
         const int set = k & 1, uk = k >> 1;
         const bool got = mbar_wait_ab(bar(6 + set), uk & 1, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
@@ -714,13 +733,13 @@ __global__ void __launch_bounds__(320, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * set + 16 * grp;
+        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * set + CR * grp;
 #pragma unroll
         for (int b4 = 0; b4 < 2; ++b4) {  // levels 0-3, then 4-6
           const int L0 = 4 * b4, nl = b4 ? 3 : 4;
-          uint32_t v[4][16];
+          uint32_t v[4][CR];
 #pragma unroll
-          for (int l = 0; l < nl; ++l) tmem_ld16_issue(ta + 32 * (L0 + l), v[l]);
+          for (int l = 0; l < nl; ++l) tmem_ld_issue(ta + 32 * (L0 + l), v[l]);
           tmem_ld_wait();
           if (b4) {
             tc_fence_before();
@@ -728,7 +747,7 @@ __global__ void __launch_bounds__(320, 1)
           }
           if (b4) {  // levels 4-6 (<= 2^-32 of the leading level): FP32 sum, one error-free addition
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < CR; ++i) {
               const float c = sc[i >> 1];
               const float x = fmaf(__uint_as_float(v[2][i]), c * 0x1p-48f,
                                    fmaf(__uint_as_float(v[1][i]), c * 0x1p-40f, __uint_as_float(v[0][i]) * (c * 0x1p-32f)));
@@ -742,7 +761,7 @@ __global__ void __launch_bounds__(320, 1)
             for (int l = 0; l < 4; ++l) {
               const float cL = __int_as_float((127 - 8 * l) << 23);  // 2^{-8L}
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
+              for (int i = 0; i < CR; ++i) {
                 const float x = __uint_as_float(v[l][i]) * (sc[i >> 1] * cL);
                 float s1, e1, s2, e2;
                 if (l < 2) {
@@ -759,7 +778,7 @@ __global__ void __launch_bounds__(320, 1)
           }
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < CR; ++i) {
           float s1, e1, s2, e2;
           two_sum(h[i], mi[i], s1, e1);
           two_sum(e1, lo[i], s2, e2);
@@ -771,21 +790,21 @@ __global__ void __launch_bounds__(320, 1)
       if (stop) break;
       // epilogue of the tile: value = (h + mi + lo) 2^{R_i + S_n}; C = beta C -/+ value.
       // Column maxima from lanes 0-7, shuffled while every lane is present.
-      int sx[8];
+      int sx[CC];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) sx[jj] = __shfl_sync(0xffffffffu, Sc, jj);
+      for (int jj = 0; jj < CC; ++jj) sx[jj] = __shfl_sync(0xffffffffu, Sc, jj);
       if (row >= g.M || g.rmask.hit(row)) continue;
       const bool ctr = (g.trans & 4) != 0;  // C stored transposed: column stride ldc
       const int64_t cs = ctr ? g.ldc : 1;
       double2* crow = arena + blockIdx.y * stride + g.c + (ctr ? (int64_t)row : (int64_t)row * g.ldc) + c8 * cs;
       const bool neg = g.neg != 0;
-      double2 cv[8];
+      double2 cv[CC];
       if (g.beta) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) cv[jj] = c8 + jj < g.N ? crow[jj * cs] : make_double2(0, 0);
+        for (int jj = 0; jj < CC; ++jj) cv[jj] = c8 + jj < g.N ? crow[jj * cs] : make_double2(0, 0);
       }
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+      for (int jj = 0; jj < CC; ++jj) {
         const int cc = c8 + jj;
         const int ex = Rm + sx[jj];
         if (cc >= g.N || g.cmask.hit(cc)) continue;
@@ -817,9 +836,23 @@ __global__ void __launch_bounds__(320, 1)
 // opt the GEMM kernel in to > 48 KB of dynamic shared memory on the current
 // device (done when a plan is set up, outside any stream capture)
 cudaError_t emu_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_chunked<kChunkedGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kCSmemBytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm_emu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
+  e = cudaFuncSetAttribute(k_gemm_emu_persist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_emu_persist<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
+}
+
+// fold groups of the persistent digit GEMM: four (576 threads, 96 registers)
+// unless CLSELINV_FOLD_GROUPS=2 (measured at 8^3x4: 63.0 -> 66.4 evals/s,
+// batch 64 77.5 -> 85.4; 12^3x6 0.477 -> 0.417 s)
+int fold_groups() {
+  static const int ng = [] {
+    const char* v = std::getenv("CLSELINV_FOLD_GROUPS");
+    return v && v[0] == '2' ? 2 : 4;
+  }();
+  return ng;
 }
 
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
@@ -832,10 +865,13 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
   const LaunchOpt lg{lo.prio, pdl_enabled()};  // follows the split pass in the same stream
   const dim3 gp((unsigned)std::min(blocks, std::max(max_ctas, 1)), (unsigned)batch);
   if (single_chunk)  // blocks = output tiles of the launch; persistent CTAs over ranges of tiles
-    return launch_k(k_gemm_emu_persist, gp, dim3(320), kPSmemBytes, st, lg, gd, ed, d0, d1, blocks, arena, stride,
-                    (const unsigned*)words, (const int*)ints, wstride, istride, status);
-  return launch_k(k_gemm_emu_chunked, gp, dim3(320), kCSmemBytes, st, lg, gd, ed, d0, d1, blocks, arena, stride,
-                  (const unsigned*)words, (const int*)ints, wstride, istride, status);
+    return fold_groups() == 4
+               ? launch_k(k_gemm_emu_persist<4>, gp, dim3(64 + 128 * 4), kPSmemBytes, st, lg, gd, ed, d0, d1, blocks,
+                          arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status)
+               : launch_k(k_gemm_emu_persist<2>, gp, dim3(64 + 128 * 2), kPSmemBytes, st, lg, gd, ed, d0, d1, blocks,
+                          arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status);
+  return launch_k(k_gemm_emu_chunked<kChunkedGroups>, gp, dim3(64 + 128 * kChunkedGroups), kCSmemBytes, st, lg, gd,
+                  ed, d0, d1, blocks, arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status);
 }
 
 // A persistent bulk CTA (320 threads x 168 registers) leaves too few
