@@ -461,8 +461,22 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
       const bool ctr = (g.trans & 4) != 0;  // C stored transposed: column stride ldc
       const int64_t cs = ctr ? g.ldc : 1;
       double2* crow = arena + blockIdx.y * stride + g.c + (ctr ? (int64_t)r : (int64_t)r * g.ldc) + col0 * cs;
-      if (row_ok && g.beta && !ctr && col0 + CC * grp < g.N)  // this group's C row segment into L1 while the MMAs run
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + CC * grp));
+      // this group's column exponents and C row segment, loaded while the MMAs run
+      const int c8 = col0 + CC * grp;
+      int fe[CC];
+      {
+        const int4* fp = reinterpret_cast<const int4*>(Id + bexp + c8);
+#pragma unroll
+        for (int q = 0; q < CC / 4; ++q) {
+          const int4 x = fp[q];
+          fe[4 * q] = x.x, fe[4 * q + 1] = x.y, fe[4 * q + 2] = x.z, fe[4 * q + 3] = x.w;
+        }
+      }
+      double2 cv[CC];
+      if (row_ok && g.beta) {
+#pragma unroll
+        for (int jj = 0; jj < CC; ++jj) cv[jj] = c8 + jj < g.N ? crow[(CC * grp + jj) * cs] : make_double2(0, 0);
+      }
       const int s = i & 1, u = i >> 1;
       const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
@@ -513,21 +527,6 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         tc_fence_before();
         mbar_arrive(bar(7 + s));  // this group is done with accumulator set s
         if (!row_ok) continue;
-        const int c8 = col0 + CC * hh;
-        int fe[CC];
-        {
-          const int4* fp = reinterpret_cast<const int4*>(Id + bexp + c8);
-#pragma unroll
-          for (int q = 0; q < CC / 4; ++q) {
-            const int4 x = fp[q];
-            fe[4 * q] = x.x, fe[4 * q + 1] = x.y, fe[4 * q + 2] = x.z, fe[4 * q + 3] = x.w;
-          }
-        }
-        double2 cv[CC];  // C row segment: all loads issued before any store
-        if (g.beta) {
-#pragma unroll
-          for (int jj = 0; jj < CC; ++jj) cv[jj] = c8 + jj < g.N ? crow[(CC * hh + jj) * cs] : make_double2(0, 0);
-        }
 #pragma unroll
         for (int jj = 0; jj < CC; ++jj) {
           const int cc = c8 + jj;
