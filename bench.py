@@ -39,7 +39,7 @@ NS, NT, M, MU = 8, 4, 0.05, 0.25
 # averaged over the 269 GEMM launches of one 8^3x4 evaluation with
 # 30-unknown panels, ncu, cold cache; profiles/gemm_emu_tcgen05_8x4.md);
 # valid for the kernels it was taken on, keyed by (precision, batch, panel)
-NCU_TRAFFIC = {("fp64_emu", 1, 30): 63.70e6}
+NCU_TRAFFIC = {("fp64_emu", 1, 30): 63.67e6}
 
 
 def measured_bf16_tflops():
