@@ -29,6 +29,16 @@
  *  - Return values are CL_* status codes.  Launch-time failures come back
  *    directly; numerical failures (a tiny pivot, a non-finite result) are
  *    recorded in a device status word and read with cl_get_status().
+ *
+ * Environment (tuning only; results are bitwise the same either way)
+ * ------------------------------------------------------------------
+ *  - CLSELINV_CHAIN_SMS=n: SMs the bulk digit-GEMM launches of a two-stream
+ *    factorisation leave free for the panel chain (default 2; read when a
+ *    plan is created).
+ *  - CLSELINV_PDL=0: no programmatic dependent launch between the front
+ *    kernels (default on; read once per process).
+ *  - CLSELINV_FOLD_GROUPS=2: two instead of four fold groups in the
+ *    persistent digit GEMM (read once per process).
  */
 #ifndef CLSELINV_H
 #define CLSELINV_H

@@ -873,7 +873,7 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
                   ed, d0, d1, blocks, arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status);
 }
 
-// A persistent bulk CTA (320 threads x 168 registers) leaves too few
+// A persistent bulk CTA (576 threads x 96 registers) leaves too few
 // registers on its SM for a panel-inverse CTA, so a bulk launch over every SM
 // would hold the next panel until the whole bulk update ends: bulk launches
 // (stream 1) leave p.chain_sms SMs to the panel chain.
