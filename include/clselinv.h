@@ -351,6 +351,47 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
                            int first_len);
 
 /*
+ * cl_plan_export -- one of the plan's schedule tables as rows of int64, for
+ * host-side checks of the schedule (a test executes the op lists in FP64 on
+ * the host and compares with an independent dense inverse).  With out ==
+ * NULL only *count (the number of int64 values) is set; otherwise out must
+ * hold cap >= *count values.  Row layouts:
+ *   CL_TABLE_META        Ns, Nt, V, N, precision, panel, pool_elems,
+ *                        tmp_elems, arena_elems, n_levels
+ *   CL_TABLE_FACTOR_OPS, CL_TABLE_SELINV_OPS
+ *                        kind (0 zero, 1 assemble, 2 extend-add, 3 panel,
+ *                        4 gemm, 5 copy, 6 gather, 7 extract), d0, d1, blocks,
+ *                        level, stream, wait, signal
+ *   CL_TABLE_GEMM        a, b, c, lda, ldb, ldc, M, N, K, neg, beta,
+ *                        rmask[4], cmask[4], trans (bit 0 A, 1 B, 2 C stored
+ *                        transposed)
+ *   CL_TABLE_PANEL       a, ld, bp, node, col0
+ *   CL_TABLE_COPY        src, dst, lds, ldd, rows, cols, rmask[4], cmask[4]
+ *   CL_TABLE_EXTADD      parent, nfp, nchild, child[2], nfc[2], kc[2], map[2]
+ *   CL_TABLE_GATHER      child, parent, nfc, kc, nfp, rs, map
+ *   CL_TABLE_MAPS        the site maps of extend-add and gather
+ *   CL_TABLE_OFF, CL_TABLE_LD
+ *                        offset / leading dimension of the D blocks in the
+ *                        fronts: [V] diagonal, [4V] (s, s+nu), [4V] (s+nu, s)
+ * Offsets are elements of one replica's arena; a mask [r0, r1, r2, r3]
+ * excludes the indices in [r0, r1) and [r2, r3).  Works on symbolic plans.
+ */
+enum {
+  CL_TABLE_META = 0,
+  CL_TABLE_FACTOR_OPS = 1,
+  CL_TABLE_SELINV_OPS = 2,
+  CL_TABLE_GEMM = 3,
+  CL_TABLE_PANEL = 4,
+  CL_TABLE_COPY = 5,
+  CL_TABLE_EXTADD = 6,
+  CL_TABLE_GATHER = 7,
+  CL_TABLE_MAPS = 8,
+  CL_TABLE_OFF = 9,
+  CL_TABLE_LD = 10
+};
+int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count);
+
+/*
  * cl_profile_enable -- enable (1) or disable (0) per-launch timing: while
  * enabled, every compute call records a CUDA event pair on its stream around
  * each kernel launch (this adds event records between launches; use it to

@@ -79,7 +79,11 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
            "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
-           "cl_analyze_symbolic_ex"]
+           "cl_analyze_symbolic_ex", "cl_plan_export"]
+
+# cl_plan_export tables (include/clselinv.h) and their int64 row widths
+TABLES = {"meta": (0, 10), "factor_ops": (1, 8), "selinv_ops": (2, 8), "gemm": (3, 20), "panel": (4, 5),
+          "copy": (5, 14), "extadd": (6, 11), "gather": (7, 7), "maps": (8, 1), "off": (9, 1), "ld": (10, 1)}
 
 
 def lib_path() -> str:
@@ -128,6 +132,7 @@ def load(build_if_missing: bool = True):
     L.cl_group_destroy.restype = None
     L.cl_zgemm_emu_workspace.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_size_t)]
     L.cl_plan_check_schedule.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, I]
+    L.cl_plan_export.argtypes = [P, I, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
     L.cl_zgemm_emu.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, ctypes.c_size_t, P, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
@@ -259,6 +264,21 @@ class Plan:
         _check(load().cl_plan_check_schedule(self._h, int(ignore_waits), ctypes.byref(n), buf, 256),
                "cl_plan_check_schedule")
         return n.value, buf.value.decode()
+
+    def export_tables(self) -> dict:
+        """The plan's schedule tables (cl_plan_export) as int64 numpy arrays,
+        one row per descriptor."""
+        import numpy as np
+        L = load()
+        out = {}
+        for name, (table, width) in TABLES.items():
+            n = ctypes.c_longlong()
+            _check(L.cl_plan_export(self._h, table, None, 0, ctypes.byref(n)), "cl_plan_export")
+            a = np.zeros(max(n.value, 1), dtype=np.int64)
+            _check(L.cl_plan_export(self._h, table, ctypes.c_void_p(a.ctypes.data), n.value, ctypes.byref(n)),
+                   "cl_plan_export")
+            out[name] = a[:n.value].reshape(-1, width) if width > 1 else a[:n.value]
+        return out
 
     def node(self, i: int) -> dict:
         L = load()

@@ -1,3 +1,4 @@
+#include <algorithm>
 #include <cstdlib>
 // C ABI of the library (declared in clselinv.h): plan creation, device memory
 // of the plan, and the stream-ordered compute calls.
@@ -470,6 +471,67 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
     std::strncpy(first, msg.c_str(), (size_t)first_len - 1);
     first[first_len - 1] = 0;
   }
+  return CL_OK;
+}
+
+int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count) {
+  if (!plan || !count || table < 0 || table > CL_TABLE_LD) return CL_ERR_INVALID_ARG;
+  const cl::Plan& p = plan->p;
+  std::vector<long long> v;
+  auto mask = [&v](const cl::Mask2& m) { v.insert(v.end(), {m.r0, m.r1, m.r2, m.r3}); };
+  switch (table) {
+    case CL_TABLE_META:
+      v = {p.Ns, p.Nt, p.V, p.N, p.precision, p.panel, p.pool_elems, p.tmp_elems, p.arena_elems, p.n_levels};
+      break;
+    case CL_TABLE_FACTOR_OPS:
+    case CL_TABLE_SELINV_OPS:
+      for (const auto& op : table == CL_TABLE_FACTOR_OPS ? p.factor_ops : p.selinv_ops)
+        v.insert(v.end(), {(long long)op.kind, op.d0, op.d1, op.blocks, op.level, op.stream, op.wait, op.signal});
+      break;
+    case CL_TABLE_GEMM:
+      for (const auto& g : p.gemm) {
+        v.insert(v.end(), {g.a, g.b, g.c, g.lda, g.ldb, g.ldc, g.M, g.N, g.K, g.neg, g.beta});
+        mask(g.rmask);
+        mask(g.cmask);
+        v.push_back(g.trans);
+      }
+      break;
+    case CL_TABLE_PANEL:
+      for (const auto& d : p.panels) v.insert(v.end(), {d.a, d.ld, d.bp, d.node, d.col0});
+      break;
+    case CL_TABLE_COPY:
+      for (const auto& d : p.copies) {
+        v.insert(v.end(), {d.src, d.dst, d.lds, d.ldd, d.rows, d.cols});
+        mask(d.rmask);
+        mask(d.cmask);
+      }
+      break;
+    case CL_TABLE_EXTADD:
+      for (const auto& d : p.extadd)
+        v.insert(v.end(), {d.parent, d.nfp, d.nchild, d.child[0], d.child[1], d.nfc[0], d.nfc[1], d.kc[0], d.kc[1],
+                           d.map[0], d.map[1]});
+      break;
+    case CL_TABLE_GATHER:
+      for (const auto& d : p.gather) v.insert(v.end(), {d.child, d.parent, d.nfc, d.kc, d.nfp, d.rs, d.map});
+      break;
+    case CL_TABLE_MAPS:
+      v.assign(p.maps.begin(), p.maps.end());
+      break;
+    case CL_TABLE_OFF:
+      v.insert(v.end(), p.off_diag.begin(), p.off_diag.end());
+      v.insert(v.end(), p.off_fwd.begin(), p.off_fwd.end());
+      v.insert(v.end(), p.off_bwd.begin(), p.off_bwd.end());
+      break;
+    case CL_TABLE_LD:
+      v.insert(v.end(), p.ld_diag.begin(), p.ld_diag.end());
+      v.insert(v.end(), p.ld_fwd.begin(), p.ld_fwd.end());
+      v.insert(v.end(), p.ld_bwd.begin(), p.ld_bwd.end());
+      break;
+  }
+  *count = (long long)v.size();
+  if (!out) return CL_OK;
+  if (cap < (long long)v.size()) return CL_ERR_INVALID_ARG;
+  std::copy(v.begin(), v.end(), out);
   return CL_OK;
 }
 

@@ -1,0 +1,170 @@
+"""Host execution of a plan's schedule (no GPU).
+
+The analyser turns the nested dissection into op lists over descriptor tables
+(front offsets, masks, transposed operands, look-ahead strips, write-backs,
+extend-add and gather maps).  Here those tables, read through
+cl_plan_export, are executed in list order in FP64 on the host, each kernel
+reduced to its definition (panel inverse = a dense inverse of the block,
+GEMM = C <- beta C -/+ A B on the unmasked entries, ...), with the dense D of
+the oracle assembled into the fronts.  The extracted blocks must equal the
+oracle's blocks of D^{-1} to the FP64 parity bar: this checks the
+arithmetic of the schedule itself, independently of the CUDA kernels (the
+race check covers the ordering of its two streams).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1707_08874_gb300 import binding as B
+from paper_1707_08874_gb300 import build as libbuild
+from paper_1707_08874_gb300 import inputs
+
+OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT = range(8)
+M, MU = 0.05, 0.25
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    libbuild.build()
+    return B.load()
+
+
+def _site(x, y, z, t, Ns):
+    return ((t * Ns + z) * Ns + y) * Ns + x
+
+
+def _fwd(s, nu, Ns, Nt):
+    x, r = s % Ns, s // Ns
+    y, r = r % Ns, r // Ns
+    z, t = r % Ns, r // Ns
+    c = [x, y, z, t]
+    c[nu] = (c[nu] + 1) % (Nt if nu == 3 else Ns)
+    return _site(*c, Ns)
+
+
+def _hit(m, idx):
+    return ((idx >= m[0]) & (idx < m[1])) | ((idx >= m[2]) & (idx < m[3]))
+
+
+def _grid(base, rows, cols, ld, trans=False):
+    """element indices of a rows x cols operand: (i, j) at base + i ld + j,
+    or at base + j ld + i when stored transposed"""
+    i = np.arange(rows, dtype=np.int64)[:, None]
+    j = np.arange(cols, dtype=np.int64)[None, :]
+    return base + (j * ld + i if trans else i * ld + j)
+
+
+def execute(t, D, Ns, Nt):
+    meta = t["meta"][0]
+    V, pool, n_arena = int(meta[2]), int(meta[6]), int(meta[8])
+    A = np.full(n_arena, np.nan + 0j)  # the workspace is never read before it is written
+    off, ld, maps = t["off"], t["ld"], t["maps"]
+    out = {}
+    for ops in (t["factor_ops"], t["selinv_ops"]):
+        for kind, d0, d1, blocks, *_ in ops:
+            if blocks == 0 and kind != OP_ZERO:
+                continue
+            writes = []  # (indices, values): every descriptor reads the state before the op
+            if kind == OP_ZERO:
+                writes.append((np.arange(pool), np.zeros(pool)))
+            elif kind == OP_ASSEMBLE:
+                for s in range(V):
+                    blocks3 = [(s, s, off[s], ld[s])]
+                    for nu in range(4):
+                        y = _fwd(s, nu, Ns, Nt)
+                        blocks3.append((s, y, off[V + 4 * s + nu], ld[V + 4 * s + nu]))
+                        blocks3.append((y, s, off[5 * V + 4 * s + nu], ld[5 * V + 4 * s + nu]))
+                    for a, b, o, l in blocks3:
+                        writes.append((_grid(o, 3, 3, l), D[3 * a:3 * a + 3, 3 * b:3 * b + 3]))
+            elif kind == OP_EXTADD:
+                for parent, nfp, nchild, c0, c1, f0, f1, k0, k1, m0, m1 in t["extadd"][d0:d1]:
+                    acc = np.zeros((nfp, nfp), complex)
+                    hit = np.zeros((nfp, nfp), bool)
+                    I = np.arange(nfp)
+                    for child, nfc, kc, mp in ((c0, f0, k0, m0), (c1, f1, k1, m1))[:nchild]:
+                        ci = maps[mp + I // 3]
+                        ok = ci >= 0
+                        pos = kc + 3 * ci + I % 3
+                        sel = np.ix_(I[ok], I[ok])
+                        acc[sel] += A[child + pos[ok][:, None] * nfc + pos[ok][None, :]]
+                        hit[sel] = True
+                    idx = _grid(parent, nfp, nfp, nfp)
+                    writes.append((idx[hit], A[idx][hit] + acc[hit]))
+            elif kind == OP_PANEL:
+                for a, l, bp, *_ in t["panel"][d0:d1]:
+                    idx = _grid(a, bp, bp, l)
+                    writes.append((idx, np.linalg.inv(A[idx])))
+            elif kind == OP_GEMM:
+                for (a, b, c, lda, ldb, ldc, Mg, Ng, Kg, neg, beta, *mk) in t["gemm"][d0:d1]:
+                    rm, cm, tr = mk[0:4], mk[4:8], mk[8]
+                    P = A[_grid(a, Mg, Kg, lda, tr & 1)] @ A[_grid(b, Kg, Ng, ldb, tr & 2)]
+                    idx = _grid(c, Mg, Ng, ldc, tr & 4)
+                    val = (A[idx] if beta else 0) + (-P if neg else P)
+                    keep = ~_hit(rm, np.arange(Mg))[:, None] & ~_hit(cm, np.arange(Ng))[None, :]
+                    writes.append((idx[keep], val[keep]))
+            elif kind == OP_COPY:
+                for src, dst, lds, ldd, rows, cols, *mk in t["copy"][d0:d1]:
+                    keep = ~_hit(mk[0:4], np.arange(rows))[:, None] & ~_hit(mk[4:8], np.arange(cols))[None, :]
+                    writes.append((_grid(dst, rows, cols, ldd)[keep], A[_grid(src, rows, cols, lds)][keep]))
+            elif kind == OP_GATHER:
+                for child, parent, nfc, kc, nfp, rs, mp in t["gather"][d0:d1]:
+                    I = np.arange(3 * rs)
+                    pi = 3 * maps[mp + I // 3] + I % 3
+                    writes.append((child + (kc + I[:, None]) * nfc + kc + I[None, :],
+                                   A[parent + pi[:, None] * nfp + pi[None, :]]))
+            elif kind == OP_EXTRACT:
+                blk = lambda o, l: A[_grid(o, 3, 3, l)]
+                out["Gdiag"] = np.array([blk(off[s], ld[s]) for s in range(V)])
+                out["Gfwd"] = np.array([[blk(off[V + 4 * s + nu], ld[V + 4 * s + nu]) for nu in range(4)]
+                                        for s in range(V)])
+                out["Gbwd"] = np.array([[blk(off[5 * V + 4 * s + nu], ld[5 * V + 4 * s + nu]) for nu in range(4)]
+                                        for s in range(V)])
+            for idx, val in writes:
+                A[idx] = val
+    return out
+
+
+def _blockwise(a, b):
+    da = np.sqrt((np.abs(a - b) ** 2).sum((-1, -2)))
+    nb = np.sqrt((np.abs(b) ** 2).sum((-1, -2)))
+    return da.max() / nb.max()
+
+
+_REF = {}
+
+
+def _reference(Ns, Nt):
+    if (Ns, Nt) not in _REF:
+        U = inputs.random_links(Ns, Nt, seed=1707)
+        D = oracle.dirac_dense(Ns, Nt, U, M, MU)
+        sv = np.linalg.svd(D, compute_uv=False)
+        _REF[(Ns, Nt)] = (D, oracle.drift_eval(Ns, Nt, U, M, MU), max(1e-10, 1e-13 * sv[0] / sv[-1]))
+    return _REF[(Ns, Nt)]
+
+
+@pytest.mark.parametrize("ns,nt,prec,panel", [
+    (4, 4, B.CL_FP64, 48), (4, 4, B.CL_FP64_EMU, 30), (4, 4, B.CL_MIXED_FP32, 30), (4, 4, B.CL_FP64_EMU, 12),
+    (4, 4, B.CL_FP64_EMU, 24), (4, 4, B.CL_FP64_EMU, 27), (4, 4, B.CL_FP64, 3), (4, 6, B.CL_FP64_EMU, 30),
+    (6, 4, B.CL_FP64_EMU, 30), (6, 4, B.CL_FP64, 48)])
+def test_schedule_reproduces_dense_inverse(ns, nt, prec, panel):
+    D, ref, tol = _reference(ns, nt)
+    tables = B.Plan.analyze_symbolic(ns, nt, prec, panel).export_tables()
+    assert int(tables["meta"][0][5]) == panel
+    if prec == B.CL_FP64_EMU:  # the panel products with few rows are issued transposed
+        assert (tables["gemm"][:, 19] == 7).any()
+    got = execute(tables, D, ns, nt)
+    for key in ("Gdiag", "Gfwd", "Gbwd"):
+        err = _blockwise(got[key], ref[key])
+        assert err < tol, (key, err, tol)
+
+
+def test_schedule_executor_sees_a_broken_table():
+    """The check has teeth: one dropped bulk update (a GEMM descriptor of the
+    factorisation turned into a no-op) must spoil the result."""
+    D, ref, tol = _reference(4, 4)
+    tables = B.Plan.analyze_symbolic(4, 4, B.CL_FP64_EMU, 30).export_tables()
+    bulk = [i for i, row in enumerate(tables["gemm"]) if row[10] == 1 and row[6] > 64 and row[7] > 64]
+    assert bulk
+    tables["gemm"][bulk[0], 8] = 0  # K = 0: the product adds nothing
+    got = execute(tables, D, 4, 4)
+    assert _blockwise(got["Gfwd"], ref["Gfwd"]) > 1e3 * tol
