@@ -156,3 +156,50 @@ def test_renorm_det_pins():
     assert np.abs(L.renorm_det(U) - U).max() < 1e-13 * np.abs(U).max()
     c = rng.uniform(0.5, 2.0)
     assert np.abs(L.renorm_det(c * A) - R).max() < 1e-13 * np.abs(R).max()
+
+
+def _sl3(rng):
+    """a random SL(3,C) matrix (non-unitary, non-diagonal)"""
+    A = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3)) + 2 * np.eye(3)
+    return A / np.linalg.det(A) ** (1.0 / 3.0)
+
+
+def test_observables_closed_form_planes_and_time_order():
+    """Links with a closed-form answer that tells the plaquette planes and the
+    time order of the Polyakov product apart (c10).  All spatial links are one
+    diagonal SL(3,C) matrix Dg (they commute, so every spatial plaquette is the
+    identity), the temporal links of time slice t are one non-diagonal
+    SL(3,C) matrix W_t, constant in space.  Then
+      plaq_s = 1,
+      plaq_t = (1/3) mean_t Tr(Dg W_t Dg^{-1} W_t^{-1})      (path x -> x+mu -> x+mu+t -> x+t),
+      P  = (1/3) Tr(W_0 W_1 ... W_{Nt-1}),  P' = (1/3) Tr((W_0 ... W_{Nt-1})^{-1}),
+      N_U = (1/4) [3 (Tr Dg Dg^dag - 3) + mean_t (Tr W_t W_t^dag - 3)].
+    Swapping the spatial and temporal sets, or multiplying the temporal links
+    in the reverse time order, changes these values (checked below)."""
+    rng = np.random.default_rng(2024)
+    ns, nt = 4, 4
+    vs = ns ** 3
+    d = np.exp(1j * rng.normal(size=3) * 0.7 + rng.normal(size=3) * 0.3)
+    Dg = np.diag(d / np.prod(d) ** (1.0 / 3.0))
+    W = [_sl3(rng) for _ in range(nt)]
+    U = np.empty((vs * nt, 4, 3, 3), np.complex128)
+    for t in range(nt):
+        U[t * vs:(t + 1) * vs, :3] = Dg
+        U[t * vs:(t + 1) * vs, 3] = W[t]
+    o = L.observables(U, ns, nt)
+    Di = np.linalg.inv(Dg)
+    pt = np.mean([np.trace(Dg @ w @ Di @ np.linalg.inv(w)) for w in W]) / 3
+    line = np.linalg.multi_dot(W)
+    rev = np.linalg.multi_dot(W[::-1])
+    nu = 0.25 * (3 * (np.trace(Dg @ Dg.conj().T).real - 3) +
+                 np.mean([np.trace(w @ w.conj().T).real - 3 for w in W]))
+    assert abs(o["plaq_s"] - 1) < 1e-13
+    assert abs(o["plaq_t"] - pt) < 1e-13
+    assert abs(o["poly"] - np.trace(line) / 3) < 1e-13
+    assert abs(o["poly_inv"] - np.trace(np.linalg.inv(line)) / 3) < 1e-13
+    assert abs(o["unitarity"] - nu) < 1e-12
+    # the pins separate the readings: temporal plaquettes differ from 1, the
+    # reversed product has another trace, and the inverse loop is not conj(P)
+    assert abs(pt - 1) > 1e-2
+    assert abs(np.trace(rev) - np.trace(line)) > 1e-2
+    assert abs(np.trace(np.linalg.inv(line)) - np.conj(np.trace(line))) > 1e-2
