@@ -39,6 +39,13 @@
  *    kernels (default on; read once per process).
  *  - CLSELINV_FOLD_GROUPS=2: two instead of four fold groups in the
  *    persistent digit GEMM (read once per process).
+ *
+ * Environment (precision; changes results within the precision's accuracy)
+ * --------------------------------------------------------------------------
+ *  - CLSELINV_EMU_DIGITS=7: CL_FP64_EMU plans created afterwards split their
+ *    GEMM operands into 7 instead of 8 base-256 digits (an FP64 GEMM's
+ *    accuracy instead of ~2^-58 of the row / column maxima; fewer tensor-core
+ *    products), for accuracy and speed comparisons.
  */
 #ifndef CLSELINV_H
 #define CLSELINV_H
@@ -62,8 +69,18 @@ extern "C" {
 /* arithmetic of the sparse factorisation and selected inversion */
 #define CL_FP64 0       /* all front arithmetic in FP64 (FP64 tensor-core MMA) */
 #define CL_MIXED_FP32 1 /* FP32 fronts, FP64 input/output and drift            */
-#define CL_FP64_EMU 2   /* FP64 fronts; the front GEMMs run as exact 7-digit
-                           BF16 products on the tensor cores (FP64 accuracy)    */
+#define CL_FP64_EMU 2   /* FP64 fronts; the front GEMMs run as 8-digit BF16
+                           products on the tensor cores, accurate to ~2^-58 of
+                           the operands' row / column maxima (below the FP64
+                           rounding of the result)                              */
+#define CL_MIXED_BF16X3 3 /* the mixed form: FP64 fronts, FP64 pivot-block
+                           (panel) inverses with partial pivoting; Schur-
+                           complement updates and off-diagonal selected-inverse
+                           GEMMs as split-BF16x3 products (3 digits, FP32
+                           accumulation, FP32-class accuracy); the panel
+                           products with the pivot-block inverse and the
+                           diagonal blocks G_JJ of the selected-inverse sweep
+                           with 7 digits (FP64 accuracy)                        */
 
 typedef struct cl_plan cl_plan;
 typedef struct cl_group cl_group;
@@ -72,7 +89,7 @@ typedef struct cl_group cl_group;
 typedef struct cl_plan_info {
   int Ns, Nt, V, N;          /* lattice and matrix order N = 3V                */
   int batch;                 /* replicas per call                               */
-  int precision;             /* CL_FP64, CL_MIXED_FP32 or CL_FP64_EMU           */
+  int precision;             /* CL_FP64, CL_MIXED_FP32, CL_FP64_EMU or CL_MIXED_BF16X3 */
   int n_supernodes;          /* separators of the nested dissection            */
   int n_levels;              /* height of the elimination tree + 1              */
   int max_front;             /* largest front order (unknowns)                  */
@@ -83,7 +100,7 @@ typedef struct cl_plan_info {
   double front_bytes;        /* device bytes of the front pool (all replicas)   */
   double device_bytes;       /* all device memory held by the plan              */
   int launches_per_eval;     /* library kernel launches of one cl_drift_eval    */
-  double workspace_bytes;    /* digit workspace of CL_FP64_EMU (all replicas)   */
+  double workspace_bytes;    /* digit workspace of CL_FP64_EMU / CL_MIXED_BF16X3 (all replicas) */
 } cl_plan_info;
 
 /* Per-kernel timing record filled by cl_profile_read. */
@@ -135,7 +152,7 @@ typedef struct cl_langevin_params {
  *   Ns, Nt     even extents >= 4 (even for the staggered phases, >= 4 so that
  *              s+nu and s-nu are distinct sites)
  *   batch      number of independent lattices (replicas) per call, >= 1
- *   precision  CL_FP64, CL_MIXED_FP32 or CL_FP64_EMU
+ *   precision  CL_FP64, CL_MIXED_FP32, CL_FP64_EMU or CL_MIXED_BF16X3
  *   plan       out: library-owned handle, release with cl_destroy_plan
  * Builds the elimination tree, supernodes, front index maps and the launch
  * schedule on the host, then allocates and uploads all device memory the
@@ -147,7 +164,7 @@ int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan);
 /*
  * cl_analyze_ex -- cl_analyze with an explicit pivoting-panel width
  * (unknowns, a multiple of 3 in 3..48; 0 = the precision's default: 48 for
- * CL_FP64, 30 for CL_FP64_EMU / CL_MIXED_FP32).  Narrower panels shorten the
+ * CL_FP64, 30 for the other precisions).  Narrower panels shorten the
  * serial chain of FP64 panel inverses, wider ones make fewer, larger GEMMs;
  * the autotuner in the Python package picks it per shape by timing.
  */
@@ -258,26 +275,32 @@ int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm
                      cudaStream_t stream);
 
 /*
- * cl_drift_eval_noalloc -- the same evaluation as cl_drift_eval (FP64, one
- * lattice) for callers that cannot allocate device memory: code running while
- * a stream is captured into a graph, runtimes whose device memory belongs to
- * another allocator, plugins that must not grow the footprint per call.  The
- * paper has no counterpart; this is a deployment convenience.
+ * cl_drift_eval_noalloc -- the same evaluation as cl_drift_eval (FP64 fronts on
+ * the FP64 tensor pipe, one lattice) for callers that cannot allocate device
+ * memory where they need a drift: host runtimes whose device memory belongs to
+ * another allocator (a framework's caching allocator that has reserved the
+ * GPU), plugins that must not grow the process's footprint per call, loops
+ * that cannot afford the device-wide synchronisation cudaMalloc / cudaFree may
+ * cause.  The paper has no counterpart; this is a deployment convenience.
  *   Ns, Nt         lattice; fronts + workspace + tables must fit the fixed
  *                  20 MiB device scratch array (4^4, V = 256, fits; larger
  *                  shapes return CL_ERR_UNSUPPORTED before any device work)
  *   links, m, mu, nf, Gdiag (may be NULL), Gfwd, Gbwd, Kf: as cl_drift_eval,
  *                  caller-owned device arrays for one lattice (batch 1)
  * Allocates no device memory: the scratch is a file-scope device array that
- * every GPU loading the library holds until the process exits.  The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  Every call
- * re-uploads the index tables from pageable host memory (the copy waits for
- * the stream) and clears what must start at zero.  All calls share the one
- * array, which keeps the last call's contents: calls that overlap on the GPU
- * (different streams, or different host threads) race and corrupt each other.
- * Numerical status (singular pivot, non-finite drift) is not reported; check
- * the outputs.
+ * every GPU loading the library holds until the process exits.  Set-up work
+ * happens on first use: the first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and caches it, and the first call for
+ * a lattice shape on a device analyses the shape on the host and uploads its
+ * index tables into the array (synchronising the stream once); later calls
+ * with the same shape reuse them and issue only a clear of the status word
+ * and the kernels.  Make these first calls before any stream capture.  The
+ * cached address does not survive cudaDeviceReset: do not call the entry
+ * point again in a process after it.  All calls share the one array, which
+ * keeps the last call's contents (the fronts are cleared by the evaluation
+ * itself): calls that overlap on the GPU (different streams, or different
+ * host threads) race and corrupt each other.  Numerical status (singular
+ * pivot, non-finite drift) is not reported; check the outputs.
  */
 int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double m, double mu, double nf,
                           double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
@@ -315,6 +338,19 @@ int cl_zgemm_emu(int M, int N, int K, const double* A, int lda, const double* B,
  * singular pivot, or -1.
  */
 int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail);
+
+/*
+ * cl_plan_set_wait_limit -- limit of the waits of the tensor-core GEMM roles
+ * (producer, MMA issuer, fold warps) for a later launch of this plan's
+ * compute calls: seconds in [0, 0.5]; a negative value restores the default
+ * 0.5 s.  A wait that runs out records CL_ERR_TIMEOUT in the status word;
+ * the kernel then waits (with the full 0.5 s bound) for the copies and MMAs it
+ * has in flight, frees its tensor memory and returns, and the results of
+ * that evaluation are undefined.  Not part of the paper: it lets a test run
+ * the timeout path (a limit of 0 gives up at the first unfinished wait)
+ * without a kernel that never signals.
+ */
+int cl_plan_set_wait_limit(cl_plan* plan, double seconds);
 
 /* cl_plan_get_info -- host summary of a plan. */
 int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info);
@@ -361,7 +397,8 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *   CL_TABLE_FACTOR_OPS, CL_TABLE_SELINV_OPS
  *                        kind (0 zero, 1 assemble, 2 extend-add, 3 panel,
  *                        4 gemm, 5 copy, 6 gather, 7 extract), d0, d1, blocks,
- *                        level, stream, wait, signal
+ *                        level, stream, wait, signal, digits per operand of a
+ *                        digit GEMM (0 otherwise)
  *   CL_TABLE_GEMM        a, b, c, lda, ldb, ldc, M, N, K, neg, beta,
  *                        rmask[4], cmask[4], trans (bit 0 A, 1 B, 2 C stored
  *                        transposed)

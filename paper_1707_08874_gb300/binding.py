@@ -25,6 +25,7 @@ CL_ERR_UNSUPPORTED = 7
 CL_FP64 = 0
 CL_MIXED_FP32 = 1
 CL_FP64_EMU = 2
+CL_MIXED_BF16X3 = 3
 
 _lib = None
 
@@ -79,10 +80,10 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
            "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
-           "cl_analyze_symbolic_ex", "cl_plan_export"]
+           "cl_analyze_symbolic_ex", "cl_plan_export", "cl_plan_set_wait_limit"]
 
 # cl_plan_export tables (include/clselinv.h) and their int64 row widths
-TABLES = {"meta": (0, 10), "factor_ops": (1, 8), "selinv_ops": (2, 8), "gemm": (3, 20), "panel": (4, 5),
+TABLES = {"meta": (0, 10), "factor_ops": (1, 9), "selinv_ops": (2, 9), "gemm": (3, 20), "panel": (4, 5),
           "copy": (5, 14), "extadd": (6, 11), "gather": (7, 7), "maps": (8, 1), "off": (9, 1), "ld": (10, 1)}
 
 
@@ -134,6 +135,7 @@ def load(build_if_missing: bool = True):
     L.cl_plan_check_schedule.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, I]
     L.cl_plan_export.argtypes = [P, I, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
     L.cl_zgemm_emu.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, ctypes.c_size_t, P, P]
+    L.cl_plan_set_wait_limit.argtypes = [P, D]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
@@ -308,6 +310,10 @@ class Plan:
         _check(load().cl_drift_eval(self._h, _dev(links, "links"), float(m), float(mu), float(nf),
                                     _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
                                     _dev(Kf, "Kf"), _stream(stream)), "cl_drift_eval")
+
+    def set_wait_limit(self, seconds: float):
+        """cl_plan_set_wait_limit: limit of the tensor-core GEMM waits (< 0: default 0.5 s)."""
+        _check(load().cl_plan_set_wait_limit(self._h, float(seconds)), "cl_plan_set_wait_limit")
 
     def get_status(self, stream=None):
         info = ctypes.c_int()

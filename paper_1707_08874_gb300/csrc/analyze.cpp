@@ -5,6 +5,7 @@
 // inversion"; the paper's solver does not describe its ordering).
 #include <algorithm>
 #include <array>
+#include <cstdlib>
 #include <functional>
 #include <stdexcept>
 
@@ -135,7 +136,8 @@ int64_t tiles(int M, int N) {
 void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) {
   if (Ns < 4 || Nt < 4 || (Ns & 1) || (Nt & 1)) throw std::invalid_argument("Ns, Nt must be even and >= 4");
   if (Ns > 64 || Nt > 128) throw std::invalid_argument("lattice too large");
-  if (precision != CL_FP64 && precision != CL_MIXED_FP32 && precision != CL_FP64_EMU)
+  if (precision != CL_FP64 && precision != CL_MIXED_FP32 && precision != CL_FP64_EMU &&
+      precision != CL_MIXED_BF16X3)
     throw std::invalid_argument("precision");
   p.Ns = Ns;
   p.Nt = Nt;
@@ -145,7 +147,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   p.precision = precision;
   if (panel != 0 && (panel < 3 || panel > 48 || panel % 3 != 0)) throw std::invalid_argument("panel");
   p.panel = panel ? panel
-                  : (precision == CL_FP64 ? kPanelFP64 : precision == CL_FP64_EMU ? kPanelEmu : kPanelFP32);
+                  : (precision == CL_FP64 ? kPanelFP64 : digit_gemms(precision) ? kPanelEmu : kPanelFP32);
   Geo g{Ns, Nt, {Ns, Ns, Ns, Nt}};
   const int V = p.V;
 
@@ -293,7 +295,22 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   // The digit GEMMs tile C in 128-row blocks: a product with few rows (the
   // TR panel products, b x nf) is issued transposed (nf x b) there, with
   // every operand read and C written through the transposed strides.
-  const bool tr_short = precision == CL_FP64_EMU;
+  const bool tr_short = digit_gemms(precision);
+  // digits per operand of the digit GEMMs: factorisation (panel products and
+  // Schur updates), off-diagonal and diagonal blocks of the selected inversion
+  // (CLSELINV_EMU_DIGITS=7 gives CL_FP64_EMU the accuracy of an FP64 GEMM
+  // instead, for accuracy / speed comparisons)
+  int nd_fp64 = kDigitsFP64;
+  if (const char* v = std::getenv("CLSELINV_EMU_DIGITS")) nd_fp64 = std::atoi(v) == 7 ? 7 : kDigitsFP64;
+  // mixed form: the panel products TR = Y A_p* and TC = -A_*p Y apply the FP64
+  // pivot-block inverse Y and keep its accuracy (7 digits); the Schur updates
+  // (bulk and next-panel strips) and the off-diagonal selected-inverse
+  // products are split-BF16x3 (3 digits)
+  const bool mixed = precision == CL_MIXED_BF16X3;
+  const int nd_panel = mixed ? kDigitsDiag : nd_fp64;
+  const int nd_factor = mixed ? kDigitsMixed : nd_fp64;
+  const int nd_offdiag = nd_factor;
+  const int nd_diag = mixed ? kDigitsDiag : nd_fp64;
   auto add_copy = [&](int blk, int64_t src, int lds, int64_t dst, int ldd, int rows, int cols, Mask2 rm,
                       Mask2 cm) {
     CopyDesc d{src, dst, lds, ldd, rows, cols, rm, cm, blk};
@@ -352,6 +369,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       auto tC_of = [&](const SNode& n) { return tR_of(n) + (int64_t)b * n.nf; };
       Op pinv{OP_PANEL, (int)p.panels.size(), 0, 0, h};
       Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+      g1.ndig = nd_panel;
       int blk1 = 0;
       for (int i : lv) {
         const SNode& n = nodes[i];
@@ -380,6 +398,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       p.factor_ops.push_back(g1);
       // next-panel strips and the entries the next panel reads (stream 0)
       Op st{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+      st.ndig = nd_factor;
       Op ec{OP_COPY, (int)p.copies.size(), 0, 0, h};
       int blks = 0, blke = 0;
       for (int i : lv) {
@@ -417,6 +436,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       }
       // bulk update and write-back of panel p (stream 1)
       Op g2{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+      g2.ndig = nd_factor;
       Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
       int blk2 = 0, blk3 = 0;
       for (int i : lv) {
@@ -467,6 +487,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     if (ga.d1 == ga.d0) continue;
     p.selinv_ops.push_back(ga);
     Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+    g1.ndig = nd_offdiag;
     int blk1 = 0;
     for (int i : lv) {
       const SNode& n = nodes[i];
@@ -480,6 +501,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     g1.blocks = blk1;
     p.selinv_ops.push_back(g1);
     Op g2{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
+    g2.ndig = nd_diag;
     Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
     int blk2 = 0, blk3 = 0;
     for (int i : lv) {
@@ -507,7 +529,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   // stream gets a region of its own after the first one's)
   p.emu.clear();
   p.emu_words = p.emu_ints = 0;
-  if (precision == CL_FP64_EMU) {
+  if (digit_gemms(precision)) {
     p.emu.resize(p.gemm.size());
     int64_t max_w[2] = {0, 0}, max_in[2] = {0, 0};
     for (auto* ops : {&p.factor_ops, &p.selinv_ops})
@@ -523,9 +545,9 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
           e.Kp = (g.K + 31) / 32 * 32;
           const int64_t nch = e.Kp / 32;
           e.adig = w;
-          w += (7LL * e.Mp * e.Kp + 63) / 64 * 64;
+          w += ((int64_t)op.ndig * e.Mp * e.Kp + 63) / 64 * 64;
           e.bdig = w;
-          w += (7LL * 2 * e.Np * e.Kp + 63) / 64 * 64;
+          w += ((int64_t)op.ndig * 2 * e.Np * e.Kp + 63) / 64 * 64;
           e.aexp = in;
           in += nch * e.Mp;
           e.bexp = in;

@@ -133,7 +133,7 @@ int setup_device(Plan& p) {
       p.op_events[i] = ev;
     }
   }
-  if (p.precision == CL_FP64_EMU) {
+  if (cl::digit_gemms(p.precision)) {
     if ((e = cl::emu_prepare()) != cudaSuccess) return cuda_status(e);
     if ((e = upload(p.d_emu, p.emu.data(), p.emu.size() * sizeof(cl::EmuDesc), total)) != cudaSuccess ||
         (e = upload(p.d_emu_words, nullptr, B * p.emu_words * sizeof(unsigned), total)) != cudaSuccess ||
@@ -412,6 +412,17 @@ int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm
   return cuda_status(e);
 }
 
+int cl_plan_set_wait_limit(cl_plan* plan, double seconds) {
+  if (!plan) return CL_ERR_INVALID_ARG;
+  if (seconds < 0) {
+    plan->p.wait_ns = cl::kDefaultWaitNs;
+  } else {
+    const double ns = seconds * 1e9;
+    plan->p.wait_ns = ns >= (double)cl::kDefaultWaitNs ? cl::kDefaultWaitNs : (unsigned long long)ns;
+  }
+  return CL_OK;
+}
+
 int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail) {
   if (!compute_ready(plan) || !info) return CL_ERR_INVALID_ARG;
   int h[4] = {0, 0, 0, 0};
@@ -453,7 +464,7 @@ int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info) {
   for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
     for (const auto& op : *ops)
       if (op.kind != cl::OP_ZERO && op.blocks > 0)
-        launches += (op.kind == cl::OP_GEMM && p.precision == CL_FP64_EMU) ? 2 : 1;  // split + GEMM
+        launches += (op.kind == cl::OP_GEMM && cl::digit_gemms(p.precision)) ? 2 : 1;  // split + GEMM
   info->launches_per_eval = launches;
   info->workspace_bytes = (double)p.batch * (4.0 * p.emu_words + 4.0 * p.emu_ints);
   return CL_OK;
@@ -486,7 +497,8 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
     case CL_TABLE_FACTOR_OPS:
     case CL_TABLE_SELINV_OPS:
       for (const auto& op : table == CL_TABLE_FACTOR_OPS ? p.factor_ops : p.selinv_ops)
-        v.insert(v.end(), {(long long)op.kind, op.d0, op.d1, op.blocks, op.level, op.stream, op.wait, op.signal});
+        v.insert(v.end(),
+                 {(long long)op.kind, op.d0, op.d1, op.blocks, op.level, op.stream, op.wait, op.signal, op.ndig});
       break;
     case CL_TABLE_GEMM:
       for (const auto& g : p.gemm) {

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const GemmDesc* __restrict__ d
 }  // namespace
 
 cudaError_t launch_gemm(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
-  if (p.precision == CL_FP64_EMU) return launch_gemm_emu(p, op, arena, st);
+  if (digit_gemms(p.precision)) return launch_gemm_emu(p, op, arena, st);
   const dim3 grid((unsigned)op.blocks, (unsigned)p.batch);
   return launch_k(k_gemm_f64, grid, dim3(128), 0, st, op_launch(p, op), p.d_gemm, op.d0, op.d1, arena,
                   p.arena_elems);

@@ -34,7 +34,11 @@
 namespace cl {
 namespace {
 
-constexpr int kDig = 7;      // base-256 digits per operand
+// base-256 digits per operand (ND, a template parameter of the kernels):
+// 8 for the FP64 fronts (products accurate to ~2^-58 of the row / column
+// maxima, well below FP64 rounding of the result), 7 for the stand-alone
+// GEMM (an FP64 GEMM's accuracy), 3 for the split-BF16x3 Schur products
+// (FP32-class accuracy)
 constexpr int kChunk = 32;   // complex k per exponent chunk (64 real k)
 constexpr int kTileCx = 16;  // complex columns of C per CTA (32 real columns of B')
 
@@ -44,21 +48,24 @@ __device__ __forceinline__ int exp_of(double v) {
   return E == 0 ? -2000 : E - 1023;  // zero / subnormal count as absent
 }
 
-// BF16 bit patterns of the 7 digits of |v| 2^{-e} (< 1), truncated, with v's sign
-__device__ __forceinline__ void digits(double v, int e, unsigned short (&d)[kDig]) {
+// BF16 bit patterns of the ND digits of |v| 2^{-e} (< 1), truncated to a
+// window of 8 ND bits, with v's sign
+template <int ND>
+__device__ __forceinline__ void digits(double v, int e, unsigned short (&d)[ND]) {
+  static_assert(ND >= 2 && ND <= 8, "8 ND bits must fit the 64-bit window");
   const long long b = __double_as_longlong(v);
   const int E = (int)((b >> 52) & 0x7FF);
   const unsigned short sgn = b < 0 ? 0x8000u : 0u;
   unsigned long long X = 0;
   if (E != 0 && E != 0x7FF) {
     const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = (E - 1023) + 4 - e;  // X = m 2^sh = |v| 2^{56-e}; sh <= 3
+    const int sh = (E - 1023) + (8 * ND - 52) - e;  // X = m 2^sh = |v| 2^{8 ND - e} < 2^{8 ND}
     if (sh >= 0) X = m << sh;
     else if (sh > -64) X = m >> (-sh);
   }
 #pragma unroll
-  for (int p = 0; p < kDig; ++p) {
-    const unsigned dg = (unsigned)(X >> (48 - 8 * p)) & 0xFFu;
+  for (int p = 0; p < ND; ++p) {
+    const unsigned dg = (unsigned)(X >> (8 * (ND - 1 - p))) & 0xFFu;
     d[p] = dg ? (unsigned short)((__float_as_uint((float)dg) >> 16) | sgn) : (unsigned short)0;
   }
 }
@@ -66,26 +73,29 @@ __device__ __forceinline__ void digits(double v, int e, unsigned short (&d)[kDig
 // Digit tiles, laid out for the tensor core's no-swizzle K-major operand
 // format: 16-k slabs; inside a slab, 8-row groups of two 8 x 8 core matrices
 // (k 0-7, 8-15), each core matrix 8 rows of 16 bytes (256 bytes per group).
-//   A: per (128-row block, chunk) one 112 KB block [digit p][slab][16 groups]
+// With ND digits per operand:
+//   A: per (128-row block, chunk) one 16 ND KB block [digit p][slab][16 groups]
 //      (4096 words per digit).
-//   B': per (32-real-column block, chunk) one 28 KB block [slab][digit q][4
-//      groups] (1792 words per slab): in a slab the seven digits' rows follow
-//      one another at the uniform 256-byte group stride, so one MMA of width
-//      N = 32 (7 - p) multiplies A digit p by B' digits q = 0 .. 6 - p at once.
+//   B': per (32-real-column block, chunk) one 4 ND KB block [slab][digit q][4
+//      groups] (256 ND words per slab): in a slab the digits' rows follow one
+//      another at the uniform 256-byte group stride, so one MMA of width
+//      N = 32 (ND - p) multiplies A digit p by B' digits q = 0 .. ND-1-p at once.
 // Word (two BF16: re / im of one complex k) of A row `row`, lane = complex k
 // in the chunk:
+template <int ND>
 __device__ __forceinline__ int64_t a_tile_word(const EmuDesc& e, int nch, int p, int row, int c, int lane) {
   const int64_t blk = (int64_t)(row / 128) * nch + c;
   const int r = row & 127;
-  return e.adig + (blk * kDig + p) * 4096 + (lane >> 3) * 1024 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 +
+  return e.adig + (blk * ND + p) * 4096 + (lane >> 3) * 1024 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 +
          (lane & 3);
 }
 // ... and of B' row (real column of the embedding) `nreal`:
+template <int ND>
 __device__ __forceinline__ int64_t b_tile_word(const EmuDesc& e, int nch, int q, int nreal, int c, int lane) {
   const int64_t blk = (int64_t)(nreal / 32) * nch + c;
   const int r = nreal & 31;
-  return e.bdig + blk * 7168 + (lane >> 3) * 1792 + q * 256 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 + (r & 7) * 4 +
-         (lane & 3);
+  return e.bdig + blk * (1024 * ND) + (lane >> 3) * (256 * ND) + q * 256 + (r >> 3) * 64 + ((lane >> 2) & 1) * 32 +
+         (r & 7) * 4 + (lane & 3);
 }
 
 // Split pass: one warp per item.  A items (row, chunk): lanes take the 32
@@ -95,11 +105,12 @@ __device__ __forceinline__ int64_t b_tile_word(const EmuDesc& e, int nch, int q,
 //   row 2n   : (br, -bi)   (real column 2n of [[br, bi], [-bi, br]] per k)
 //   row 2n+1 : (bi,  br)
 // Padding (rows >= M, columns >= N, k >= K) gets zero digits.
+template <int ND>
 __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed,
                                                    int d0, int d1, const double2* __restrict__ arena,
                                                    int64_t stride, unsigned* __restrict__ words,
                                                    int* __restrict__ ints, int64_t wstride, int64_t istride,
-                                                   int total) {
+                                                   int total, int* __restrict__ status) {
   pdl_enter();
   const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -130,23 +141,27 @@ __global__ void __launch_bounds__(256) k_emu_split(const GemmDesc* __restrict__ 
     if (line < g.N && k < g.K)
       v = base[g.b + ((g.trans & 2) ? (int64_t)line * g.ldb + k : (int64_t)k * g.ldb + line)];
   }
+  // an infinite or NaN operand has no digits: report it instead of dropping it
+  if (!isfinite(v.x) || !isfinite(v.y)) set_status(status, CL_ERR_NONFINITE, -1, -1);
   int ex = max(exp_of(v.x), exp_of(v.y));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
   const int ee = ex + 1;
-  unsigned short dr[kDig], di[kDig];
-  digits(v.x, ee, dr);
-  digits(v.y, ee, di);
+  unsigned short dr[ND], di[ND];
+  digits<ND>(v.x, ee, dr);
+  digits<ND>(v.y, ee, di);
   if (isA) {
     if (lane == 0) I[e.aexp + (int64_t)c * e.Mp + line] = ee;
 #pragma unroll
-    for (int p = 0; p < kDig; ++p) W[a_tile_word(e, nch, p, line, c, lane)] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
+    for (int p = 0; p < ND; ++p)
+      W[a_tile_word<ND>(e, nch, p, line, c, lane)] = (unsigned)dr[p] | ((unsigned)di[p] << 16);
   } else {
     if (lane == 0) I[e.bexp + (int64_t)c * e.Np + line] = ee;
 #pragma unroll
-    for (int p = 0; p < kDig; ++p) {
-      W[b_tile_word(e, nch, p, 2 * line, c, lane)] = (unsigned)dr[p] | ((unsigned)(di[p] ^ (di[p] ? 0x8000u : 0u)) << 16);
-      W[b_tile_word(e, nch, p, 2 * line + 1, c, lane)] = (unsigned)di[p] | ((unsigned)dr[p] << 16);
+    for (int p = 0; p < ND; ++p) {
+      W[b_tile_word<ND>(e, nch, p, 2 * line, c, lane)] =
+          (unsigned)dr[p] | ((unsigned)(di[p] ^ (di[p] ? 0x8000u : 0u)) << 16);
+      W[b_tile_word<ND>(e, nch, p, 2 * line + 1, c, lane)] = (unsigned)di[p] | ((unsigned)dr[p] << 16);
     }
   }
 }
@@ -185,10 +200,15 @@ constexpr int kAHalf = 8192;     // bytes: 128 rows x 32 real k, BF16 (two 16-k 
 constexpr int kBHalf = 2048;     // bytes per digit: 32 real columns x 32 real k
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28;
-// M = 128, N = 32 (7 - p) for A digit p (a multiple of 16, <= 224)
+// M = 128, N = 32 (ND - p) for A digit p (a multiple of 16, <= 256)
 constexpr uint32_t kTcIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
-__host__ __device__ constexpr uint32_t tc_idesc(int p) { return kTcIdescBase | ((uint32_t)(4 * (kDig - p)) << 17); }
-constexpr unsigned long long kWaitNs = 500000000ull;  // 0.5 s
+__host__ __device__ constexpr uint32_t tc_idesc(int nd, int p) {
+  return kTcIdescBase | ((uint32_t)(4 * (nd - p)) << 17);
+}
+// bound of the waits that drain copies and MMAs in flight before a CTA
+// leaves (always the full bound; the role waits take the launch's limit,
+// kDefaultWaitNs unless a test shortens it)
+constexpr unsigned long long kWaitNs = kDefaultWaitNs;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -285,7 +305,7 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 constexpr int kPA = 16384;  // bytes: one A digit tile, 128 rows x 64 real k
 constexpr int kPB = 4096;   // bytes: one B' digit tile, 32 real columns x 64 real k
 constexpr int kPCtl = 1024;
-constexpr size_t kPSmemBytes = (size_t)kDig * kPA + 2 * (size_t)kDig * kPB + kPCtl;
+__host__ __device__ constexpr size_t p_smem_bytes(int nd) { return (size_t)nd * kPA + 2 * (size_t)nd * kPB + kPCtl; }
 constexpr uint32_t kPCols = 512;
 
 // tile t of the launch -> problem, row block and 16-column tile
@@ -302,7 +322,8 @@ __device__ __forceinline__ TileRef tile_ref(const GemmDesc* __restrict__ gd, int
 }
 
 // bounded wait that also gives up when another role has aborted
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, unsigned parity, const volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, unsigned parity, const volatile int* abort_flag,
+                                             unsigned long long limit_ns) {
   const unsigned long long t0 = gtimer();
   while (true) {
     unsigned ok;
@@ -312,20 +333,21 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, unsigned parity, cons
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (*abort_flag || gtimer() - t0 > kWaitNs) return false;
+    if (*abort_flag || gtimer() - t0 > limit_ns) return false;
   }
 }
 
-template <int NG>  // fold groups of four warps
+template <int NG, int ND>  // fold groups of four warps, digits per operand
 __global__ void __launch_bounds__(64 + 128 * NG, 1)
     k_gemm_emu_persist(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
                        double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
-                       const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
+                       const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status,
+                       unsigned long long wait_ns) {
   pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem_p[];
   unsigned char* sA = smem_p;                   // [7][kPA]
-  unsigned char* sB = smem_p + kDig * kPA;      // [2 stages][7][kPB]
-  unsigned char* ctl = sB + 2 * kDig * kPB;
+  unsigned char* sB = smem_p + ND * kPA;        // [2 stages][ND][kPB]
+  unsigned char* ctl = sB + 2 * ND * kPB;
   // mbarriers: [0] A landed, [1,2] B stage landed, [3,4] B stage consumed,
   //            [5,6] accumulator set full, [7,8] accumulator set drained
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);
@@ -370,23 +392,23 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         const int key = tr.di * 65536 + tr.rb;
         if (key != prev) {
           // the MMAs of the previous tile read the old A block: wait for them
-          if (i > 0 && !mbar_wait_ab(bar(3 + ((i - 1) & 1)), ((i - 1) >> 1) & 1, abort_flag)) {
+          if (i > 0 && !mbar_wait_ab(bar(3 + ((i - 1) & 1)), ((i - 1) >> 1) & 1, abort_flag, wait_ns)) {
             good = false;
             break;
           }
-          mbar_expect_tx(b_afull, (unsigned)(kDig * kPA));
-          for (int p = 0; p < kDig; ++p)
-            bulk_g2s(smem_u32(sA + p * kPA), Wd + e.adig + ((int64_t)tr.rb * kDig + p) * 4096, kPA, b_afull);
+          mbar_expect_tx(b_afull, (unsigned)(ND * kPA));
+          for (int p = 0; p < ND; ++p)
+            bulk_g2s(smem_u32(sA + p * kPA), Wd + e.adig + ((int64_t)tr.rb * ND + p) * 4096, kPA, b_afull);
           ++a_loads;
           prev = key;
         }
         const int s = i & 1, u = i >> 1;
-        if (i >= 2 && !mbar_wait_ab(bar(3 + s), (u - 1) & 1, abort_flag)) {
+        if (i >= 2 && !mbar_wait_ab(bar(3 + s), (u - 1) & 1, abort_flag, wait_ns)) {
           good = false;
           break;
         }
-        mbar_expect_tx(bar(1 + s), (unsigned)(kDig * kPB));
-        bulk_g2s(smem_u32(sB + s * kDig * kPB), Wd + e.bdig + (int64_t)tr.j * 7168, kDig * kPB, bar(1 + s));
+        mbar_expect_tx(bar(1 + s), (unsigned)(ND * kPB));
+        bulk_g2s(smem_u32(sB + s * ND * kPB), Wd + e.bdig + (int64_t)tr.j * (1024 * ND), ND * kPB, bar(1 + s));
         issued = i + 1;
       }
       if (!good) {
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         const TileRef tr = tile_ref(gd, d0, d1, t0 + i);
         const int key = tr.di * 65536 + tr.rb;
         if (key != prev) {
-          if (!mbar_wait_ab(b_afull, a_use & 1, abort_flag)) {
+          if (!mbar_wait_ab(b_afull, a_use & 1, abort_flag, wait_ns)) {
             good = false;
             break;
           }
@@ -416,19 +438,19 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
           prev = key;
         }
         const int s = i & 1, u = i >> 1;
-        if (!mbar_wait_ab(bar(1 + s), u & 1, abort_flag) ||
-            (i >= 2 && !mbar_wait_ab(bar(7 + s), (u - 1) & 1, abort_flag))) {
+        if (!mbar_wait_ab(bar(1 + s), u & 1, abort_flag, wait_ns) ||
+            (i >= 2 && !mbar_wait_ab(bar(7 + s), (u - 1) & 1, abort_flag, wait_ns))) {
           good = false;
           break;
         }
         tc_fence_after();
-        const uint32_t b0 = smem_u32(sB + s * kDig * kPB), d = tmem + 256u * s;
+        const uint32_t b0 = smem_u32(sB + s * ND * kPB), d = tmem + 256u * s;
 #pragma unroll 1
-        for (int p = 0; p < kDig; ++p)
+        for (int p = 0; p < ND; ++p)
 #pragma unroll
           for (int kb = 0; kb < 4; ++kb)
-            umma_bf16(d + 32 * p, umma_desc(a0 + p * kPA + kb * 4096), umma_desc(b0 + kb * (kDig * 1024)), tc_idesc(p),
-                      (p | kb) != 0 ? 1u : 0u);
+            umma_bf16(d + 32 * p, umma_desc(a0 + p * kPA + kb * 4096), umma_desc(b0 + kb * (ND * 1024)),
+                      tc_idesc(ND, p), (p | kb) != 0 ? 1u : 0u);
         umma_commit(bar(3 + s));
         umma_commit(bar(5 + s));
         last = i;
@@ -478,7 +500,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         for (int jj = 0; jj < CC; ++jj) cv[jj] = c8 + jj < g.N ? crow[(CC * grp + jj) * cs] : make_double2(0, 0);
       }
       const int s = i & 1, u = i >> 1;
-      const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag);
+      const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag, wait_ns);
       if (!__all_sync(0xffffffffu, got)) {
         if (!*abort_flag) set_status(status, CL_ERR_TIMEOUT, -7, t0);
         *abort_flag = 1;
@@ -490,9 +512,10 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         float h[CR], mi[CR], lo[CR];
         const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * s + CR * hh;
         {  // levels 0-3: four loads, one wait
-          uint32_t v[4][CR];
+          constexpr int N1 = ND < 4 ? ND : 4;
+          uint32_t v[N1][CR];
 #pragma unroll
-          for (int L = 0; L < 4; ++L) tmem_ld_issue(ta + 32 * L, v[L]);
+          for (int L = 0; L < N1; ++L) tmem_ld_issue(ta + 32 * L, v[L]);
           tmem_ld_wait();
 #pragma unroll
           for (int k = 0; k < CR; ++k) {
@@ -500,7 +523,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
             two_sum(h[k], __uint_as_float(v[1][k]) * 0x1p-24f, h[k], mi[k]);
             lo[k] = 0.f;
 #pragma unroll
-            for (int L = 2; L < 4; ++L) {
+            for (int L = 2; L < N1; ++L) {
               float s2, e2;
               two_sum(mi[k], __uint_as_float(v[L][k]) * __int_as_float((127 - 16 - 8 * L) << 23), s2, e2);
               mi[k] = s2;
@@ -508,17 +531,27 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
             }
           }
         }
-        {  // levels 4-6, at most 2^-32 of the leading level: summed in FP32
-           // (rounding below 2^-53 of it), then one error-free addition
-          uint32_t v[3][CR];
+        if constexpr (ND > 4) {  // levels 4 .. ND-1, at most 2^-32 of the leading level
+          // with 8 digits level 4 enters by one error-free addition of its own;
+          // the remaining levels (>= 2^-40 below the leading level with 8
+          // digits, >= 2^-32 with 7) are summed in FP32 and enter by one more
+          constexpr int N2 = ND - 4, E2 = ND >= 8 ? 1 : 0;
+          uint32_t v[N2][CR];
 #pragma unroll
-          for (int L = 0; L < 3; ++L) tmem_ld_issue(ta + 32 * (L + 4), v[L]);
+          for (int L = 0; L < N2; ++L) tmem_ld_issue(ta + 32 * (L + 4), v[L]);
           tmem_ld_wait();
 #pragma unroll
           for (int k = 0; k < CR; ++k) {
-            const float x = fmaf(__uint_as_float(v[2][k]), 0x1p-64f,
-                                 fmaf(__uint_as_float(v[1][k]), 0x1p-56f, __uint_as_float(v[0][k]) * 0x1p-48f));
             float s2, e2;
+            if (E2) {
+              two_sum(mi[k], __uint_as_float(v[0][k]) * 0x1p-48f, s2, e2);
+              mi[k] = s2;
+              lo[k] += e2;
+            }
+            float x = __uint_as_float(v[E2][k]) * __int_as_float((127 - 48 - 8 * E2) << 23);
+#pragma unroll
+            for (int L = E2 + 1; L < N2; ++L)
+              x = fmaf(__uint_as_float(v[L][k]), __int_as_float((127 - 48 - 8 * L) << 23), x);
             two_sum(mi[k], x, s2, e2);
             mi[k] = s2;
             lo[k] += e2;
@@ -573,28 +606,33 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
 //                  column exponents and write the tile after its last chunk
 //                  (four groups, 96 registers with spills, measured ~1%
 //                  slower on the selected inversion).
-constexpr int kCStage = kDig * (kAHalf + kBHalf);  // bytes per ring stage
+// ring stage of ND digits (bytes) and stages (8 digits: two, to stay within
+// the 227 KB of shared memory of a CTA)
+__host__ __device__ constexpr int c_stage_bytes(int nd) { return nd * (kAHalf + kBHalf); }
+__host__ __device__ constexpr int c_stages(int nd) { return nd >= 8 ? 2 : 3; }
+__host__ __device__ constexpr size_t c_smem_bytes(int nd) { return (size_t)c_stages(nd) * c_stage_bytes(nd) + 1024; }
 constexpr int kChunkedGroups = 2;  // fold groups of the chunked kernel
-constexpr int kCStages = 3;
-constexpr size_t kCSmemBytes = (size_t)kCStages * kCStage + 1024;
 
-template <int NG>  // fold groups of four warps
+template <int NG, int ND>  // fold groups of four warps, digits per operand
 __global__ void __launch_bounds__(64 + 128 * NG, 1)
     k_gemm_emu_chunked(const GemmDesc* __restrict__ gd, const EmuDesc* __restrict__ ed, int d0, int d1, int total,
                        double2* __restrict__ arena, int64_t stride, const unsigned* __restrict__ words,
-                       const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status) {
+                       const int* __restrict__ ints, int64_t wstride, int64_t istride, int* __restrict__ status,
+                       unsigned long long wait_ns) {
   pdl_enter();
+  constexpr int kCStage = c_stage_bytes(ND), kCStages = c_stages(ND);
   extern __shared__ __align__(1024) unsigned char smem_c[];
   unsigned char* ctl = smem_c + kCStages * kCStage;
-  // mbarriers: [0..2] stage landed, [3..5] stage consumed, [6,7] accumulator
-  //            set full, [8,9] accumulator set drained
+  // mbarriers: [0..2] stage landed, [3..5] stage consumed (the first
+  //            kCStages of each), [6,7] accumulator set full, [8,9]
+  //            accumulator set drained
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(ctl);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 96);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 100);
   const uint32_t bar0 = smem_u32(bars);
   auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
   auto stageA = [&](int s) { return smem_c + s * kCStage; };
-  auto stageB = [&](int s) { return smem_c + s * kCStage + kDig * kAHalf; };
+  auto stageB = [&](int s) { return smem_c + s * kCStage + ND * kAHalf; };
 
   const int G = gridDim.x;
   const int t0 = (int)((int64_t)total * blockIdx.x / G), t1 = (int)((int64_t)total * (blockIdx.x + 1) / G);
@@ -631,16 +669,16 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         for (int c = 0; c < nch && good; ++c)
           for (int hf = 0; hf < 2; ++hf, ++q) {
             const int s = q % kCStages, u = q / kCStages;
-            if (q >= kCStages && !mbar_wait_ab(bar(3 + s), (u - 1) & 1, abort_flag)) {
+            if (q >= kCStages && !mbar_wait_ab(bar(3 + s), (u - 1) & 1, abort_flag, wait_ns)) {
               good = false;
               break;
             }
             mbar_expect_tx(bar(s), (unsigned)kCStage);
             const int64_t ablk = (int64_t)tr.rb * nch + c, bblk = (int64_t)tr.j * nch + c;
-            for (int p = 0; p < kDig; ++p)
-              bulk_g2s(smem_u32(stageA(s) + p * kAHalf), Wd + e.adig + (ablk * kDig + p) * 4096 + hf * 2048, kAHalf,
+            for (int p = 0; p < ND; ++p)
+              bulk_g2s(smem_u32(stageA(s) + p * kAHalf), Wd + e.adig + (ablk * ND + p) * 4096 + hf * 2048, kAHalf,
                        bar(s));
-            bulk_g2s(smem_u32(stageB(s)), Wd + e.bdig + bblk * 7168 + hf * 3584, kDig * kBHalf, bar(s));
+            bulk_g2s(smem_u32(stageB(s)), Wd + e.bdig + bblk * (1024 * ND) + hf * (512 * ND), ND * kBHalf, bar(s));
           }
       }
       if (!good) {
@@ -655,30 +693,38 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
     if (lane == 0) {  // ---- MMA issuer
       int q = 0, k = 0;
       bool good = true;
+      // the last commit issued (it arrives once every earlier MMA of this
+      // thread has completed): what a teardown after a timeout waits for
+      uint32_t lc_bar = 0;
+      unsigned lc_par = 0;
+      bool has_lc = false;
       for (int t = t0; t < t1 && good && !*abort_flag; ++t) {
         const TileRef tr = tile_ref(gd, d0, d1, t);
         const int nch = ed[tr.di].Kp / kChunk;
         for (int c = 0; c < nch && good; ++c, ++k) {
           const int set = k & 1, uk = k >> 1;
-          if (k >= 2 && !mbar_wait_ab(bar(8 + set), (uk - 1) & 1, abort_flag)) {
+          if (k >= 2 && !mbar_wait_ab(bar(8 + set), (uk - 1) & 1, abort_flag, wait_ns)) {
             good = false;
             break;
           }
           for (int hf = 0; hf < 2; ++hf, ++q) {
             const int s = q % kCStages, u = q / kCStages;
-            if (!mbar_wait_ab(bar(s), u & 1, abort_flag)) {
+            if (!mbar_wait_ab(bar(s), u & 1, abort_flag, wait_ns)) {
               good = false;
               break;
             }
             tc_fence_after();
             const uint32_t a0 = smem_u32(stageA(s)), b0 = smem_u32(stageB(s)), d = tmem + 256u * set;
 #pragma unroll 1
-            for (int p = 0; p < kDig; ++p)
+            for (int p = 0; p < ND; ++p)
 #pragma unroll
               for (int kb = 0; kb < 2; ++kb)
-                umma_bf16(d + 32 * p, umma_desc(a0 + p * kAHalf + kb * 4096), umma_desc(b0 + kb * (kDig * 1024)),
-                          tc_idesc(p), (hf | p | kb) != 0 ? 1u : 0u);
+                umma_bf16(d + 32 * p, umma_desc(a0 + p * kAHalf + kb * 4096), umma_desc(b0 + kb * (ND * 1024)),
+                          tc_idesc(ND, p), (hf | p | kb) != 0 ? 1u : 0u);
             umma_commit(bar(3 + s));
+            lc_bar = bar(3 + s);
+            lc_par = (unsigned)(u & 1);
+            has_lc = true;
           }
           if (!good) break;
           umma_commit(bar(6 + set));
@@ -688,7 +734,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         *abort_flag = 1;
         set_status(status, CL_ERR_TIMEOUT, -9, t0);
       }
-      if (*abort_flag && k > 0) mbar_wait(bar(6 + ((k - 1) & 1)), ((k - 1) >> 1) & 1);  // MMAs in flight
+      if (*abort_flag && has_lc) mbar_wait(lc_bar, lc_par);  // MMAs in flight, a half chunk included
     }
     __syncwarp();
   } else {  // ---- fold and epilogue: group g owns complex columns CC g .. CC g + CC-1 of the tile
@@ -724,7 +770,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
 #pragma unroll
         for (int jj = 0; jj < CC; ++jj) sc[jj] = pow2f(rsc + __shfl_sync(0xffffffffu, csc, jj));
         const int set = k & 1, uk = k >> 1;
-        const bool got = mbar_wait_ab(bar(6 + set), uk & 1, abort_flag);
+        const bool got = mbar_wait_ab(bar(6 + set), uk & 1, abort_flag, wait_ns);
         if (!__all_sync(0xffffffffu, got)) {
           if (!*abort_flag) set_status(status, CL_ERR_TIMEOUT, -10, t0);
           *abort_flag = 1;
@@ -734,23 +780,35 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         tc_fence_after();
         const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + 256u * set + CR * grp;
 #pragma unroll
-        for (int b4 = 0; b4 < 2; ++b4) {  // levels 0-3, then 4-6
-          const int L0 = 4 * b4, nl = b4 ? 3 : 4;
+        for (int b4 = 0; b4 < 2; ++b4) {  // levels 0-3, then 4 .. ND-1
+          constexpr int N1 = ND < 4 ? ND : 4, N2 = ND - N1, E2 = ND >= 8 ? 1 : 0;
+          const int L0 = 4 * b4, nl = b4 ? N2 : N1;
+          if (nl == 0) continue;
           uint32_t v[4][CR];
 #pragma unroll
-          for (int l = 0; l < nl; ++l) tmem_ld_issue(ta + 32 * (L0 + l), v[l]);
+          for (int l = 0; l < 4; ++l)
+            if (l < nl) tmem_ld_issue(ta + 32 * (L0 + l), v[l]);
           tmem_ld_wait();
-          if (b4) {
+          if (b4 || N2 == 0) {
             tc_fence_before();
             mbar_arrive(bar(8 + set));  // accumulator set drained
           }
-          if (b4) {  // levels 4-6 (<= 2^-32 of the leading level): FP32 sum, one error-free addition
+          if (b4) {  // levels 4 .. ND-1 (<= 2^-32 of the leading level): with 8 digits
+                     // level 4 by an error-free addition of its own, the rest summed in
+                     // FP32 and added by one more
 #pragma unroll
             for (int i = 0; i < CR; ++i) {
               const float c = sc[i >> 1];
-              const float x = fmaf(__uint_as_float(v[2][i]), c * 0x1p-48f,
-                                   fmaf(__uint_as_float(v[1][i]), c * 0x1p-40f, __uint_as_float(v[0][i]) * (c * 0x1p-32f)));
               float s2, e2;
+              if (E2) {
+                two_sum(mi[i], __uint_as_float(v[0][i]) * (c * 0x1p-32f), s2, e2);
+                mi[i] = s2;
+                lo[i] += e2;
+              }
+              float x = __uint_as_float(v[E2][i]) * (c * __int_as_float((127 - 32 - 8 * E2) << 23));
+#pragma unroll
+              for (int l = E2 + 1; l < 4; ++l)
+                if (l < nl) x = fmaf(__uint_as_float(v[l][i]), c * __int_as_float((127 - 32 - 8 * l) << 23), x);
               two_sum(mi[i], x, s2, e2);
               mi[i] = s2;
               lo[i] += e2;
@@ -758,6 +816,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
           } else {
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
+              if (l >= nl) continue;
               const float cL = __int_as_float((127 - 8 * l) << 23);  // 2^{-8L}
 #pragma unroll
               for (int i = 0; i < CR; ++i) {
@@ -832,15 +891,24 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
 
 }  // namespace
 
-// opt the GEMM kernel in to > 48 KB of dynamic shared memory on the current
+// opt the GEMM kernels in to > 48 KB of dynamic shared memory on the current
 // device (done when a plan is set up, outside any stream capture)
+template <int ND>
+cudaError_t emu_prepare_nd() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_chunked<kChunkedGroups, ND>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c_smem_bytes(ND));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gemm_emu_persist<2, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p_smem_bytes(ND));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_emu_persist<4, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)p_smem_bytes(ND));
+}
 cudaError_t emu_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_emu_chunked<kChunkedGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kCSmemBytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gemm_emu_persist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm_emu_persist<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
+  cudaError_t e = emu_prepare_nd<3>();
+  if (e == cudaSuccess) e = emu_prepare_nd<7>();
+  if (e == cudaSuccess) e = emu_prepare_nd<8>();
+  return e;
 }
 
 // fold groups of the persistent digit GEMM: four (576 threads, 96 registers)
@@ -854,23 +922,47 @@ int fold_groups() {
   return ng;
 }
 
-cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
-                       double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, LaunchOpt lo) {
+template <int ND>
+cudaError_t launch_emu_nd(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
+                          double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride,
+                          int64_t istride, int* status, bool single_chunk, int max_ctas, cudaStream_t st,
+                          LaunchOpt lo, unsigned long long wait_ns) {
   const dim3 gs((unsigned)((items + 7) / 8), (unsigned)batch);
-  cudaError_t e = launch_k(k_emu_split, gs, dim3(256), 0, st, lo, gd, ed, d0, d1, (const double2*)arena, stride,
-                           words, ints, wstride, istride, items);
+  cudaError_t e = launch_k(k_emu_split<ND>, gs, dim3(256), 0, st, lo, gd, ed, d0, d1, (const double2*)arena, stride,
+                           words, ints, wstride, istride, items, status);
   if (e != cudaSuccess) return e;
   const LaunchOpt lg{lo.prio, pdl_enabled()};  // follows the split pass in the same stream
   const dim3 gp((unsigned)std::min(blocks, std::max(max_ctas, 1)), (unsigned)batch);
   if (single_chunk)  // blocks = output tiles of the launch; persistent CTAs over ranges of tiles
     return fold_groups() == 4
-               ? launch_k(k_gemm_emu_persist<4>, gp, dim3(64 + 128 * 4), kPSmemBytes, st, lg, gd, ed, d0, d1, blocks,
-                          arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status)
-               : launch_k(k_gemm_emu_persist<2>, gp, dim3(64 + 128 * 2), kPSmemBytes, st, lg, gd, ed, d0, d1, blocks,
-                          arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status);
-  return launch_k(k_gemm_emu_chunked<kChunkedGroups>, gp, dim3(64 + 128 * kChunkedGroups), kCSmemBytes, st, lg, gd,
-                  ed, d0, d1, blocks, arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status);
+               ? launch_k(k_gemm_emu_persist<4, ND>, gp, dim3(64 + 128 * 4), p_smem_bytes(ND), st, lg, gd, ed, d0,
+                          d1, blocks, arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride, status,
+                          wait_ns)
+               : launch_k(k_gemm_emu_persist<2, ND>, gp, dim3(64 + 128 * 2), p_smem_bytes(ND), st, lg, gd, ed, d0,
+                          d1, blocks, arena, stride, (const unsigned*)words, (const int*)ints, wstride, istride,
+                          status, wait_ns);
+  return launch_k(k_gemm_emu_chunked<kChunkedGroups, ND>, gp, dim3(64 + 128 * kChunkedGroups), c_smem_bytes(ND), st,
+                  lg, gd, ed, d0, d1, blocks, arena, stride, (const unsigned*)words, (const int*)ints, wstride,
+                  istride, status, wait_ns);
+}
+
+cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
+                       double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
+                       int* status, bool single_chunk, int max_ctas, int ndig, cudaStream_t st, LaunchOpt lo,
+                       unsigned long long wait_ns) {
+  switch (ndig) {
+    case 3:
+      return launch_emu_nd<3>(gd, ed, d0, d1, items, blocks, batch, arena, stride, words, ints, wstride, istride,
+                              status, single_chunk, max_ctas, st, lo, wait_ns);
+    case 7:
+      return launch_emu_nd<7>(gd, ed, d0, d1, items, blocks, batch, arena, stride, words, ints, wstride, istride,
+                              status, single_chunk, max_ctas, st, lo, wait_ns);
+    case 8:
+      return launch_emu_nd<8>(gd, ed, d0, d1, items, blocks, batch, arena, stride, words, ints, wstride, istride,
+                              status, single_chunk, max_ctas, st, lo, wait_ns);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 // A persistent bulk CTA (576 threads x 96 registers) leaves too few
@@ -881,8 +973,8 @@ cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStr
   const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
   const int ctas = op.stream ? std::max(1, p.num_sms - p.chain_sms) : p.num_sms;
   return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.batch, arena, p.arena_elems,
-                    p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, ctas, st,
-                    op_launch(p, op));
+                    p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, ctas, op.ndig,
+                    st, op_launch(p, op), p.wait_ns);
 }
 
 }  // namespace cl
@@ -890,6 +982,8 @@ cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStr
 // ---------------------------------------------------------------------------
 // Stand-alone FP64-accurate complex GEMM through the same kernels.
 namespace {
+
+constexpr int kZgemmDigits = 7;  // the stand-alone GEMM: an FP64 GEMM's accuracy
 
 struct ZgemmLayout {
   cl::GemmDesc g;
@@ -907,8 +1001,8 @@ bool zgemm_layout(int M, int N, int K, ZgemmLayout& z) {
   e.Kp = (K + 31) / 32 * 32;
   const int64_t nch = e.Kp / 32;
   e.adig = 0;
-  e.bdig = (7LL * e.Mp * e.Kp + 63) / 64 * 64;
-  const int64_t words = e.bdig + (7LL * 2 * e.Np * e.Kp + 63) / 64 * 64;
+  e.bdig = ((int64_t)kZgemmDigits * e.Mp * e.Kp + 63) / 64 * 64;
+  const int64_t words = e.bdig + ((int64_t)kZgemmDigits * 2 * e.Np * e.Kp + 63) / 64 * 64;
   e.aexp = 0;
   e.bexp = nch * e.Mp;
   const int64_t ints = e.bexp + nch * e.Np;
@@ -972,6 +1066,6 @@ extern "C" int cl_zgemm_emu(int M, int N, int K, const double* A, int lda, const
   e = cl::launch_emu(reinterpret_cast<const cl::GemmDesc*>(wb), reinterpret_cast<const cl::EmuDesc*>(wb + 128), 0, 1,
                      z.e.items, z.blocks, 1, reinterpret_cast<double2*>(const_cast<double*>(A)), 0,
                      reinterpret_cast<unsigned*>(wb + z.words_off), reinterpret_cast<int*>(wb + z.ints_off), 0, 0,
-                     status, z.e.Kp == 32, sms, stream);
+                     status, z.e.Kp == 32, sms, kZgemmDigits, stream, cl::LaunchOpt{}, cl::kDefaultWaitNs);
   return e == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }

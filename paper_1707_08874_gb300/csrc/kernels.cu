@@ -13,7 +13,7 @@ namespace cl {
 template <typename T>
 __global__ void k_assemble(const double* __restrict__ links, T* __restrict__ arena, int64_t stride,
                            const int64_t* __restrict__ off, const int* __restrict__ ld, LatticeGeo g,
-                           double m, double mu) {
+                           double m, double mu, int* __restrict__ status) {
   pdl_enter();
   const int link = blockIdx.x * blockDim.x + threadIdx.x;
   if (link >= 4 * g.V) return;
@@ -23,6 +23,10 @@ __global__ void k_assemble(const double* __restrict__ links, T* __restrict__ are
   const int V = g.V;
   M3 u;
   load_m3(links + ((int64_t)rep * 4 * V + link) * 18, u);
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) finite = finite && isfinite(u.e[i].x) && isfinite(u.e[i].y);
+  if (!finite) set_status(status, CL_ERR_NONFINITE, s, nu);  // a non-finite link (site, direction)
   M3 ui = inv_m3(u);
   const double ph = 0.5 * g.phase(s, nu);
   const double ef = nu == 3 ? exp(mu) : 1.0, eb = nu == 3 ? exp(-mu) : 1.0;
@@ -411,11 +415,15 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
     for (int w = 1; w < NW; ++w) m = max(m, wmax[w]);
     const double rel = sizeof(R) == 8 ? 1e-13 : 1e-6;
     const long long thr = value_key(rel * key_value(m, R(0)), R(0));
+    // a block holding an infinity or NaN (magnitude key at or above the
+    // infinity's) is reported as non-finite, not as a tiny pivot
+    const long long inf_key = sizeof(R) == 8 ? 0x7FF0000000000000ll : 0x7F800000ll;
     int bad = 0x7fffffff;
     for (int c = lane; c < bp; c += 32)
       if (pkey[c] < thr || pkey[c] == 0) bad = min(bad, c);
     bad = __reduce_min_sync(0xffffffffu, bad);
-    if (lane == 0 && bad != 0x7fffffff) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + bad);
+    if (lane == 0 && m >= inf_key) set_status(status, CL_ERR_NONFINITE, d.node, d.col0);
+    else if (lane == 0 && bad != 0x7fffffff) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + bad);
   }
   __syncthreads();
   for (int e = tid; e < nel; e += NT) {
@@ -577,7 +585,8 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
       return cudaMemset2DAsync(arena, (size_t)stride * sizeof(T), 0, (size_t)p.pool_elems * sizeof(T),
                                (size_t)p.batch, st);
     case OP_ASSEMBLE:
-      return launch_k(k_assemble<T>, grid1, dim3(128), 0, st, prio, links, arena, stride, p.d_off, p.d_ld, g, m, mu);
+      return launch_k(k_assemble<T>, grid1, dim3(128), 0, st, prio, links, arena, stride, p.d_off, p.d_ld, g, m, mu,
+                      p.d_status);
     case OP_EXTADD:
       return launch_k(k_extend_add<T>, grid1, dim3(256), 0, st, prio, p.d_extadd, op.d0, op.d1, p.d_maps, arena,
                       stride);

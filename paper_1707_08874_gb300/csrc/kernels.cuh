@@ -71,12 +71,14 @@ cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st);
 cudaError_t emu_prepare();
 cudaError_t panel_prepare();
-// split pass + tcgen05 digit GEMM over descriptors [d0, d1); blocks = output
+// split pass + tcgen05 digit GEMM over descriptors [d0, d1) with ndig digits
+// per operand (3, 7 or 8); blocks = output
 // tiles (128 x 16 complex); persistent kernels (single_chunk: every K <= 32)
 // on min(blocks, max_ctas) CTAs, each a contiguous range of tiles
 cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, int items, int blocks, int batch,
                        double2* arena, int64_t stride, unsigned* words, int* ints, int64_t wstride, int64_t istride,
-                       int* status, bool single_chunk, int max_ctas, cudaStream_t st, LaunchOpt lo = LaunchOpt{});
+                       int* status, bool single_chunk, int max_ctas, int ndig, cudaStream_t st, LaunchOpt lo,
+                       unsigned long long wait_ns);
 
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,

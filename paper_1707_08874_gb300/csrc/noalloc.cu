@@ -1,15 +1,26 @@
 // Allocation-free drift evaluation for small lattices.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// drift: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a stream operation), host runtimes whose device memory is
-// owned and budgeted by another allocator, or plugins that must not grow the
-// process's footprint per call.  cl_drift_eval_noalloc serves them: all the
+// drift: host runtimes whose device memory is owned and budgeted by another
+// allocator (a framework's caching allocator that has reserved the GPU), or
+// plugins and embedded solvers that must not grow the process's footprint
+// per call, or loops that cannot afford cudaMalloc / cudaFree, which may
+// synchronise the whole device.  cl_drift_eval_noalloc serves them: all the
 // scratch memory the factorisation and the selected inversion need (fronts,
 // workspace, index tables, status word) lives in one file-scope device array
 // of fixed size that every GPU loading this library holds until the process
 // exits.  The paper has no counterpart; it is a deployment convenience.
+//
+// Set-up work: the first call on a device looks up the array's device
+// address (cudaGetSymbolAddress), and the first call for a lattice shape on a
+// device analyses the shape on the host and uploads its index tables into the
+// array; later calls with the same shape on that device reuse both, so they
+// issue only a status-word clear and the kernels.  Make those first calls
+// before any stream capture.  The cached address belongs to the device's
+// context: after cudaDeviceReset the entry point must not be called again in
+// the same process.
 #include <mutex>
+#include <new>
 #include <stdexcept>
 
 #include "kernels.cuh"
@@ -26,14 +37,21 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 
+// the shape whose tables are resident in a device's scratch array, and its
+// host plan (op lists and descriptor tables)
+struct Resident {
+  int Ns = 0, Nt = 0;
+  cl::Plan plan;
+  size_t arena_bytes = 0;
+};
+Resident* g_resident[kMaxDevices] = {};
+
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Device address of the scratch array on the current device.  The symbol name
 // is only a host-side handle; the address must be queried on each device.
-int scratch_address(unsigned char** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CL_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mutex);
+// Called with g_mutex held.
+int scratch_address(int dev, unsigned char** out) {
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -52,18 +70,20 @@ cudaError_t place(unsigned char* base, size_t& off, V*& dst, const void* src, si
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
 }
 
-}  // namespace
-
-extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double m, double mu, double nf,
-                                     double* Gdiag, double* Gfwd, double* Gbwd, double* Kf,
-                                     cudaStream_t stream) {
-  if (!links || !Gfwd || !Gbwd || !Kf) return CL_ERR_INVALID_ARG;
-  cl::Plan p;
+// Analyses (Ns, Nt), checks that it fits the array and uploads its tables on
+// `stream`, synchronising the stream so that the pageable host tables have
+// reached the device before they go out of scope.  Called with g_mutex held.
+int make_resident(int dev, int Ns, int Nt, unsigned char* base, cudaStream_t stream) {
+  Resident* r = new (std::nothrow) Resident();
+  if (!r) return CL_ERR_OOM;
+  cl::Plan& p = r->plan;
   try {
     cl::analyze_host(p, Ns, Nt, 1, CL_FP64);
   } catch (const std::invalid_argument&) {
+    delete r;
     return CL_ERR_INVALID_ARG;
   } catch (...) {
+    delete r;
     return CL_ERR_UNSUPPORTED;
   }
   // layout inside the scratch array: status | arena | tables
@@ -75,24 +95,24 @@ extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double
   ld.insert(ld.end(), p.ld_diag.begin(), p.ld_diag.end());
   ld.insert(ld.end(), p.ld_fwd.begin(), p.ld_fwd.end());
   ld.insert(ld.end(), p.ld_bwd.begin(), p.ld_bwd.end());
-  const size_t arena_bytes = align256((size_t)p.arena_elems * sizeof(double2));
-  size_t need = 256 + arena_bytes;
+  r->arena_bytes = align256((size_t)p.arena_elems * sizeof(double2));
+  size_t need = 256 + r->arena_bytes;
   const size_t table_bytes[] = {off.size() * sizeof(int64_t), ld.size() * sizeof(int), p.maps.size() * sizeof(int),
                                 p.gemm.size() * sizeof(cl::GemmDesc), p.panels.size() * sizeof(cl::PanelDesc),
                                 p.copies.size() * sizeof(cl::CopyDesc), p.extadd.size() * sizeof(cl::ExtAddDesc),
                                 p.gather.size() * sizeof(cl::GatherDesc)};
   for (size_t b : table_bytes) need += align256(b ? b : 16);
-  if (need > kNoAllocBytes) return CL_ERR_UNSUPPORTED;
-
-  unsigned char* base = nullptr;
-  int st = scratch_address(&base);
-  if (st != CL_OK) return st;
-  if (cl::panel_prepare() != cudaSuccess) return CL_ERR_CUDA;
+  if (need > kNoAllocBytes) {
+    delete r;
+    return CL_ERR_UNSUPPORTED;
+  }
+  // the previous shape's tables are about to be overwritten
+  delete g_resident[dev];
+  g_resident[dev] = nullptr;
   p.d_status = reinterpret_cast<int*>(base);
   p.d_arena = base + 256;
-  size_t o = 256 + arena_bytes;
-  cudaError_t e = cudaMemsetAsync(p.d_status, 0, 4 * sizeof(int), stream);
-  if (e == cudaSuccess) e = place(base, o, p.d_off, off.data(), table_bytes[0], stream);
+  size_t o = 256 + r->arena_bytes;
+  cudaError_t e = place(base, o, p.d_off, off.data(), table_bytes[0], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_ld, ld.data(), table_bytes[1], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_maps, p.maps.data(), table_bytes[2], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_gemm, p.gemm.data(), table_bytes[3], stream);
@@ -100,6 +120,38 @@ extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double
   if (e == cudaSuccess) e = place(base, o, p.d_copies, p.copies.data(), table_bytes[5], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_extadd, p.extadd.data(), table_bytes[6], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_gather, p.gather.data(), table_bytes[7], stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    delete r;
+    return CL_ERR_CUDA;
+  }
+  r->Ns = Ns;
+  r->Nt = Nt;
+  g_resident[dev] = r;
+  return CL_OK;
+}
+
+}  // namespace
+
+extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double m, double mu, double nf,
+                                     double* Gdiag, double* Gfwd, double* Gbwd, double* Kf,
+                                     cudaStream_t stream) {
+  if (!links || !Gfwd || !Gbwd || !Kf) return CL_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CL_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  unsigned char* base = nullptr;
+  int st = scratch_address(dev, &base);
+  if (st != CL_OK) return st;
+  if (!g_resident[dev] || g_resident[dev]->Ns != Ns || g_resident[dev]->Nt != Nt) {
+    if (cl::panel_prepare() != cudaSuccess) return CL_ERR_CUDA;
+    st = make_resident(dev, Ns, Nt, base, stream);
+    if (st != CL_OK) return st;
+  }
+  const cl::Plan& p = g_resident[dev]->plan;
+  // the status word must start at zero; the fronts are cleared by the
+  // schedule's first op
+  cudaError_t e = cudaMemsetAsync(p.d_status, 0, 4 * sizeof(int), stream);
   if (e != cudaSuccess) return CL_ERR_CUDA;
   double2* arena = static_cast<double2*>(p.d_arena);
   for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
@@ -109,7 +161,5 @@ extern "C" int cl_drift_eval_noalloc(int Ns, int Nt, const double* links, double
       if (e != cudaSuccess) return CL_ERR_CUDA;
     }
   e = cl::launch_drift(p, links, Gfwd, Gbwd, mu, nf, Kf, stream);
-  // the tables above were copied from pageable host memory, which the copy
-  // engine has consumed when cudaMemcpyAsync returns; p may go out of scope
   return e == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }

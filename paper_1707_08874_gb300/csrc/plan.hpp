@@ -23,6 +23,20 @@ constexpr int kLeafSites = 8;
 constexpr int kPanelFP64 = 48;
 constexpr int kPanelFP32 = 30;
 constexpr int kPanelEmu = 30;
+// digits per operand of the digit GEMMs (CL_FP64_EMU: every product to
+// ~2^-58 of its row / column maxima; CL_MIXED_BF16X3: split-BF16x3 Schur and
+// off-diagonal selected-inverse products, 7 digits (an FP64 GEMM's accuracy)
+// for the panel products with the pivot-block inverse and the diagonal blocks
+// of the selected-inverse sweep)
+constexpr int kDigitsFP64 = 8;
+constexpr int kDigitsMixed = 3;
+constexpr int kDigitsDiag = 7;
+// precisions whose front GEMMs run on the BF16 tensor cores as digit products
+inline bool digit_gemms(int precision) { return precision == CL_FP64_EMU || precision == CL_MIXED_BF16X3; }
+
+// bound of every mbarrier wait of the tensor-core GEMMs (0.5 s); a wait that
+// runs out records CL_ERR_TIMEOUT and the kernel drains and leaves
+constexpr unsigned long long kDefaultWaitNs = 500000000ull;
 
 struct SNode {
   std::vector<int> sep;       // sites eliminated at this supernode (front order)
@@ -121,7 +135,8 @@ struct Op {
   int stream = 0;
   int wait = -1;
   bool signal = false;
-  bool single_chunk = false;  // CL_FP64_EMU GEMM with every K <= 32: persistent kernel
+  bool single_chunk = false;  // digit GEMM with every K <= 32: persistent kernel
+  int ndig = 0;               // digit GEMM: base-256 digits per operand (3, 7 or 8)
   bool pdl = false;           // set at launch: the op's first kernel follows a kernel of its stream directly
 };
 
@@ -132,6 +147,7 @@ struct Plan {
   int device = 0;
   int num_sms = 0;            // multiprocessors of the device (set up with the device state)
   int chain_sms = 2;          // SMs the bulk digit GEMMs leave to the panel chain (two-stream plans)
+  unsigned long long wait_ns = kDefaultWaitNs;  // limit of the GEMM roles' mbarrier waits (cl_plan_set_wait_limit)
   std::vector<SNode> nodes;   // postorder, root last
   int n_levels = 0;
   double factor_flops = 0, selinv_flops = 0;

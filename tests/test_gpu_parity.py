@@ -1,14 +1,19 @@
 """GPU parity: the CUDA selected inversion and drift against the CPU oracle.
 
-Tolerance (FP64 path).  The oracle is a dense LU with partial pivoting; the
-multifrontal factorisation may pivot only inside each supernode's panels
-(static ordering, as in every supernodal selected inversion).  Its rounding
-error is therefore bounded by the condition number of D times a growth factor
-of the static ordering: on the paper's link distribution the measured ratio
-err / kappa(D) is about 1e-14.  The bar is the 1e-10 normwise target wherever
-kappa(D) allows it and 1e-13 * kappa(D) above (kappa from the oracle's own
-dense D), for the G blocks (max_b |dG_b|_F / max_b |G_b|_F) and for the drift
-(max |dK| / max |K|).
+Tolerances (c14: normwise, max_b |dG_b|_F / max_b |G_b|_F over the selected
+blocks and max |dK| / max |K| for the drift).
+
+* CL_FP64_EMU, the FP64 path of the library: 1e-10 at every size, the 8^3 x 4
+  benchmark lattice included.  Its front GEMMs are 8-digit products accurate
+  to ~2^-58 of the operands' row / column maxima, far below the FP64 rounding
+  of their results; with products that accurate the static (supernode-
+  restricted) pivoting of the multifrontal method stays well inside the bar.
+* CL_FP64, the same factorisation on the FP64 tensor pipe with plain FP64
+  products (K u rounding per GEMM): the textbook bound of FP64 arithmetic with
+  static pivoting, 1e-13 kappa(D) (kappa from the oracle's dense D), or 1e-10
+  where that is larger.  On 8^3 x 4 (kappa 2e4) its error is ~1.5e-10.
+* CL_MIXED_BF16X3: split-BF16x3 Schur products with FP64 pivot blocks; the
+  bound stated per lattice in MIXED_BOUND.
 """
 import numpy as np
 import pytest
@@ -20,6 +25,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 M, MU = 0.05, 0.25
+BAR = 1e-10
 
 
 def _binding():
@@ -27,10 +33,14 @@ def _binding():
     return B
 
 
-def _tol(D):
+def _tol(D, prec="fp64_emu"):
+    """(bar, kappa): 1e-10 for the FP64 path, the static-pivoting FP64 bound for
+    the plain-FP64 tensor-pipe path"""
     sv = np.linalg.svd(D, compute_uv=False)
     kappa = sv[0] / sv[-1]
-    return max(1e-10, 1e-13 * kappa), kappa
+    if prec == "fp64":
+        return max(BAR, 1e-13 * kappa), kappa
+    return BAR, kappa
 
 
 def _blockwise(a, b):
@@ -55,18 +65,19 @@ PRECS = ["fp64", "fp64_emu"]
 
 
 def _prec(B, name):
-    return {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_FP32}[name]
+    return {"fp64": B.CL_FP64, "fp64_emu": B.CL_FP64_EMU, "mixed": B.CL_MIXED_BF16X3,
+            "fp32": B.CL_MIXED_FP32}[name]
 
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("ns,nt,seed", [(4, 4, 1707), (4, 4, 1), (6, 4, 1707), (4, 6, 3)])
 def test_fp64_parity_small(ns, nt, seed, prec):
     """FP64 fronts, and FP64 fronts whose GEMMs are exact BF16 digit products
-    (CL_FP64_EMU): both held to the FP64 bar."""
+    (CL_FP64_EMU), each held to its bar."""
     B = _binding()
     U = inputs.random_links(ns, nt, seed=seed)
     ref = oracle.drift_eval(ns, nt, U, M, MU)
-    tol, kappa = _tol(oracle.dirac_dense(ns, nt, U, M, MU))
+    tol, kappa = _tol(oracle.dirac_dense(ns, nt, U, M, MU), prec)
     plan = B.Plan.analyze(ns, nt, 1, _prec(B, prec))
     got, st = _run(plan, U)
     assert st == B.CL_OK
@@ -92,8 +103,9 @@ def test_fp64_parity_panel_widths(panel, prec):
     U = inputs.random_links(6, 4, seed=1707)
     if not _REF64:
         _REF64["ref"] = oracle.drift_eval(6, 4, U, M, MU)
-        _REF64["tol"] = _tol(oracle.dirac_dense(6, 4, U, M, MU))
-    ref, (tol, kappa) = _REF64["ref"], _REF64["tol"]
+        _REF64["D"] = oracle.dirac_dense(6, 4, U, M, MU)
+    ref = _REF64["ref"]
+    tol, kappa = _tol(_REF64["D"], prec)
     plan = B.Plan.analyze_ex(6, 4, 1, _prec(B, prec), panel)
     assert plan.info["panel"] == panel
     got, st = _run(plan, U)
@@ -132,7 +144,7 @@ def test_fp64_batch_replicas_independent(prec):
     assert st == B.CL_OK
     for b in range(3):
         ref = oracle.drift_eval(4, 4, U[b], M, MU)
-        tol, _ = _tol(oracle.dirac_dense(4, 4, U[b], M, MU))
+        tol, _ = _tol(oracle.dirac_dense(4, 4, U[b], M, MU), prec)
         assert _blockwise(got["Gbwd"][b], ref["Gbwd"]) < tol
         assert np.abs(got["Kf"][b] - ref["Kf"]).max() < tol * np.abs(ref["Kf"]).max()
     plan.close()
@@ -168,44 +180,126 @@ def test_free_chain_sms_bitwise(monkeypatch):
             assert np.array_equal(got[key], outs[0][key]), key
 
 
-def test_nonfinite_status():
-    """A NaN link is reported through the status word, not a fault."""
+@pytest.mark.parametrize("prec", PRECS + ["mixed"])
+def test_nonfinite_status(prec):
+    """A NaN link is reported as CL_ERR_NONFINITE (naming its site and
+    direction), not as a singular pivot and not as a fault; a clean
+    configuration afterwards clears it."""
     B = _binding()
     U = inputs.random_links(4, 4, seed=2)
     U[17, 2, 1, 1] = np.nan
-    plan = B.Plan.analyze(4, 4, 1, B.CL_FP64)
-    got, st = _run(plan, U)
-    assert st in (B.CL_ERR_NONFINITE, B.CL_ERR_SINGULAR)
+    plan = B.Plan.analyze(4, 4, 1, _prec(B, prec))
+    links = torch.from_numpy(U[None].copy()).to("cuda")
+    out = plan.alloc_outputs()
+    plan.drift_eval(links, M, MU, 1.0, out["Gdiag"], out["Gfwd"], out["Gbwd"], out["Kf"])
+    st, detail = plan.get_status()
+    assert st == B.CL_ERR_NONFINITE and detail == (17, 2), (st, detail)
     U = inputs.random_links(4, 4, seed=2)
     got, st = _run(plan, U)
     assert st == B.CL_OK
     plan.close()
 
 
+def test_nonfinite_drift_input():
+    """A NaN only in the G blocks handed to cl_fermion_drift (the factorisation
+    itself clean) is reported by the drift kernel as CL_ERR_NONFINITE with the
+    link's site and direction."""
+    B = _binding()
+    U = inputs.random_links(4, 4, seed=3)
+    plan = B.Plan.analyze(4, 4, 1, B.CL_FP64_EMU)
+    got, st = _run(plan, U)
+    assert st == B.CL_OK
+    links = torch.from_numpy(U[None].copy()).to("cuda")
+    Gf = torch.from_numpy(got["Gfwd"]).to("cuda")
+    Gb = torch.from_numpy(got["Gbwd"]).to("cuda")
+    Gf[0, 40, 1, 2, 0] = complex(np.nan, 0.0)
+    Kf = torch.zeros_like(plan.alloc_outputs()["Kf"])
+    plan.fermion_drift(links, Gf, Gb, MU, 1.0, Kf)
+    st, detail = plan.get_status()
+    assert st == B.CL_ERR_NONFINITE and detail == (40, 1), (st, detail)
+    plan.close()
+
+
+def test_wait_timeout_reported_and_recovered():
+    """The tensor-core GEMMs' waits are bounded.  With the plan's wait limit
+    set to 0 a wait that is not already complete gives up: the kernel records
+    CL_ERR_TIMEOUT, drains its copies and MMAs with the full bound, frees its
+    tensor memory and returns.  The context stays usable: with the default
+    limit restored the next evaluation is clean and matches the oracle."""
+    B = _binding()
+    U = inputs.random_links(4, 4, seed=1707)
+    plan = B.Plan.analyze(4, 4, 1, B.CL_FP64_EMU)
+    plan.set_wait_limit(0.0)
+    got, st = _run(plan, U)
+    assert st == B.CL_ERR_TIMEOUT, B.error_string(st)
+    plan.set_wait_limit(-1.0)
+    got, st = _run(plan, U)
+    assert st == B.CL_OK
+    ref = oracle.drift_eval(4, 4, U, M, MU)
+    assert _blockwise(got["Gfwd"][0], ref["Gfwd"]) < BAR
+    assert np.abs(got["Kf"][0] - ref["Kf"]).max() < BAR * np.abs(ref["Kf"]).max()
+    plan.close()
+
+
+# Mixed form (CL_MIXED_BF16X3): stated bounds of the normwise G-block and drift
+# errors against the oracle per lattice (seed 1707, m = 0.05, mu = 0.25), about
+# twice the errors measured on GB300 (G blocks / drift: 2.7e-3 / 1.5e-3 at 4^4,
+# 1.9e-2 / 1.8e-2 at 6^3x4, 8.9e-2 / 1.2e-1 at 8^3x4): kappa(D) x growth x 2^-24
+MIXED_BOUND = {(4, 4): 6e-3, (6, 4): 4e-2, (8, 4): 0.25}
+
+
+@pytest.mark.parametrize("ns,nt", sorted(MIXED_BOUND))
+def test_mixed_bf16x3_bound(ns, nt, full_size):
+    """The benchmark spec's mixed form: Schur-complement and off-diagonal
+    selected-inverse GEMMs as split-BF16x3 products with FP32 accumulation,
+    FP64 pivot-block inverses and FP64-accurate diagonal selected-inverse
+    blocks; its G blocks and drift stay within the bound stated for the
+    lattice, and it is not an FP64-accurate result (the bound is not vacuous)."""
+    B = _binding()
+    if (ns, nt) == (8, 4):
+        U, ref = full_size["U"], full_size["ref"]
+    else:
+        U = inputs.random_links(ns, nt, seed=1707)
+        ref = oracle.drift_eval(ns, nt, U, M, MU)
+    plan = B.Plan.analyze(ns, nt, 1, B.CL_MIXED_BF16X3)
+    got, st = _run(plan, U)
+    assert st == B.CL_OK
+    bound = MIXED_BOUND[(ns, nt)]
+    errs = [_blockwise(got[k][0], ref[k]) for k in ("Gdiag", "Gfwd", "Gbwd")]
+    kerr = np.abs(got["Kf"][0] - ref["Kf"]).max() / np.abs(ref["Kf"]).max()
+    assert max(errs) < bound and kerr < bound, (errs, kerr, bound)
+    assert kerr > 1e-9  # FP32-class, not FP64
+    plan.close()
+
+
 @pytest.fixture(scope="module")
 def full_size():
+    """8^3 x 4 with the benchmark's links (seed 1707): the oracle's full
+    inverse (dense LU with partial pivoting, every column solved) and its
+    selected blocks and drift; kappa(D) from the SVD."""
     ns, nt = 8, 4
     U = inputs.random_links(ns, nt, seed=1707)
     D = oracle.dirac_dense(ns, nt, U, M, MU)
-    tol, kappa = _tol(D)
-    LU, piv, info = oracle.lu(D)
-    assert info == 0
-    return U, D, tol, LU, piv
+    return {"U": U, "D": D, "ref": oracle.drift_eval(ns, nt, U, M, MU)}
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_fp64_full_size_sampled(prec, full_size):
-    """8^3 x 4 (the benchmark workload, batch 1): sampled columns of D^{-1} from
-    the oracle's LU, every selected block touching them, the drift of the links
-    whose both blocks are known, and D G = 1 on every site."""
+def test_fp64_full_size(prec, full_size):
+    """8^3 x 4 (the benchmark workload, batch 1, default panel width): every
+    selected block G_xx, G_x,x+nu, G_x+nu,x and every drift entry against the
+    oracle's full inverse, and D G = 1 on every site from the selected blocks."""
     B = _binding()
     ns, nt = 8, 4
     V = ns ** 3 * nt
-    U, D, tol, LU, piv = full_size
+    U, D, ref = full_size["U"], full_size["D"], full_size["ref"]
+    tol, kappa = _tol(D, prec)
     plan = B.Plan.analyze(ns, nt, 1, _prec(B, prec))
     got, st = _run(plan, U)
     assert st == B.CL_OK
     Gd, Gf, Gb, K = got["Gdiag"][0], got["Gfwd"][0], got["Gbwd"][0], got["Kf"][0]
+    errs = {k: _blockwise(got[k][0], ref[k]) for k in ("Gdiag", "Gfwd", "Gbwd")}
+    kerr = np.abs(K - ref["Kf"]).max() / np.abs(ref["Kf"]).max()
+    assert max(errs.values()) < tol and kerr < tol, (errs, kerr, tol, kappa)
     # D G = 1 on the diagonal blocks, from the selected blocks only
     up = inputs.shift_table(ns, nt)
     dn = np.empty_like(up)
@@ -218,29 +312,6 @@ def test_fp64_full_size_sampled(prec, full_size):
         dg = dg + Db[x, up[:, nu]] @ Gb[:, nu] + Db[x, dn[:, nu]] @ Gf[dn[:, nu], nu]
     gnorm = np.sqrt((np.abs(Gf) ** 2).sum((-1, -2))).max()
     assert np.abs(dg - np.eye(3)).max() < 10 * tol * gnorm
-    # sampled columns
-    rng = np.random.default_rng(0)
-    ys = rng.choice(V, 6, replace=False)
-    sites = sorted(set(int(y) for y in ys) | {int(up[y, nu]) for y in ys for nu in range(4)})
-    cols = np.array([3 * s + a for s in sites for a in range(3)])
-    X = oracle.solve_unit_columns(LU, piv, cols)
-    col = {s: X[:, 3 * i:3 * i + 3] for i, s in enumerate(sites)}
-    scale = np.sqrt((np.abs(Gf) ** 2).sum((-1, -2))).max()
-    Gf_ref = np.zeros_like(Gf)
-    Gb_ref = np.zeros_like(Gb)
-    for y in ys:
-        blk = lambda x: col[int(y)][3 * x:3 * x + 3]
-        assert np.linalg.norm(Gd[y] - blk(y)) < tol * scale
-        for nu in range(4):
-            yp = int(up[y, nu])
-            assert np.linalg.norm(Gb[y, nu] - blk(yp)) < tol * scale          # G_{y+nu,y}
-            assert np.linalg.norm(Gf[dn[y, nu], nu] - blk(int(dn[y, nu]))) < tol * scale  # G_{y-nu,y}
-            Gb_ref[y, nu] = blk(yp)
-            Gf_ref[y, nu] = col[yp][3 * y:3 * y + 3]                          # G_{y,y+nu}
-            assert np.linalg.norm(Gf[y, nu] - Gf_ref[y, nu]) < tol * scale
-    Kref = oracle.fermion_drift(ns, nt, U, Gf_ref, Gb_ref, MU)
-    kmax = np.abs(K).max()
-    assert np.abs(K[ys] - Kref[ys]).max() < tol * kmax
     plan.close()
 
 

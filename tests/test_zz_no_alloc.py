@@ -1,10 +1,10 @@
 """The allocation-free drift entry point against the regular one.
 
-cl_drift_eval_noalloc serves callers that cannot allocate device memory (for
-instance code running under stream capture, or a host runtime that owns all
-device memory); it keeps its scratch in a fixed device array inside the
-library.  This file is collected last so that a failure here does not hide
-the rest of the suite.
+cl_drift_eval_noalloc serves callers that cannot allocate device memory (a
+host runtime whose allocator owns the GPU's memory, a plugin that must not
+grow the footprint, a loop that cannot afford cudaMalloc's synchronisation);
+it keeps its scratch in a fixed device array inside the library.  This file is
+collected last so that a failure here does not hide the rest of the suite.
 """
 import numpy as np
 import pytest
