@@ -87,20 +87,23 @@ typedef struct cl_group cl_group;
 
 /* Summary of a plan (host values, no device access). */
 typedef struct cl_plan_info {
-  int Ns, Nt, V, N;          /* lattice and matrix order N = 3V                */
-  int batch;                 /* replicas per call                               */
+  int Ns, Nt, V, N;          /* lattice and matrix order N = 3V (ragged plan:
+                                Ns = Nt = 0, V = sites of all its lattices)    */
+  int batch;                 /* replicas per call (ragged: lattices per call)   */
   int precision;             /* CL_FP64, CL_MIXED_FP32, CL_FP64_EMU or CL_MIXED_BF16X3 */
   int n_supernodes;          /* separators of the nested dissection            */
   int n_levels;              /* height of the elimination tree + 1              */
   int max_front;             /* largest front order (unknowns)                  */
   int max_pivot_block;       /* largest supernode (pivot unknowns)              */
   int panel;                 /* pivoting panel width (unknowns, multiple of 3)  */
-  double factor_flops;       /* real flops of one factorisation (per replica)   */
-  double selinv_flops;       /* real flops of one selected inversion            */
+  double factor_flops;       /* real flops of one factorisation (per replica;
+                                ragged: averaged over its lattices)            */
+  double selinv_flops;       /* real flops of one selected inversion (same)     */
   double front_bytes;        /* device bytes of the front pool (all replicas)   */
   double device_bytes;       /* all device memory held by the plan              */
   int launches_per_eval;     /* library kernel launches of one cl_drift_eval    */
   double workspace_bytes;    /* digit workspace of CL_FP64_EMU / CL_MIXED_BF16X3 (all replicas) */
+  int n_shapes;              /* lattice shapes: 1, or nshapes of cl_analyze_ragged */
 } cl_plan_info;
 
 /* Per-kernel timing record filled by cl_profile_read. */
@@ -171,6 +174,35 @@ int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan);
 int cl_analyze_ex(int Ns, int Nt, int batch, int precision, int panel, cl_plan** plan);
 
 /*
+ * cl_analyze_ragged -- one plan over lattices of several shapes (Sec. 4: the
+ * paper's runs span lattice sizes; production batches mix them):
+ *   nshapes     number of shapes, >= 1
+ *   Ns, Nt      host arrays [nshapes]: extents of each shape (even, >= 4)
+ *   count       host array [nshapes]: lattices (replicas) of each shape, >= 1
+ *   precision   as cl_analyze
+ *   plan        out: library-owned handle, release with cl_destroy_plan
+ * Every shape is analysed once; the fronts of all lattices of all shapes lie
+ * side by side in one arena and one fixed schedule runs them level by level
+ * (height above the leaves), so each step of every level -- panel inverses,
+ * tensor-core GEMMs over all their output tiles, copies, extend-adds and
+ * gathers -- is one launch across all shapes and replicas; persistent GEMM
+ * CTAs take tile ranges of that launch regardless of the lattice they belong
+ * to.  The per-site steps (assembly, extraction, drift) run one launch per
+ * shape.  The compute calls cl_factor, cl_selinv_blocks, cl_fermion_drift and
+ * cl_drift_eval take the site-indexed arrays of all lattices concatenated in
+ * shape order, each shape's replicas in order: links [sum_i count_i V_i][4][3][3],
+ * Gdiag [..][3][3], Gfwd / Gbwd [..][4][3][3], Kf [..][4][8], V_i = Ns_i^3 Nt_i.
+ * The Langevin calls return CL_ERR_UNSUPPORTED on a ragged plan, and
+ * cl_plan_get_node too.  Returns CL_ERR_INVALID_ARG for bad shapes or counts
+ * (more than 65535 lattices), CL_ERR_OOM / CL_ERR_CUDA on allocation failure.
+ */
+int cl_analyze_ragged(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, cl_plan** plan);
+/* cl_analyze_ragged_ex -- cl_analyze_ragged with an explicit pivoting-panel
+ * width, common to all shapes (as cl_analyze_ex). */
+int cl_analyze_ragged_ex(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, int panel,
+                         cl_plan** plan);
+
+/*
  * cl_analyze_symbolic -- the host half of cl_analyze only (no device memory,
  * usable without a GPU).  The plan supports cl_plan_get_info and
  * cl_plan_get_node; compute calls on it return CL_ERR_INVALID_ARG.
@@ -178,6 +210,10 @@ int cl_analyze_ex(int Ns, int Nt, int batch, int precision, int panel, cl_plan**
 int cl_analyze_symbolic(int Ns, int Nt, int precision, cl_plan** plan);
 /* cl_analyze_symbolic_ex -- the same with an explicit pivot-panel width (as cl_analyze_ex). */
 int cl_analyze_symbolic_ex(int Ns, int Nt, int precision, int panel, cl_plan** plan);
+/* cl_analyze_ragged_symbolic -- the host half of cl_analyze_ragged_ex (panel
+ * 0 = the precision's default); supports the plan queries and exports. */
+int cl_analyze_ragged_symbolic(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, int panel,
+                               cl_plan** plan);
 
 /*
  * cl_factor -- numeric sparse LU of D(m;mu) (Sec. 3, first half of the
@@ -409,7 +445,12 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *   CL_TABLE_MAPS        the site maps of extend-add and gather
  *   CL_TABLE_OFF, CL_TABLE_LD
  *                        offset / leading dimension of the D blocks in the
- *                        fronts: [V] diagonal, [4V] (s, s+nu), [4V] (s+nu, s)
+ *                        fronts, per lattice shape: [V] diagonal, [4V]
+ *                        (s, s+nu), [4V] (s+nu, s)
+ *   CL_TABLE_SEGMENTS    per lattice shape: Ns, Nt, V, count, pool_base,
+ *                        rep_stride, table_base, site_base (replica r of the
+ *                        shape has its fronts at pool_base + r rep_stride, its
+ *                        tables at table_base, its sites at site_base + r V)
  * Offsets are elements of one replica's arena; a mask [r0, r1, r2, r3]
  * excludes the indices in [r0, r1) and [r2, r3).  Works on symbolic plans.
  */
@@ -424,7 +465,8 @@ enum {
   CL_TABLE_GATHER = 7,
   CL_TABLE_MAPS = 8,
   CL_TABLE_OFF = 9,
-  CL_TABLE_LD = 10
+  CL_TABLE_LD = 10,
+  CL_TABLE_SEGMENTS = 11
 };
 int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count);
 

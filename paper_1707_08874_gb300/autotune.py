@@ -73,6 +73,33 @@ def tune_panel(Ns, Nt, batch=1, precision=B.CL_FP64_EMU, candidates=CANDIDATES, 
     return best
 
 
+def tune_panel_ragged(shapes, precision=B.CL_FP64_EMU, candidates=CANDIDATES, steps=2) -> int:
+    """Panel width of a ragged plan (one width for all its shapes), timed on
+    the plan itself (not cached: the shape mix is the caller's)."""
+    import numpy as np
+    import torch
+    links = torch.from_numpy(np.concatenate(
+        [inputs.random_links(ns, nt, seed=inputs.BASE_SEED + i, batch=c).reshape((-1, 4, 3, 3))
+         for i, (ns, nt, c) in enumerate(shapes)])[None].copy()).to("cuda")
+    times = {}
+    for panel in candidates:
+        plan = B.Plan.analyze_ragged(shapes, precision, panel)
+        o = plan.alloc_outputs()
+        plan.drift_eval(links, 0.05, 0.25, 1.0, None, o["Gfwd"], o["Gbwd"], o["Kf"])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.drift_eval(links, 0.05, 0.25, 1.0, None, o["Gfwd"], o["Gbwd"], o["Kf"])
+        e1.record()
+        torch.cuda.synchronize()
+        st, _ = plan.get_status()
+        plan.close()
+        times[panel] = e0.elapsed_time(e1) / steps if st == B.CL_OK else float("inf")
+    return min(times, key=times.get)
+
+
 def tuned_plan(Ns, Nt, batch=1, precision=B.CL_FP64_EMU, **kw):
     panel = tune_panel(Ns, Nt, batch, precision, **kw)
     return B.Plan.analyze_ex(Ns, Nt, batch, precision, panel), panel

@@ -42,7 +42,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_levels", ctypes.c_int), ("max_front", ctypes.c_int), ("max_pivot_block", ctypes.c_int),
                 ("panel", ctypes.c_int), ("factor_flops", ctypes.c_double), ("selinv_flops", ctypes.c_double),
                 ("front_bytes", ctypes.c_double), ("device_bytes", ctypes.c_double),
-                ("launches_per_eval", ctypes.c_int), ("workspace_bytes", ctypes.c_double)]
+                ("launches_per_eval", ctypes.c_int), ("workspace_bytes", ctypes.c_double),
+                ("n_shapes", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,11 +81,13 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
            "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
-           "cl_analyze_symbolic_ex", "cl_plan_export", "cl_plan_set_wait_limit"]
+           "cl_analyze_symbolic_ex", "cl_plan_export", "cl_plan_set_wait_limit", "cl_analyze_ragged",
+           "cl_analyze_ragged_ex", "cl_analyze_ragged_symbolic"]
 
 # cl_plan_export tables (include/clselinv.h) and their int64 row widths
 TABLES = {"meta": (0, 10), "factor_ops": (1, 9), "selinv_ops": (2, 9), "gemm": (3, 20), "panel": (4, 5),
-          "copy": (5, 14), "extadd": (6, 11), "gather": (7, 7), "maps": (8, 1), "off": (9, 1), "ld": (10, 1)}
+          "copy": (5, 14), "extadd": (6, 11), "gather": (7, 7), "maps": (8, 1), "off": (9, 1), "ld": (10, 1),
+          "segments": (11, 8)}
 
 
 def lib_path() -> str:
@@ -136,6 +139,10 @@ def load(build_if_missing: bool = True):
     L.cl_plan_export.argtypes = [P, I, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
     L.cl_zgemm_emu.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, ctypes.c_size_t, P, P]
     L.cl_plan_set_wait_limit.argtypes = [P, D]
+    IA = ctypes.POINTER(I)
+    L.cl_analyze_ragged.argtypes = [I, IA, IA, IA, I, ctypes.POINTER(P)]
+    L.cl_analyze_ragged_ex.argtypes = [I, IA, IA, IA, I, I, ctypes.POINTER(P)]
+    L.cl_analyze_ragged_symbolic.argtypes = [I, IA, IA, IA, I, I, ctypes.POINTER(P)]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
@@ -235,6 +242,20 @@ class Plan:
         h = ctypes.c_void_p()
         _check(load().cl_analyze_ex(Ns, Nt, batch, precision, panel, ctypes.byref(h)), "cl_analyze_ex")
         return cls(h, False)
+
+    @classmethod
+    def analyze_ragged(cls, shapes, precision: int = CL_FP64_EMU, panel: int = 0, symbolic: bool = False) -> "Plan":
+        """cl_analyze_ragged_ex (or its host half) over shapes = [(Ns, Nt,
+        count), ...]: the site-indexed arrays of every lattice concatenated in
+        shape order."""
+        n = len(shapes)
+        arr = lambda k: (ctypes.c_int * n)(*[int(sh[k]) for sh in shapes])
+        h = ctypes.c_void_p()
+        fn = load().cl_analyze_ragged_symbolic if symbolic else load().cl_analyze_ragged_ex
+        _check(fn(n, arr(0), arr(1), arr(2), precision, panel, ctypes.byref(h)), "cl_analyze_ragged")
+        plan = cls(h, symbolic)
+        plan.shapes = [tuple(int(x) for x in sh) for sh in shapes]
+        return plan
 
     @classmethod
     def analyze_symbolic(cls, Ns: int, Nt: int, precision: int = CL_FP64, panel: int = 0) -> "Plan":
@@ -364,8 +385,12 @@ class Plan:
 
     # -- convenience: allocate outputs and run one evaluation --------------
     def alloc_outputs(self):
+        """Output arrays of a drift evaluation: [batch][V]... for one shape, one
+        [sites of all lattices]... row (leading dimension 1) for a ragged plan."""
         import torch
         B, V = self.info["batch"], self.info["V"]
+        if self.info["n_shapes"] > 1 or getattr(self, "shapes", None):
+            B = 1  # ragged: V counts the sites of all lattices
         kw = dict(dtype=torch.complex128, device="cuda")
         return dict(Gdiag=torch.empty((B, V, 3, 3), **kw), Gfwd=torch.empty((B, V, 4, 3, 3), **kw),
                     Gbwd=torch.empty((B, V, 4, 3, 3), **kw), Kf=torch.empty((B, V, 4, 8), **kw))

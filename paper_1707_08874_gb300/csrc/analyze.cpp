@@ -131,32 +131,48 @@ int64_t tiles(int M, int N) {
   return (int64_t)((M + kTileM - 1) / kTileM) * ((N + kTileN - 1) / kTileN);
 }
 
-}  // namespace
-
-void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) {
+void check_shape(int Ns, int Nt) {
   if (Ns < 4 || Nt < 4 || (Ns & 1) || (Nt & 1)) throw std::invalid_argument("Ns, Nt must be even and >= 4");
   if (Ns > 64 || Nt > 128) throw std::invalid_argument("lattice too large");
+}
+
+int check_precision_panel(int precision, int panel) {
   if (precision != CL_FP64 && precision != CL_MIXED_FP32 && precision != CL_FP64_EMU &&
       precision != CL_MIXED_BF16X3)
     throw std::invalid_argument("precision");
-  p.Ns = Ns;
-  p.Nt = Nt;
-  p.V = Ns * Ns * Ns * Nt;
-  p.N = 3 * p.V;
-  p.batch = batch;
-  p.precision = precision;
   if (panel != 0 && (panel < 3 || panel > 48 || panel % 3 != 0)) throw std::invalid_argument("panel");
-  p.panel = panel ? panel
-                  : (precision == CL_FP64 ? kPanelFP64 : digit_gemms(precision) ? kPanelEmu : kPanelFP32);
+  return panel ? panel : (precision == CL_FP64 ? kPanelFP64 : digit_gemms(precision) ? kPanelEmu : kPanelFP32);
+}
+
+// Everything of the analysis that depends on one lattice shape: the
+// supernodal elimination tree (postorder), front offsets inside the shape's
+// own pool, the block tables of D and G, the extend-add and gather site maps
+// (SNode::ea_map / ga_map index `maps`) and the flop counts at panel width b.
+struct Tree {
+  int Ns = 0, Nt = 0, V = 0;
+  std::vector<SNode> nodes;
+  int n_levels = 0;
+  int64_t pool_elems = 0;
+  double factor_flops = 0, selinv_flops = 0;
+  std::vector<int64_t> off;  // diagonal [V] | forward [4V] | backward [4V]
+  std::vector<int> ld;
+  std::vector<int> maps;
+};
+
+void build_tree(Tree& t, int Ns, int Nt, int b) {
+  check_shape(Ns, Nt);
+  t.Ns = Ns;
+  t.Nt = Nt;
+  t.V = Ns * Ns * Ns * Nt;
   Geo g{Ns, Nt, {Ns, Ns, Ns, Nt}};
-  const int V = p.V;
+  const int V = t.V;
 
   // ---- elimination tree -------------------------------------------------
   std::vector<Box> boxes;
   Box whole{{0, 0, 0, 0}, {Ns, Ns, Ns, Nt}, {true, true, true, true}};
-  p.nodes.clear();
-  dissect(g, whole, p.nodes, boxes);
-  auto& nodes = p.nodes;
+  t.nodes.clear();
+  dissect(g, whole, t.nodes, boxes);
+  auto& nodes = t.nodes;
   const int nn = (int)nodes.size();
   std::vector<int> sn(V, -1);
   for (int i = 0; i < nn; ++i)
@@ -175,25 +191,25 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     front.insert(front.end(), P.bnd.begin(), P.bnd.end());
     for (size_t q = 0; q < front.size(); ++q) pos[front[q]] = (int)q;
     for (int c : P.children) {
-      std::vector<int> b;
+      std::vector<int> bb;
       for (int s : g.sites(boxes[c]))
         for (int nu = 0; nu < 4; ++nu)
           for (int dir = -1; dir <= 1; dir += 2) {
             int y = g.nbr(s, nu, dir);
-            if (!g.in_box(boxes[c], y)) b.push_back(y);
+            if (!g.in_box(boxes[c], y)) bb.push_back(y);
           }
-      std::sort(b.begin(), b.end());
-      b.erase(std::unique(b.begin(), b.end()), b.end());
-      for (int s : b)
+      std::sort(bb.begin(), bb.end());
+      bb.erase(std::unique(bb.begin(), bb.end()), bb.end());
+      for (int s : bb)
         if (pos[s] < 0) throw std::logic_error("boundary outside the parent front");
-      std::sort(b.begin(), b.end(), [&](int a, int c2) { return pos[a] < pos[c2]; });
-      nodes[c].bnd = b;
+      std::sort(bb.begin(), bb.end(), [&](int a, int c2) { return pos[a] < pos[c2]; });
+      nodes[c].bnd = bb;
     }
     for (int s : front) pos[s] = -1;
   }
 
   // ---- sizes, levels, front offsets ---------------------------------------
-  p.n_levels = 0;
+  t.n_levels = 0;
   int64_t off = 0;
   for (int i = 0; i < nn; ++i) {
     SNode& n = nodes[i];
@@ -202,35 +218,21 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     n.nf = n.k + n.r;
     n.level = 0;
     for (int c : n.children) n.level = std::max(n.level, nodes[c].level + 1);
-    p.n_levels = std::max(p.n_levels, n.level + 1);
+    t.n_levels = std::max(t.n_levels, n.level + 1);
     n.off = off;
     off += ((int64_t)n.nf * n.nf + 15) / 16 * 16;
   }
-  p.pool_elems = off;
-
-  // per-node workspace inside its level (panel temps / selected-inversion temps)
-  const int b = p.panel;
-  std::vector<int64_t> level_tmp(p.n_levels, 0);
-  for (int i = 0; i < nn; ++i) {
-    SNode& n = nodes[i];
-    int64_t need = std::max<int64_t>(4LL * b * n.nf, 2LL * n.r * n.k);  // two TR/TC sets (look-ahead)
-    need = (need + 15) / 16 * 16;
-    n.tmp = p.pool_elems + level_tmp[n.level];
-    level_tmp[n.level] += need;
-  }
-  p.tmp_elems = 0;
-  for (auto t : level_tmp) p.tmp_elems = std::max(p.tmp_elems, t);
-  p.arena_elems = (p.pool_elems + p.tmp_elems + 63) / 64 * 64;
+  t.pool_elems = off;
 
   // ---- flop counts (complex multiply-add = 8 real flops) ------------------
-  p.factor_flops = p.selinv_flops = 0;
+  t.factor_flops = t.selinv_flops = 0;
   for (auto& n : nodes) {
     for (int c0 = 0; c0 < n.k; c0 += b) {
       double bp = std::min(b, n.k - c0), nf = n.nf;
-      p.factor_flops += 8.0 * (bp * bp * bp + 2 * nf * bp * bp + nf * nf * bp);
+      t.factor_flops += 8.0 * (bp * bp * bp + 2 * nf * bp * bp + nf * nf * bp);
     }
     double k = n.k, r = n.r;
-    p.selinv_flops += 8.0 * (2 * r * r * k + k * k * r);
+    t.selinv_flops += 8.0 * (2 * r * r * k + k * k * r);
   }
 
   // ---- assembly / extraction tables -----------------------------------------
@@ -252,26 +254,96 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     if (it == v.end() || it->first != s) throw std::logic_error("site not in front");
     return (int)nodes[node].sep.size() + it->second;
   };
-  auto block_off = [&](int x, int y, int64_t& o, int& ld) {
+  auto block_off = [&](int x, int y, int64_t& o, int& l) {
     int node = std::min(sn[x], sn[y]);  // the supernode eliminated first (postorder)
     const SNode& n = nodes[node];
     o = n.off + (int64_t)3 * front_pos(node, x) * n.nf + 3 * front_pos(node, y);
-    ld = n.nf;
+    l = n.nf;
   };
-  p.off_diag.assign(V, 0);
-  p.ld_diag.assign(V, 0);
-  p.off_fwd.assign(4 * V, 0);
-  p.ld_fwd.assign(4 * V, 0);
-  p.off_bwd.assign(4 * V, 0);
-  p.ld_bwd.assign(4 * V, 0);
+  t.off.assign(9 * (size_t)V, 0);
+  t.ld.assign(9 * (size_t)V, 0);
   for (int s = 0; s < V; ++s) {
-    block_off(s, s, p.off_diag[s], p.ld_diag[s]);
+    block_off(s, s, t.off[s], t.ld[s]);
     for (int nu = 0; nu < 4; ++nu) {
       int y = g.nbr(s, nu, +1);
-      block_off(s, y, p.off_fwd[4 * s + nu], p.ld_fwd[4 * s + nu]);
-      block_off(y, s, p.off_bwd[4 * s + nu], p.ld_bwd[4 * s + nu]);
+      block_off(s, y, t.off[V + 4 * s + nu], t.ld[V + 4 * s + nu]);
+      block_off(y, s, t.off[5 * V + 4 * s + nu], t.ld[5 * V + 4 * s + nu]);
     }
   }
+
+  // ---- site maps of the extend-add (parent front site -> child boundary
+  // index or -1) and of the selected-inversion gather (child boundary index
+  // -> parent front site) ---------------------------------------------------
+  t.maps.clear();
+  for (int i = 0; i < nn; ++i) {
+    SNode& P = nodes[i];
+    if (P.children.size() > 2) throw std::logic_error("more than two children");
+    const size_t nfs = P.sep.size() + P.bnd.size();
+    for (size_t q = 0; q < P.children.size(); ++q) {
+      const SNode& C = nodes[P.children[q]];
+      P.ea_map[q] = (int)t.maps.size();
+      std::vector<int> inv(nfs, -1);
+      for (size_t j = 0; j < C.bnd.size(); ++j) inv[front_pos(i, C.bnd[j])] = (int)j;
+      t.maps.insert(t.maps.end(), inv.begin(), inv.end());
+    }
+  }
+  for (int i = 0; i < nn; ++i) {
+    SNode& C = nodes[i];
+    if (C.parent < 0 || C.r == 0) continue;
+    C.ga_map = (int)t.maps.size();
+    for (int s : C.bnd) t.maps.push_back(front_pos(C.parent, s));
+  }
+}
+
+// A front of the merged schedule: one supernode of one lattice, at its
+// offset in the arena (fronts of every lattice of a ragged plan side by side).
+struct FNode {
+  int64_t off = 0, tmp = 0;
+  int nf = 0, k = 0, r = 0, level = 0;
+  int nchild = 0;
+  int child[2] = {-1, -1};
+  int ea_map[2] = {-1, -1};
+  int ga_map = -1;
+};
+
+FNode fnode_of(const SNode& n, int64_t base, int index_base, int maps_base) {
+  FNode f;
+  f.off = base + n.off;
+  f.nf = n.nf;
+  f.k = n.k;
+  f.r = n.r;
+  f.level = n.level;
+  f.nchild = (int)n.children.size();
+  for (int q = 0; q < f.nchild; ++q) {
+    f.child[q] = index_base + n.children[q];
+    f.ea_map[q] = maps_base + n.ea_map[q];
+  }
+  f.ga_map = n.ga_map >= 0 ? maps_base + n.ga_map : -1;
+  return f;
+}
+
+// The fixed launch schedule of the factorisation and the selected-inversion
+// sweep over the fronts F (by level: every front of a level, of every lattice,
+// in the same launches), the workspace layout after p.pool_elems and the
+// digit workspace of the tensor-core GEMMs.  p.panel, p.pool_elems and p.maps
+// are set by the caller.
+void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision) {
+  const int nn = (int)F.size();
+  const int b = p.panel;
+  p.n_levels = n_levels;
+
+  // per-node workspace inside its level (panel temps / selected-inversion temps)
+  std::vector<int64_t> level_tmp(n_levels, 0);
+  for (int i = 0; i < nn; ++i) {
+    FNode& n = F[i];
+    int64_t need = std::max<int64_t>(4LL * b * n.nf, 2LL * n.r * n.k);  // two TR/TC sets (look-ahead)
+    need = (need + 15) / 16 * 16;
+    n.tmp = p.pool_elems + level_tmp[n.level];
+    level_tmp[n.level] += need;
+  }
+  p.tmp_elems = 0;
+  for (auto t : level_tmp) p.tmp_elems = std::max(p.tmp_elems, t);
+  p.arena_elems = (p.pool_elems + p.tmp_elems + 63) / 64 * 64;
 
   // ---- schedule ----------------------------------------------------------
   p.gemm.clear();
@@ -279,11 +351,10 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   p.copies.clear();
   p.extadd.clear();
   p.gather.clear();
-  p.maps.clear();
   p.factor_ops.clear();
   p.selinv_ops.clear();
-  std::vector<std::vector<int>> by_level(p.n_levels);
-  for (int i = 0; i < nn; ++i) by_level[nodes[i].level].push_back(i);
+  std::vector<std::vector<int>> by_level(n_levels);
+  for (int i = 0; i < nn; ++i) by_level[F[i].level].push_back(i);
 
   const Mask2 none{0, 0, 0, 0};
   auto add_gemm = [&](int blk, int64_t a, int lda, int64_t bb, int ldb, int64_t c, int ldc, int M, int N,
@@ -319,32 +390,29 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   };
 
   p.factor_ops.push_back(Op{OP_ZERO, 0, 0, 0, -1});
-  p.factor_ops.push_back(Op{OP_ASSEMBLE, 0, 0, (4 * V + 127) / 128, -1});
-  std::vector<int> level_last_copy(p.n_levels, -1);
-  for (int h = 0; h < p.n_levels; ++h) {
+  int assemble_blocks = 0;
+  for (const Segment& sg : p.segs) assemble_blocks = std::max(assemble_blocks, (4 * sg.V + 127) / 128);
+  p.factor_ops.push_back(Op{OP_ASSEMBLE, 0, 0, assemble_blocks, -1});
+  std::vector<int> level_last_copy(n_levels, -1);
+  for (int h = 0; h < n_levels; ++h) {
     const auto& lv = by_level[h];
     if (h > 0) {
       Op op{OP_EXTADD, (int)p.extadd.size(), 0, 0, h};
       op.wait = level_last_copy[h - 1];  // the children's Schur complements are complete
       int blk = 0;
       for (int i : lv) {
-        const SNode& P = nodes[i];
-        if (P.children.empty()) continue;
+        const FNode& P = F[i];
+        if (P.nchild == 0) continue;
         ExtAddDesc d{};
         d.parent = P.off;
         d.nfp = P.nf;
-        d.nchild = (int)P.children.size();
-        if (d.nchild > 2) throw std::logic_error("more than two children");
-        std::vector<int> front(P.sep.size() + P.bnd.size());
+        d.nchild = P.nchild;
         for (int q = 0; q < d.nchild; ++q) {
-          const SNode& C = nodes[P.children[q]];
+          const FNode& C = F[P.child[q]];
           d.child[q] = C.off;
           d.nfc[q] = C.nf;
           d.kc[q] = C.k;
-          d.map[q] = (int)p.maps.size();
-          std::vector<int> inv(front.size(), -1);
-          for (size_t j = 0; j < C.bnd.size(); ++j) inv[front_pos(i, C.bnd[j])] = (int)j;
-          p.maps.insert(p.maps.end(), inv.begin(), inv.end());
+          d.map[q] = P.ea_map[q];
         }
         d.blk0 = blk;
         blk += (int)(((int64_t)P.nf * P.nf + 255) / 256);
@@ -361,18 +429,18 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     // rest of the front and the write-back of the panel.  TR/TC alternate
     // between two workspace sets by panel parity.
     int maxk = 0;
-    for (int i : lv) maxk = std::max(maxk, nodes[i].k);
+    for (int i : lv) maxk = std::max(maxk, F[i].k);
     int last_copy = -1;  // op index of the previous step's stream-1 write-back
     for (int c0 = 0, step = 0; c0 < maxk; c0 += b, ++step) {
       const int set = step & 1;
-      auto tR_of = [&](const SNode& n) { return n.tmp + (int64_t)set * 2 * b * n.nf; };
-      auto tC_of = [&](const SNode& n) { return tR_of(n) + (int64_t)b * n.nf; };
+      auto tR_of = [&](const FNode& n) { return n.tmp + (int64_t)set * 2 * b * n.nf; };
+      auto tC_of = [&](const FNode& n) { return tR_of(n) + (int64_t)b * n.nf; };
       Op pinv{OP_PANEL, (int)p.panels.size(), 0, 0, h};
       Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
       g1.ndig = nd_panel;
       int blk1 = 0;
       for (int i : lv) {
-        const SNode& n = nodes[i];
+        const FNode& n = F[i];
         if (c0 >= n.k) continue;
         const int bp = std::min(b, n.k - c0);
         p.panels.push_back(PanelDesc{n.off + (int64_t)c0 * n.nf + c0, n.nf, bp, i, c0});
@@ -402,7 +470,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       Op ec{OP_COPY, (int)p.copies.size(), 0, 0, h};
       int blks = 0, blke = 0;
       for (int i : lv) {
-        const SNode& n = nodes[i];
+        const FNode& n = F[i];
         if (c0 >= n.k) continue;
         const int bp = std::min(b, n.k - c0), c1 = c0 + b;
         if (n.nf == bp || c1 >= n.k) continue;
@@ -440,7 +508,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
       Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
       int blk2 = 0, blk3 = 0;
       for (int i : lv) {
-        const SNode& n = nodes[i];
+        const FNode& n = F[i];
         if (c0 >= n.k) continue;
         const int bp = std::min(b, n.k - c0), c1 = c0 + b;
         if (n.nf == bp) continue;
@@ -469,16 +537,18 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   }
 
   // selected inversion: root to leaves
-  for (int h = p.n_levels - 1; h >= 0; --h) {
+  std::vector<int> parent(nn, -1);
+  for (int i = 0; i < nn; ++i)
+    for (int q = 0; q < F[i].nchild; ++q) parent[F[i].child[q]] = i;
+  for (int h = n_levels - 1; h >= 0; --h) {
     const auto& lv = by_level[h];
     Op ga{OP_GATHER, (int)p.gather.size(), 0, 0, h};
     int blk = 0;
     for (int i : lv) {
-      const SNode& C = nodes[i];
-      if (C.parent < 0 || C.r == 0) continue;
-      const SNode& P = nodes[C.parent];
-      GatherDesc d{C.off, P.off, C.nf, C.k, P.nf, (int)C.bnd.size(), (int)p.maps.size(), blk};
-      for (int s : C.bnd) p.maps.push_back(front_pos(C.parent, s));
+      const FNode& C = F[i];
+      if (parent[i] < 0 || C.r == 0) continue;
+      const FNode& P = F[parent[i]];
+      GatherDesc d{C.off, P.off, C.nf, C.k, P.nf, C.r / 3, C.ga_map, blk};
       blk += (int)(((int64_t)C.r * C.r + 255) / 256);
       p.gather.push_back(d);
     }
@@ -490,7 +560,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     g1.ndig = nd_offdiag;
     int blk1 = 0;
     for (int i : lv) {
-      const SNode& n = nodes[i];
+      const FNode& n = F[i];
       if (n.r == 0) continue;
       int64_t tSJ = n.tmp, tJS = n.tmp + (int64_t)n.r * n.k;
       int64_t SS = n.off + (int64_t)n.k * n.nf + n.k, SJ = n.off + (int64_t)n.k * n.nf, JS = n.off + n.k;
@@ -505,7 +575,7 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     Op cp{OP_COPY, (int)p.copies.size(), 0, 0, h};
     int blk2 = 0, blk3 = 0;
     for (int i : lv) {
-      const SNode& n = nodes[i];
+      const FNode& n = F[i];
       if (n.r == 0) continue;
       int64_t tSJ = n.tmp, tJS = n.tmp + (int64_t)n.r * n.k;
       int64_t SJ = n.off + (int64_t)n.k * n.nf, JS = n.off + n.k;
@@ -521,9 +591,9 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     p.selinv_ops.push_back(g2);
     p.selinv_ops.push_back(cp);
   }
-  p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, (4 * V + 127) / 128, -1});
+  p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, assemble_blocks, -1});
 
-  // split-digit workspace of the FP64 emulation: per GEMM launch the problems
+  // split-digit workspace of the digit GEMMs: per GEMM launch the problems
   // are laid out one after the other from the start of that launch's stream
   // region (launches of one stream run in order; the factorisation's second
   // stream gets a region of its own after the first one's)
@@ -578,6 +648,105 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
     p.emu_words = max_w[0] + max_w[1];
     p.emu_ints = max_in[0] + max_in[1];
   }
+}
+
+}  // namespace
+
+void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) {
+  check_shape(Ns, Nt);
+  p.panel = check_precision_panel(precision, panel);
+  p.precision = precision;
+  Tree t;
+  build_tree(t, Ns, Nt, p.panel);
+  p.Ns = Ns;
+  p.Nt = Nt;
+  p.V = t.V;
+  p.N = 3 * t.V;
+  p.batch = batch;
+  p.fbatch = batch;
+  p.ragged = false;
+  p.nodes = t.nodes;
+  p.pool_elems = t.pool_elems;
+  p.factor_flops = t.factor_flops;
+  p.selinv_flops = t.selinv_flops;
+  const int V = t.V;
+  p.off_diag.assign(t.off.begin(), t.off.begin() + V);
+  p.off_fwd.assign(t.off.begin() + V, t.off.begin() + 5 * V);
+  p.off_bwd.assign(t.off.begin() + 5 * V, t.off.end());
+  p.ld_diag.assign(t.ld.begin(), t.ld.begin() + V);
+  p.ld_fwd.assign(t.ld.begin() + V, t.ld.begin() + 5 * V);
+  p.ld_bwd.assign(t.ld.begin() + 5 * V, t.ld.end());
+  p.off_all = t.off;
+  p.ld_all = t.ld;
+  p.maps = t.maps;
+  p.segs.assign(1, Segment{Ns, Nt, V, batch, 0, 0, 0, 0});
+  std::vector<FNode> F;
+  F.reserve(t.nodes.size());
+  for (const SNode& n : t.nodes) F.push_back(fnode_of(n, 0, 0, 0));
+  build_schedule(p, F, t.n_levels, precision);
+  for (size_t i = 0; i < F.size(); ++i) p.nodes[i].tmp = F[i].tmp;
+  p.segs[0].rep_stride = p.arena_elems;  // each replica: its own fronts and workspace (grid.y)
+}
+
+void analyze_ragged(Plan& p, int nshapes, const int* Ns, const int* Nt, const int* count, int precision,
+                    int panel) {
+  if (nshapes < 1 || !Ns || !Nt || !count) throw std::invalid_argument("shapes");
+  int64_t lattices = 0, sites = 0;
+  for (int s = 0; s < nshapes; ++s) {
+    check_shape(Ns[s], Nt[s]);
+    if (count[s] < 1) throw std::invalid_argument("count");
+    lattices += count[s];
+    sites += (int64_t)count[s] * Ns[s] * Ns[s] * Ns[s] * Nt[s];
+  }
+  if (lattices > 65535 || sites * 3 > (1LL << 31) - 1) throw std::invalid_argument("too many lattices");
+  p.panel = check_precision_panel(precision, panel);
+  p.precision = precision;
+  p.ragged = true;
+  p.fbatch = 1;
+  p.batch = (int)lattices;
+  p.V = (int)sites;
+  p.N = 3 * p.V;
+  p.Ns = p.Nt = 0;
+  p.nodes.clear();
+  p.maps.clear();
+  p.off_all.clear();
+  p.ld_all.clear();
+  p.off_diag.clear();
+  p.off_fwd.clear();
+  p.off_bwd.clear();
+  p.ld_diag.clear();
+  p.ld_fwd.clear();
+  p.ld_bwd.clear();
+  p.segs.clear();
+  p.factor_flops = p.selinv_flops = 0;
+  std::vector<FNode> F;
+  int n_levels = 0;
+  int64_t base = 0, table_base = 0, site_base = 0;
+  for (int s = 0; s < nshapes; ++s) {
+    Tree t;
+    build_tree(t, Ns[s], Nt[s], p.panel);
+    const int maps_base = (int)p.maps.size();
+    p.maps.insert(p.maps.end(), t.maps.begin(), t.maps.end());
+    p.off_all.insert(p.off_all.end(), t.off.begin(), t.off.end());
+    p.ld_all.insert(p.ld_all.end(), t.ld.begin(), t.ld.end());
+    p.segs.push_back(Segment{Ns[s], Nt[s], t.V, count[s], base, t.pool_elems, table_base, site_base});
+    for (int r = 0; r < count[s]; ++r) {
+      const int index_base = (int)F.size();
+      for (const SNode& n : t.nodes) F.push_back(fnode_of(n, base, index_base, maps_base));
+      base += t.pool_elems;
+    }
+    p.nodes.insert(p.nodes.end(), t.nodes.begin(), t.nodes.end());
+    n_levels = std::max(n_levels, t.n_levels);
+    table_base += 9LL * t.V;
+    site_base += (int64_t)count[s] * t.V;
+    p.factor_flops += count[s] * t.factor_flops;
+    p.selinv_flops += count[s] * t.selinv_flops;
+  }
+  // flops per lattice (averaged), so that info.batch x flops is the plan's work
+  p.factor_flops /= (double)lattices;
+  p.selinv_flops /= (double)lattices;
+  p.pool_elems = base;
+  build_schedule(p, F, n_levels, precision);
 }
 
 }  // namespace cl

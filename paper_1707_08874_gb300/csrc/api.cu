@@ -73,21 +73,13 @@ int setup_device(Plan& p) {
   size_t total = 0;
   cudaError_t e;
   if ((e = cl::panel_prepare()) != cudaSuccess) return cuda_status(e);
-  const size_t arena = (size_t)p.arena_elems * p.batch * elem_bytes(p);
+  const size_t arena = (size_t)p.arena_elems * p.fbatch * elem_bytes(p);
   if ((e = cudaMalloc(&p.d_arena, arena)) != cudaSuccess) return cuda_status(e);
   total += arena;
   p.has_device = true;
-  std::vector<int64_t> off;
-  off.insert(off.end(), p.off_diag.begin(), p.off_diag.end());
-  off.insert(off.end(), p.off_fwd.begin(), p.off_fwd.end());
-  off.insert(off.end(), p.off_bwd.begin(), p.off_bwd.end());
-  std::vector<int> ld;
-  ld.insert(ld.end(), p.ld_diag.begin(), p.ld_diag.end());
-  ld.insert(ld.end(), p.ld_fwd.begin(), p.ld_fwd.end());
-  ld.insert(ld.end(), p.ld_bwd.begin(), p.ld_bwd.end());
   if ((e = upload(p.d_status, nullptr, 4 * sizeof(int), total)) != cudaSuccess ||
-      (e = upload(p.d_off, off.data(), off.size() * sizeof(int64_t), total)) != cudaSuccess ||
-      (e = upload(p.d_ld, ld.data(), ld.size() * sizeof(int), total)) != cudaSuccess ||
+      (e = upload(p.d_off, p.off_all.data(), p.off_all.size() * sizeof(int64_t), total)) != cudaSuccess ||
+      (e = upload(p.d_ld, p.ld_all.data(), p.ld_all.size() * sizeof(int), total)) != cudaSuccess ||
       (e = upload(p.d_maps, p.maps.data(), p.maps.size() * sizeof(int), total)) != cudaSuccess ||
       (e = upload(p.d_gemm, p.gemm.data(), p.gemm.size() * sizeof(cl::GemmDesc), total)) != cudaSuccess ||
       (e = upload(p.d_panels, p.panels.data(), p.panels.size() * sizeof(cl::PanelDesc), total)) != cudaSuccess ||
@@ -95,7 +87,8 @@ int setup_device(Plan& p) {
       (e = upload(p.d_extadd, p.extadd.data(), p.extadd.size() * sizeof(cl::ExtAddDesc), total)) != cudaSuccess ||
       (e = upload(p.d_gather, p.gather.data(), p.gather.size() * sizeof(cl::GatherDesc), total)) != cudaSuccess)
     return cuda_status(e);
-  const size_t B = p.batch, V = p.V;
+  // Langevin-step buffers (single-shape plans; a ragged plan evaluates drifts only)
+  const size_t B = p.ragged ? 0 : p.batch, V = p.V;
   if ((e = upload(p.d_Gdiag, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
       (e = upload(p.d_Gfwd, nullptr, B * V * 72 * sizeof(double), total)) != cudaSuccess ||
       (e = upload(p.d_Gbwd, nullptr, B * V * 72 * sizeof(double), total)) != cudaSuccess ||
@@ -104,7 +97,8 @@ int setup_device(Plan& p) {
       (e = upload(p.d_F, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
       (e = upload(p.d_Om, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
       (e = upload(p.d_Omi, nullptr, B * V * 18 * sizeof(double), total)) != cudaSuccess ||
-      (e = upload(p.d_part, nullptr, B * cl::obs_partial_doubles(p) * sizeof(double), total)) != cudaSuccess ||
+      (e = upload(p.d_part, nullptr, B ? B * cl::obs_partial_doubles(p) * sizeof(double) : 0, total)) !=
+          cudaSuccess ||
       (e = upload(p.d_slots, nullptr, B * 4 * sizeof(unsigned long long), total)) != cudaSuccess)
     return cuda_status(e);
   // streams and events of the two-stream factorisation
@@ -136,8 +130,9 @@ int setup_device(Plan& p) {
   if (cl::digit_gemms(p.precision)) {
     if ((e = cl::emu_prepare()) != cudaSuccess) return cuda_status(e);
     if ((e = upload(p.d_emu, p.emu.data(), p.emu.size() * sizeof(cl::EmuDesc), total)) != cudaSuccess ||
-        (e = upload(p.d_emu_words, nullptr, B * p.emu_words * sizeof(unsigned), total)) != cudaSuccess ||
-        (e = upload(p.d_emu_ints, nullptr, B * p.emu_ints * sizeof(int), total)) != cudaSuccess)
+        (e = upload(p.d_emu_words, nullptr, (size_t)p.fbatch * p.emu_words * sizeof(unsigned), total)) !=
+            cudaSuccess ||
+        (e = upload(p.d_emu_ints, nullptr, (size_t)p.fbatch * p.emu_ints * sizeof(int), total)) != cudaSuccess)
       return cuda_status(e);
   }
   p.device_bytes = total;
@@ -153,11 +148,13 @@ const char* kFamilyName[cl::F_COUNT] = {"zero",  "assemble", "extend_add", "pane
 // products (8 real flops per complex multiply-add) and bytes that must cross
 // DRAM (reads + writes of the data the op touches once)
 void op_work(const Plan& p, const cl::Op& op, int& family, double& flops, double& bytes) {
-  const double es = p.precision == CL_MIXED_FP32 ? 8.0 : 16.0, B = p.batch;
+  // B: replicas sharing each descriptor (grid.y); sites: of every lattice
+  const double es = p.precision == CL_MIXED_FP32 ? 8.0 : 16.0, B = p.fbatch;
+  const double sites = p.ragged ? p.V : (double)p.V * p.batch;
   flops = bytes = 0;
   switch (op.kind) {
     case cl::OP_ZERO: family = cl::F_ZERO; bytes = es * p.pool_elems * B; break;
-    case cl::OP_ASSEMBLE: family = cl::F_ASSEMBLE; bytes = B * p.V * (4 * 144.0 + (8 * 9 + 9) * es); break;
+    case cl::OP_ASSEMBLE: family = cl::F_ASSEMBLE; bytes = sites * (4 * 144.0 + (8 * 9 + 9) * es); break;
     case cl::OP_EXTADD:
       family = cl::F_EXTADD;
       for (int d = op.d0; d < op.d1; ++d) bytes += 3.0 * es * p.extadd[d].nfp * p.extadd[d].nfp * B;
@@ -186,7 +183,7 @@ void op_work(const Plan& p, const cl::Op& op, int& family, double& flops, double
       family = cl::F_GATHER;
       for (int d = op.d0; d < op.d1; ++d) bytes += 2.0 * es * 9.0 * p.gather[d].rs * p.gather[d].rs * B;
       break;
-    case cl::OP_EXTRACT: family = cl::F_EXTRACT; bytes = B * p.V * 9 * 9 * (es + 16.0); break;
+    case cl::OP_EXTRACT: family = cl::F_EXTRACT; bytes = sites * 9 * 9 * (es + 16.0); break;
   }
 }
 
@@ -308,9 +305,54 @@ int make_plan(int Ns, int Nt, int batch, int precision, int panel, cl_plan** out
   return CL_OK;
 }
 
+int make_ragged(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, int panel,
+                cl_plan** out, bool device = true) {
+  if (!out) return CL_ERR_INVALID_ARG;
+  *out = nullptr;
+  cl_plan* plan = new (std::nothrow) cl_plan();
+  if (!plan) return CL_ERR_OOM;
+  try {
+    cl::analyze_ragged(plan->p, nshapes, Ns, Nt, count, precision, panel);
+  } catch (const std::invalid_argument&) {
+    delete plan;
+    return CL_ERR_INVALID_ARG;
+  } catch (const std::bad_alloc&) {
+    delete plan;
+    return CL_ERR_OOM;
+  } catch (...) {
+    delete plan;
+    return CL_ERR_UNSUPPORTED;
+  }
+  int st = device ? setup_device(plan->p) : CL_OK;
+  if (st != CL_OK) {
+    free_device(plan->p);
+    delete plan;
+    return st;
+  }
+  *out = plan;
+  return CL_OK;
+}
+
+// the Langevin pieces need one lattice shape (a ragged plan evaluates drifts)
+bool langevin_ready(const cl_plan* plan) { return compute_ready(plan) && !plan->p.ragged; }
+
 }  // namespace
 
 extern "C" {
+
+int cl_analyze_ragged(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, cl_plan** plan) {
+  return make_ragged(nshapes, Ns, Nt, count, precision, 0, plan);
+}
+
+int cl_analyze_ragged_ex(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, int panel,
+                         cl_plan** plan) {
+  return make_ragged(nshapes, Ns, Nt, count, precision, panel, plan);
+}
+
+int cl_analyze_ragged_symbolic(int nshapes, const int* Ns, const int* Nt, const int* count, int precision, int panel,
+                               cl_plan** plan) {
+  return make_ragged(nshapes, Ns, Nt, count, precision, panel, plan, false);
+}
 
 int cl_analyze(int Ns, int Nt, int batch, int precision, cl_plan** plan) {
   return make_plan(Ns, Nt, batch, precision, 0, plan, true);
@@ -345,7 +387,8 @@ int cl_fermion_drift(cl_plan* plan, const double* links, const double* Gfwd, con
   cudaEvent_t e0;
   prof_begin(p, stream, e0);
   int st = cuda_status(cl::launch_drift(p, links, Gfwd, Gbwd, mu, nf, Kf, stream));
-  prof_end(p, stream, e0, cl::F_DRIFT, 0.0, (double)p.batch * p.V * 4 * (3 * 144.0 + 128.0));
+  const double sites = p.ragged ? p.V : (double)p.V * p.batch;
+  prof_end(p, stream, e0, cl::F_DRIFT, 0.0, sites * 4 * (3 * 144.0 + 128.0));
   return st;
 }
 
@@ -360,11 +403,13 @@ int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, doubl
 
 int cl_gauge_drift(cl_plan* plan, const double* links, double beta, double* Kg, cudaStream_t stream) {
   if (!compute_ready(plan) || !links || !Kg) return CL_ERR_INVALID_ARG;
+  if (!langevin_ready(plan)) return CL_ERR_UNSUPPORTED;
   return cuda_status(cl::launch_gauge_drift(plan->p, links, plan->p.d_Ui, beta, Kg, 0, stream));
 }
 
 int cl_gauge_cool(cl_plan* plan, double* links, int n_cool, double alpha0, cudaStream_t stream) {
   if (!compute_ready(plan) || !links || n_cool < 0) return CL_ERR_INVALID_ARG;
+  if (!langevin_ready(plan)) return CL_ERR_UNSUPPORTED;
   Plan& p = plan->p;
   return cuda_status(cl::launch_cool(p, links, n_cool, alpha0, p.d_F, p.d_Om, p.d_Omi, p.d_slots, stream));
 }
@@ -372,6 +417,7 @@ int cl_gauge_cool(cl_plan* plan, double* links, int n_cool, double alpha0, cudaS
 int cl_link_update(cl_plan* plan, double* links, const double* K, double eps, unsigned long long seed, long long step,
                    cudaStream_t stream) {
   if (!compute_ready(plan) || !links || !K || !(eps > 0)) return CL_ERR_INVALID_ARG;
+  if (!langevin_ready(plan)) return CL_ERR_UNSUPPORTED;
   cl::LangevinArgs a{eps, 0.0, eps, seed, step};
   return cuda_status(cl::launch_update(plan->p, links, K, a, plan->p.d_slots, nullptr, stream));
 }
@@ -379,6 +425,7 @@ int cl_link_update(cl_plan* plan, double* links, const double* K, double eps, un
 int cl_observables(cl_plan* plan, const double* links, const double* Gdiag, const double* Gfwd, const double* Gbwd,
                    double mu, double nf, double* obs, cudaStream_t stream) {
   if (!compute_ready(plan) || !links || !obs) return CL_ERR_INVALID_ARG;
+  if (!langevin_ready(plan)) return CL_ERR_UNSUPPORTED;
   Plan& p = plan->p;
   cl::LangevinArgs a{0.0, 0.0, 0.0, 0ull, 0};
   cudaError_t e = cl::launch_obs_partial(p, links, p.d_Ui, Gdiag, Gfwd, Gbwd, mu, p.d_part, true, stream);
@@ -391,6 +438,7 @@ int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm
                      cudaStream_t stream) {
   if (!compute_ready(plan) || !links || !prm || !state || !obs) return CL_ERR_INVALID_ARG;
   if (!(prm->eps_max > 0) || prm->n_cool < 0) return CL_ERR_INVALID_ARG;
+  if (!langevin_ready(plan)) return CL_ERR_UNSUPPORTED;
   Plan& p = plan->p;
   int st = CL_OK;
   const bool ferm = prm->fermions != 0;
@@ -458,15 +506,19 @@ int cl_plan_get_info(const cl_plan* plan, cl_plan_info* info) {
   info->panel = p.panel;
   info->factor_flops = p.factor_flops;
   info->selinv_flops = p.selinv_flops;
-  info->front_bytes = (double)p.pool_elems * p.batch * elem_bytes(p);
+  info->front_bytes = (double)p.pool_elems * p.fbatch * elem_bytes(p);
   info->device_bytes = (double)p.device_bytes;
-  int launches = 1;  // drift
+  const int nseg = (int)p.segs.size();
+  int launches = nseg;  // drift, per lattice shape
   for (const auto* ops : {&p.factor_ops, &p.selinv_ops})
-    for (const auto& op : *ops)
-      if (op.kind != cl::OP_ZERO && op.blocks > 0)
-        launches += (op.kind == cl::OP_GEMM && cl::digit_gemms(p.precision)) ? 2 : 1;  // split + GEMM
+    for (const auto& op : *ops) {
+      if (op.kind == cl::OP_ZERO || op.blocks == 0) continue;
+      if (op.kind == cl::OP_ASSEMBLE || op.kind == cl::OP_EXTRACT) launches += nseg;
+      else launches += (op.kind == cl::OP_GEMM && cl::digit_gemms(p.precision)) ? 2 : 1;  // split + GEMM
+    }
   info->launches_per_eval = launches;
-  info->workspace_bytes = (double)p.batch * (4.0 * p.emu_words + 4.0 * p.emu_ints);
+  info->workspace_bytes = (double)p.fbatch * (4.0 * p.emu_words + 4.0 * p.emu_ints);
+  info->n_shapes = nseg;
   return CL_OK;
 }
 
@@ -486,7 +538,7 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
 }
 
 int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count) {
-  if (!plan || !count || table < 0 || table > CL_TABLE_LD) return CL_ERR_INVALID_ARG;
+  if (!plan || !count || table < 0 || table > CL_TABLE_SEGMENTS) return CL_ERR_INVALID_ARG;
   const cl::Plan& p = plan->p;
   std::vector<long long> v;
   auto mask = [&v](const cl::Mask2& m) { v.insert(v.end(), {m.r0, m.r1, m.r2, m.r3}); };
@@ -499,6 +551,10 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
       for (const auto& op : table == CL_TABLE_FACTOR_OPS ? p.factor_ops : p.selinv_ops)
         v.insert(v.end(),
                  {(long long)op.kind, op.d0, op.d1, op.blocks, op.level, op.stream, op.wait, op.signal, op.ndig});
+      break;
+    case CL_TABLE_SEGMENTS:
+      for (const auto& g : p.segs)
+        v.insert(v.end(), {g.Ns, g.Nt, g.V, g.count, g.pool_base, g.rep_stride, g.table_base, g.site_base});
       break;
     case CL_TABLE_GEMM:
       for (const auto& g : p.gemm) {
@@ -530,14 +586,10 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
       v.assign(p.maps.begin(), p.maps.end());
       break;
     case CL_TABLE_OFF:
-      v.insert(v.end(), p.off_diag.begin(), p.off_diag.end());
-      v.insert(v.end(), p.off_fwd.begin(), p.off_fwd.end());
-      v.insert(v.end(), p.off_bwd.begin(), p.off_bwd.end());
+      v.assign(p.off_all.begin(), p.off_all.end());
       break;
     case CL_TABLE_LD:
-      v.insert(v.end(), p.ld_diag.begin(), p.ld_diag.end());
-      v.insert(v.end(), p.ld_fwd.begin(), p.ld_fwd.end());
-      v.insert(v.end(), p.ld_bwd.begin(), p.ld_bwd.end());
+      v.assign(p.ld_all.begin(), p.ld_all.end());
       break;
   }
   *count = (long long)v.size();
@@ -549,6 +601,7 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
 
 int cl_plan_get_node(const cl_plan* plan, int i, int* parent, int* level, int* n_sep, int* n_bnd, int* sep,
                      int* bnd) {
+  if (plan && plan->p.ragged) return CL_ERR_UNSUPPORTED;
   if (!plan || i < 0 || i >= (int)plan->p.nodes.size()) return CL_ERR_INVALID_ARG;
   const cl::SNode& n = plan->p.nodes[i];
   if (parent) *parent = n.parent;

@@ -175,13 +175,13 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const GemmDesc* __restrict__ d
 
 cudaError_t launch_gemm(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
   if (digit_gemms(p.precision)) return launch_gemm_emu(p, op, arena, st);
-  const dim3 grid((unsigned)op.blocks, (unsigned)p.batch);
+  const dim3 grid((unsigned)op.blocks, (unsigned)p.fbatch);
   return launch_k(k_gemm_f64, grid, dim3(128), 0, st, op_launch(p, op), p.d_gemm, op.d0, op.d1, arena,
                   p.arena_elems);
 }
 
 cudaError_t launch_gemm(const Plan& p, const Op& op, float2* arena, cudaStream_t st) {
-  const dim3 grid((unsigned)op.blocks, (unsigned)p.batch);
+  const dim3 grid((unsigned)op.blocks, (unsigned)p.fbatch);
   return launch_k(k_gemm_f32, grid, dim3(256), 0, st, op_launch(p, op), p.d_gemm, op.d0, op.d1, arena,
                   p.arena_elems);
 }

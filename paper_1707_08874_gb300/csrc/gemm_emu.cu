@@ -591,13 +591,14 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
 
 // ---------------------------------------------------------------------------
 // Persistent digit GEMM for chunked launches (some K > 32: the products of the
-// selected inversion, K up to a pivot block).  One CTA per SM over a
-// contiguous range of output tiles (128 rows x 16 complex columns); per tile
-// its chunks of 32 complex k in order, each chunk in two halves of 32 real k.
-// Warp-specialised, 64 + 128 NG threads:
-//   warp 0 lane 0  producer: per half, the 7 A digit half-tiles (56 KB) and
-//                  the B' half-block (14 KB) into a three-stage ring;
-//   warp 1 lane 0  MMA issuer: 14 wide MMAs per half into one of two TMEM
+// selected inversion, K up to a pivot block).  One CTA per SM over the output
+// tiles (128 rows x 16 complex columns) t = blockIdx.x, + gridDim.x, ...; per
+// tile its chunks of 32 complex k in order, each chunk in two halves of 32
+// real k.  Warp-specialised, 64 + 128 NG threads:
+//   warp 0 lane 0  producer: per half, the ND A digit half-tiles (8 KB each)
+//                  and the B' half-block (2 ND KB) into a ring of three
+//                  stages (two with 8 digits);
+//   warp 1 lane 0  MMA issuer: 2 ND wide MMAs per half into one of two TMEM
 //                  accumulator sets (set = chunk parity), so the MMAs of
 //                  chunk k+1 run while chunk k is folded;
 //   warps 2-9      fold: NG = 2 groups of four warps, group g owning complex
@@ -634,8 +635,13 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
   auto stageA = [&](int s) { return smem_c + s * kCStage; };
   auto stageB = [&](int s) { return smem_c + s * kCStage + ND * kAHalf; };
 
+  // tiles are dealt round-robin (tile t to CTA t mod G): the CTAs then work
+  // on neighbouring tiles at any moment, so the row blocks of A and column
+  // blocks of B' in flight stay few and are served from L2 (each tile streams
+  // every chunk of its operands; a contiguous range per CTA would stream all
+  // row blocks at once)
   const int G = gridDim.x;
-  const int t0 = (int)((int64_t)total * blockIdx.x / G), t1 = (int)((int64_t)total * (blockIdx.x + 1) / G);
+  const int t0 = blockIdx.x, t1 = total;
   const unsigned* Wd = words + blockIdx.y * wstride;
   const int* Id = ints + blockIdx.y * istride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -662,7 +668,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
     if (lane == 0) {  // ---- producer
       int q = 0;
       bool good = true;
-      for (int t = t0; t < t1 && good && !*abort_flag; ++t) {
+      for (int t = t0; t < t1 && good && !*abort_flag; t += G) {
         const TileRef tr = tile_ref(gd, d0, d1, t);
         const EmuDesc& e = ed[tr.di];
         const int nch = e.Kp / kChunk;
@@ -698,7 +704,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
       uint32_t lc_bar = 0;
       unsigned lc_par = 0;
       bool has_lc = false;
-      for (int t = t0; t < t1 && good && !*abort_flag; ++t) {
+      for (int t = t0; t < t1 && good && !*abort_flag; t += G) {
         const TileRef tr = tile_ref(gd, d0, d1, t);
         const int nch = ed[tr.di].Kp / kChunk;
         for (int c = 0; c < nch && good; ++c, ++k) {
@@ -742,7 +748,7 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
     const int grp = (warp - 2) >> 2, q4 = warp & 3, rl = q4 * 32 + lane;
     int k = 0;
     bool stop = false;
-    for (int t = t0; t < t1 && !stop; ++t) {
+    for (int t = t0; t < t1 && !stop; t += G) {
       const TileRef tr = tile_ref(gd, d0, d1, t);
       const GemmDesc g = gd[tr.di];
       const EmuDesc e = ed[tr.di];
@@ -972,7 +978,7 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
 cudaError_t launch_gemm_emu(const Plan& p, const Op& op, double2* arena, cudaStream_t st) {
   const int items = p.emu[op.d1 - 1].it0 + p.emu[op.d1 - 1].items;
   const int ctas = op.stream ? std::max(1, p.num_sms - p.chain_sms) : p.num_sms;
-  return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.batch, arena, p.arena_elems,
+  return launch_emu(p.d_gemm, p.d_emu, op.d0, op.d1, items, op.blocks, p.fbatch, arena, p.arena_elems,
                     p.d_emu_words, p.d_emu_ints, p.emu_words, p.emu_ints, p.d_status, op.single_chunk, ctas, op.ndig,
                     st, op_launch(p, op), p.wait_ns);
 }

@@ -577,16 +577,23 @@ template <typename T, typename R>
 cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links, double m, double mu,
                       double* Gdiag, double* Gfwd, double* Gbwd, cudaStream_t st) {
   const int64_t stride = p.arena_elems;
-  const dim3 grid1((unsigned)op.blocks, (unsigned)p.batch);
-  const LatticeGeo g{p.Ns, p.Nt, p.V};
+  const dim3 grid1((unsigned)op.blocks, (unsigned)p.fbatch);
   const LaunchOpt prio = op_launch(p, op);
   switch (op.kind) {
     case OP_ZERO:
       return cudaMemset2DAsync(arena, (size_t)stride * sizeof(T), 0, (size_t)p.pool_elems * sizeof(T),
-                               (size_t)p.batch, st);
+                               (size_t)p.fbatch, st);
     case OP_ASSEMBLE:
-      return launch_k(k_assemble<T>, grid1, dim3(128), 0, st, prio, links, arena, stride, p.d_off, p.d_ld, g, m, mu,
-                      p.d_status);
+      // one launch per lattice shape: its replicas on grid.y, its links, fronts and block tables
+      for (const Segment& sg : p.segs) {
+        const LatticeGeo g{sg.Ns, sg.Nt, sg.V};
+        const dim3 grid((unsigned)((4 * sg.V + 127) / 128), (unsigned)sg.count);
+        const cudaError_t e =
+            launch_k(k_assemble<T>, grid, dim3(128), 0, st, prio, links + sg.site_base * 72, arena + sg.pool_base,
+                     sg.rep_stride, p.d_off + sg.table_base, p.d_ld + sg.table_base, g, m, mu, p.d_status);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
     case OP_EXTADD:
       return launch_k(k_extend_add<T>, grid1, dim3(256), 0, st, prio, p.d_extadd, op.d0, op.d1, p.d_maps, arena,
                       stride);
@@ -603,8 +610,16 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
       k_gather<T><<<grid1, 256, 0, st>>>(p.d_gather, op.d0, op.d1, p.d_maps, arena, stride);
       break;
     case OP_EXTRACT:
-      k_extract<T><<<grid1, 128, 0, st>>>(arena, stride, p.d_off, p.d_ld, p.V, Gdiag, Gfwd, Gbwd);
-      break;
+      for (const Segment& sg : p.segs) {
+        const dim3 grid((unsigned)((4 * sg.V + 127) / 128), (unsigned)sg.count);
+        k_extract<T><<<grid, 128, 0, st>>>(arena + sg.pool_base, sg.rep_stride, p.d_off + sg.table_base,
+                                           p.d_ld + sg.table_base, sg.V, Gdiag ? Gdiag + sg.site_base * 18 : nullptr,
+                                           Gfwd ? Gfwd + sg.site_base * 72 : nullptr,
+                                           Gbwd ? Gbwd + sg.site_base * 72 : nullptr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
   }
   return cudaGetLastError();
 }
@@ -616,10 +631,15 @@ template cudaError_t launch_op<float2, float>(const Plan&, const Op&, float2*, c
 
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,
                          double nf, double* Kf, cudaStream_t st) {
-  const LatticeGeo g{p.Ns, p.Nt, p.V};
-  const dim3 grid((unsigned)((4 * p.V + 127) / 128), (unsigned)p.batch);
-  k_drift<<<grid, 128, 0, st>>>(links, Gfwd, Gbwd, g, mu, nf, Kf, p.d_status);
-  return cudaGetLastError();
+  for (const Segment& sg : p.segs) {
+    const LatticeGeo g{sg.Ns, sg.Nt, sg.V};
+    const dim3 grid((unsigned)((4 * sg.V + 127) / 128), (unsigned)sg.count);
+    const int64_t b = sg.site_base;
+    k_drift<<<grid, 128, 0, st>>>(links + b * 72, Gfwd + b * 72, Gbwd + b * 72, g, mu, nf, Kf + b * 64, p.d_status);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace cl

@@ -47,6 +47,18 @@ struct SNode {
   int k = 0, r = 0, nf = 0;   // pivot unknowns, boundary unknowns, front order
   int64_t off = 0;            // front offset (elements) in the arena of one replica
   int64_t tmp = 0;            // offset of this front's workspace (elements)
+  int ea_map[2] = {-1, -1};   // extend-add site maps of the children (offsets into the plan's maps)
+  int ga_map = -1;            // gather site map of this node's boundary (offset into the plan's maps)
+};
+
+// One lattice shape of a plan: `count` replicas whose fronts lie in the arena
+// at pool_base + r * rep_stride (r < count), with the shape's block tables at
+// table_base in the plan's off / ld tables (9 V entries: diagonal, forward,
+// backward blocks) and its sites at site_base of the caller's site-indexed
+// arrays (links, G blocks, drift: sum of count x V of the earlier shapes).
+struct Segment {
+  int Ns = 0, Nt = 0, V = 0, count = 0;
+  int64_t pool_base = 0, rep_stride = 0, table_base = 0, site_base = 0;
 };
 
 // Two excluded index ranges [r0, r1) and [r2, r3) (empty ranges allowed).
@@ -141,7 +153,15 @@ struct Op {
 };
 
 struct Plan {
+  // a single-shape plan: Ns, Nt, V of the lattice, batch replicas (grid.y of
+  // every front launch, one arena_elems block per replica); a ragged plan
+  // (several shapes, cl_analyze_ragged): V = sites of all lattices, batch =
+  // number of lattices, fbatch = 1, every front of every lattice at its own
+  // offset in one arena and in the same launches
   int Ns = 0, Nt = 0, V = 0, N = 0, batch = 0, precision = CL_FP64;
+  int fbatch = 1;             // grid.y of the front launches (replicas sharing the descriptors)
+  bool ragged = false;
+  std::vector<Segment> segs;  // lattice shapes: the per-site kernels run once per segment
   int panel = kPanelFP64;
   bool has_device = false;
   int device = 0;
@@ -155,8 +175,10 @@ struct Plan {
   int64_t tmp_elems = 0;      // workspace, per replica
   int64_t arena_elems = 0;    // per replica (pool + workspace, padded)
   // host tables
-  std::vector<int64_t> off_diag, off_fwd, off_bwd;  // assembly / extraction offsets
+  std::vector<int64_t> off_diag, off_fwd, off_bwd;  // assembly / extraction offsets (single shape)
   std::vector<int> ld_diag, ld_fwd, ld_bwd;
+  std::vector<int64_t> off_all;                     // per segment: diagonal | forward | backward
+  std::vector<int> ld_all;
   std::vector<int> maps;                            // int maps of extend-add and gather
   std::vector<GemmDesc> gemm;
   std::vector<PanelDesc> panels;
@@ -219,6 +241,9 @@ enum Family { F_ZERO, F_ASSEMBLE, F_EXTADD, F_PANEL, F_GEMM, F_COPY, F_GATHER, F
 // host analysis (analyze.cpp); throws std::invalid_argument on invalid input.
 // panel: pivoting panel width in unknowns (multiple of 3, 3..48), 0 = default
 void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel = 0);
+// several shapes (count[i] lattices of Ns[i]^3 x Nt[i]) in one merged schedule
+void analyze_ragged(Plan& p, int nshapes, const int* Ns, const int* Nt, const int* count, int precision,
+                    int panel = 0);
 // number of unordered conflicting element accesses between the two streams of
 // the factor schedule (0: race-free); ignore_waits drops the cross-stream
 // waits (the check must then find races); *first describes the first one

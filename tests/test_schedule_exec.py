@@ -54,12 +54,23 @@ def _grid(base, rows, cols, ld, trans=False):
     return base + (j * ld + i if trans else i * ld + j)
 
 
-def execute(t, D, Ns, Nt):
+def execute(t, D, Ns=None, Nt=None):
+    """Run the plan's op lists in order on a host arena.  D: the dense Dirac
+    matrix of the one lattice of a single-shape plan, or the list of the dense
+    matrices of every lattice of a ragged plan (shape order, replicas in
+    order).  Returns the extracted blocks, one dict per lattice for a list."""
+    segs = t["segments"]
+    Ds = D if isinstance(D, list) else [D]
+    assert len(Ds) == int(segs[:, 3].sum())
     meta = t["meta"][0]
-    V, pool, n_arena = int(meta[2]), int(meta[6]), int(meta[8])
+    pool, n_arena = int(meta[6]), int(meta[8])
     A = np.full(n_arena, np.nan + 0j)  # the workspace is never read before it is written
     off, ld, maps = t["off"], t["ld"], t["maps"]
-    out = {}
+    lattices = []  # (Ns, Nt, V, arena base, table base) per lattice
+    for sNs, sNt, V, count, pbase, rstride, tbase, _ in segs:
+        for r in range(count):
+            lattices.append((int(sNs), int(sNt), int(V), int(pbase + r * rstride), int(tbase)))
+    outs = [dict() for _ in lattices]
     for ops in (t["factor_ops"], t["selinv_ops"]):
         for kind, d0, d1, blocks, *_ in ops:
             if blocks == 0 and kind != OP_ZERO:
@@ -68,14 +79,16 @@ def execute(t, D, Ns, Nt):
             if kind == OP_ZERO:
                 writes.append((np.arange(pool), np.zeros(pool)))
             elif kind == OP_ASSEMBLE:
-                for s in range(V):
-                    blocks3 = [(s, s, off[s], ld[s])]
-                    for nu in range(4):
-                        y = _fwd(s, nu, Ns, Nt)
-                        blocks3.append((s, y, off[V + 4 * s + nu], ld[V + 4 * s + nu]))
-                        blocks3.append((y, s, off[5 * V + 4 * s + nu], ld[5 * V + 4 * s + nu]))
-                    for a, b, o, l in blocks3:
-                        writes.append((_grid(o, 3, 3, l), D[3 * a:3 * a + 3, 3 * b:3 * b + 3]))
+                for (ns, nt, V, base, tb), Dl in zip(lattices, Ds):
+                    for s in range(V):
+                        blocks3 = [(s, s, off[tb + s], ld[tb + s])]
+                        for nu in range(4):
+                            y = _fwd(s, nu, ns, nt)
+                            j = tb + V + 4 * s + nu
+                            blocks3.append((s, y, off[j], ld[j]))
+                            blocks3.append((y, s, off[j + 4 * V], ld[j + 4 * V]))
+                        for a, b, o, l in blocks3:
+                            writes.append((_grid(base + o, 3, 3, l), Dl[3 * a:3 * a + 3, 3 * b:3 * b + 3]))
             elif kind == OP_EXTADD:
                 for parent, nfp, nchild, c0, c1, f0, f1, k0, k1, m0, m1 in t["extadd"][d0:d1]:
                     acc = np.zeros((nfp, nfp), complex)
@@ -113,15 +126,14 @@ def execute(t, D, Ns, Nt):
                     writes.append((child + (kc + I[:, None]) * nfc + kc + I[None, :],
                                    A[parent + pi[:, None] * nfp + pi[None, :]]))
             elif kind == OP_EXTRACT:
-                blk = lambda o, l: A[_grid(o, 3, 3, l)]
-                out["Gdiag"] = np.array([blk(off[s], ld[s]) for s in range(V)])
-                out["Gfwd"] = np.array([[blk(off[V + 4 * s + nu], ld[V + 4 * s + nu]) for nu in range(4)]
-                                        for s in range(V)])
-                out["Gbwd"] = np.array([[blk(off[5 * V + 4 * s + nu], ld[5 * V + 4 * s + nu]) for nu in range(4)]
-                                        for s in range(V)])
+                for (ns, nt, V, base, tb), out in zip(lattices, outs):
+                    blk = lambda j: A[_grid(base + off[j], 3, 3, ld[j])]
+                    out["Gdiag"] = np.array([blk(tb + s) for s in range(V)])
+                    out["Gfwd"] = np.array([[blk(tb + V + 4 * s + nu) for nu in range(4)] for s in range(V)])
+                    out["Gbwd"] = np.array([[blk(tb + 5 * V + 4 * s + nu) for nu in range(4)] for s in range(V)])
             for idx, val in writes:
                 A[idx] = val
-    return out
+    return outs if isinstance(D, list) else outs[0]
 
 
 def _blockwise(a, b):
@@ -168,3 +180,30 @@ def test_schedule_executor_sees_a_broken_table():
     tables["gemm"][bulk[0], 8] = 0  # K = 0: the product adds nothing
     got = execute(tables, D, 4, 4)
     assert _blockwise(got["Gfwd"], ref["Gfwd"]) > 1e3 * tol
+
+
+def test_ragged_schedule_reproduces_dense_inverses():
+    """A ragged plan (two 4^4 lattices and one 4^3 x 6 lattice in one merged
+    schedule: each level's panels, products, copies, extend-adds and gathers
+    over the fronts of all three lattices at once) reproduces every lattice's
+    blocks of D^{-1}."""
+    shapes = [(4, 4, 2), (4, 6, 1)]
+    plan = B.Plan.analyze_ragged(shapes, B.CL_FP64_EMU, 0, symbolic=True)
+    tables = plan.export_tables()
+    segs = tables["segments"]
+    assert segs.shape == (2, 8) and list(segs[:, 3]) == [2, 1]
+    assert plan.info["batch"] == 3 and plan.info["V"] == 2 * 256 + 384 and plan.info["n_shapes"] == 2
+    Us = [inputs.random_links(4, 4, seed=1707 + r) for r in range(2)] + [inputs.random_links(4, 6, seed=3)]
+    Ds = [oracle.dirac_dense(4, 4, Us[0], M, MU), oracle.dirac_dense(4, 4, Us[1], M, MU),
+          oracle.dirac_dense(4, 6, Us[2], M, MU)]
+    got = execute(tables, Ds)
+    for (ns, nt), U, g in zip([(4, 4), (4, 4), (4, 6)], Us, got):
+        ref = oracle.drift_eval(ns, nt, U, M, MU)
+        for key in ("Gdiag", "Gfwd", "Gbwd"):
+            assert _blockwise(g[key], ref[key]) < 1e-10, key
+    # one launch per step across all lattices: the level-0 panel inverses of
+    # the three lattices share launches, and the GEMM problems of a launch
+    # span the lattices' fronts
+    ops = tables["factor_ops"]
+    panel_ops = ops[ops[:, 0] == OP_PANEL]
+    assert panel_ops[:, 3].max() >= 3 * 4  # >= 4 leaves per 4^4 lattice, three lattices

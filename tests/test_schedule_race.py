@@ -39,3 +39,16 @@ def test_check_finds_races_without_waits(ns, nt, prec, panel):
     conflicts, first = p.check_schedule(ignore_waits=True)
     assert conflicts > 0 and "unordered" in first
     p.close()
+
+
+@pytest.mark.parametrize("prec", [B.CL_FP64_EMU, B.CL_MIXED_BF16X3, B.CL_FP64])
+def test_ragged_schedule_race_free(prec):
+    """The merged schedule of a ragged plan (fronts of three lattice shapes in
+    the same launches, trees of different heights) is race-free as well, and
+    the check still finds races when its waits are dropped."""
+    p = B.Plan.analyze_ragged([(4, 4, 2), (6, 4, 1), (4, 6, 1)], prec, 0, symbolic=True)
+    conflicts, first = p.check_schedule()
+    assert conflicts == 0, first
+    conflicts, first = p.check_schedule(ignore_waits=True)
+    assert conflicts > 0
+    p.close()
