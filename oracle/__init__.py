@@ -218,3 +218,55 @@ def neighbour_table(Ns: int, Nt: int) -> np.ndarray:
     up[:, 2] = ((t * Ns + (z + 1) % Ns) * Ns + y) * Ns + x
     up[:, 3] = ((((t + 1) % Nt) * Ns + z) * Ns + y) * Ns + x
     return up
+
+
+def derivative_blocks(Ns: int, Nt: int, links, mu: float):
+    """The two non-zero 3x3 blocks of d_{a x nu} D for every link (the left Lie
+    derivative d_a U = i lambda_a U, d_a U^{-1} = -i U^{-1} lambda_a applied to
+    Eq. 1 with the readings of the library's header):
+        F[x, nu, a] = d_a D_{x, x+nu} = +1/2 eta_nu(x) s_nu(x) e^{+mu d_{nu,t}} i lambda_a U_{x,nu}
+        B[x, nu, a] = d_a D_{x+nu, x} = -1/2 eta_nu(x) s_nu(x) e^{-mu d_{nu,t}} (-i U_{x,nu}^{-1} lambda_a)
+    Returns F, B of shape [V, 4, 8, 3, 3]."""
+    U = _c128(links)
+    V = volume(Ns, Nt)
+    s = np.arange(V)
+    c = np.stack([s % Ns, (s // Ns) % Ns, (s // Ns ** 2) % Ns, s // Ns ** 3], 1)
+    lam = gell_mann()
+    Ui = np.linalg.inv(U)
+    F = np.empty((V, 4, 8, 3, 3), np.complex128)
+    Bk = np.empty_like(F)
+    for nu in range(4):
+        eta = (-1.0) ** c[:, :nu].sum(1)
+        sgn = np.where((nu == 3) & (c[:, 3] == Nt - 1), -1.0, 1.0)
+        ph = 0.5 * eta * sgn
+        ef, eb = (np.exp(mu), np.exp(-mu)) if nu == 3 else (1.0, 1.0)
+        F[:, nu] = (ph * ef)[:, None, None, None] * 1j * np.einsum("aij,xjk->xaik", lam, U[:, nu])
+        Bk[:, nu] = (-ph * eb)[:, None, None, None] * (-1j) * np.einsum("xij,ajk->xaik", Ui[:, nu], lam)
+    return F, Bk
+
+
+def stochastic_drift(Ns: int, Nt: int, links, m: float, mu: float, eta, nf: float = 1.0,
+                     per_vector: bool = False) -> np.ndarray:
+    """The stochastic estimator of the fermion drift, Eq. 7, written out:
+        K^f_{a x nu} ~ nf (1/n) sum_i eta_i^dag D^{-1} (d_{a x nu} D) eta_i
+    for noise vectors eta [n, V, 3] (normalised so that E[eta eta^dag] = 1).
+    d_{a x nu} D has two non-zero blocks, so with w_i = eta_i^dag D^{-1} (a row
+    vector, from the dense inverse) each term is
+        w_i[x] F_a eta_i[x+nu] + w_i[x+nu] B_a eta_i[x].
+    Returns K [V, 4, 8] (with per_vector: the n single-vector estimates, [n, V, 4, 8])."""
+    V = volume(Ns, Nt)
+    eta = _c128(eta).reshape(-1, V, 3)
+    D = dirac_dense(Ns, Nt, links, m, mu)
+    LU, piv, info = lu(D)
+    if info != 0:
+        raise RuntimeError("oracle: singular Dirac matrix (info=%d)" % info)
+    G = inverse(LU, piv)
+    w = (eta.reshape(len(eta), 3 * V).conj() @ G).reshape(len(eta), V, 3)
+    F, Bk = derivative_blocks(Ns, Nt, links, mu)
+    up = neighbour_table(Ns, Nt)
+    K = np.zeros((len(eta), V, 4, 8), np.complex128)
+    for nu in range(4):
+        y = up[:, nu]
+        K[:, :, nu] = (np.einsum("ixj,xajk,ixk->ixa", w, F[:, nu], eta[:, y]) +
+                       np.einsum("ixj,xajk,ixk->ixa", w[:, y], Bk[:, nu], eta))
+    return nf * K if per_vector else nf * K.mean(0)

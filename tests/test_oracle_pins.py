@@ -301,3 +301,41 @@ def test_number_density_is_mu_derivative(rand):
     V = NS ** 3 * NT
     n = oracle.number_density(NS, NT, U, res["Gfwd"], res["Gbwd"], MU)
     assert abs(n * V - fd) < 1e-6 * abs(fd)
+
+
+def test_stochastic_drift_complete_basis_is_exact():
+    """Eq. 7 with the complete unit basis as noise, each vector with its own
+    phase (eta_i = sqrt(N) e^{i theta_i} e_i, so that (1/N) sum_i eta_i
+    eta_i^dag = 1 exactly, and a missing complex conjugate shows), reproduces
+    the exact drift of Eq. 6 / Eq. 8 from the selected blocks."""
+    ns, nt = 4, 4
+    V = ns ** 3 * nt
+    N = 3 * V
+    U = inputs.random_links(ns, nt, seed=61)
+    phase = np.exp(2j * np.pi * np.random.default_rng(3).random(N))
+    eta = (np.sqrt(N) * phase[:, None] * np.eye(N, dtype=np.complex128)).reshape(N, V, 3)
+    K = oracle.stochastic_drift(ns, nt, U, 0.05, 0.25, eta)
+    ref = oracle.drift_eval(ns, nt, U, 0.05, 0.25)["Kf"]
+    assert np.abs(K - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_stochastic_drift_is_unbiased():
+    """Z4 noise (entries 1, i, -1, -i, E[eta eta^dag] = 1): the estimator is unbiased, so
+    the mean over n = 256 noise vectors lies within a few standard errors of
+    the exact drift for every component (standard errors from the samples);
+    one noise vector alone is far from it (the indefinite-matrix variance the
+    paper warns about)."""
+    ns, nt = 4, 4
+    V = ns ** 3 * nt
+    U = inputs.random_links(ns, nt, seed=62)
+    ref = oracle.drift_eval(ns, nt, U, 0.05, 0.25)["Kf"]
+    rng = np.random.default_rng(7)
+    n = 256
+    eta = rng.choice(np.array([1.0, 1j, -1.0, -1j]), size=(n, V, 3))
+    samples = oracle.stochastic_drift(ns, nt, U, 0.05, 0.25, eta, per_vector=True)
+    K = samples.mean(0)
+    assert np.abs(K - oracle.stochastic_drift(ns, nt, U, 0.05, 0.25, eta)).max() < 1e-13 * np.abs(K).max()
+    se = np.sqrt(samples.real.var(0) + samples.imag.var(0)) / np.sqrt(n)
+    z = np.abs(K - ref) / np.maximum(se, 1e-300)
+    assert np.percentile(z, 99) < 4.0 and z.max() < 8.0, (np.percentile(z, 99), z.max())
+    assert np.abs(samples[0] - ref).max() > 3 * np.abs(K - ref).max()
