@@ -270,6 +270,41 @@ def compare_precisions(B, torch, links, bsz, ref, steps=3):
     return out
 
 
+def compare_stochastic(B, torch, links, bsz, kf_exact, counts=(1, 16), steps=3):
+    """The paper's comparison path (Sec. 3, Eq. 7): the drift from n Z4 noise
+    vectors (factorisation, n row-vector solves with its factors, estimated
+    blocks, drift) on the same links; rate and max |K_est - K| / max |K|
+    against the exact selected-inversion drift of replica 0."""
+    out = {}
+    V = NS ** 3 * NT
+    rng = np.random.default_rng(11)
+    plan = B.Plan.analyze(NS, NT, bsz, B.CL_FP64_EMU)
+    o = plan.alloc_outputs()
+    K0 = kf_exact[0].cpu().numpy()
+    for n in counts:
+        eta = torch.from_numpy(rng.choice(np.array([1.0, 1j, -1.0, -1j]), size=(n, bsz * V, 3))).to("cuda")
+        w = torch.empty_like(eta)
+        work = plan.stochastic_drift(links, M, MU, 1.0, eta, w, None, o["Gfwd"], o["Gbwd"], o["Kf"])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.stochastic_drift(links, M, MU, 1.0, eta, w, None, o["Gfwd"], o["Gbwd"], o["Kf"])
+        e1.record()
+        torch.cuda.synchronize()
+        del work
+        ms = e0.elapsed_time(e1) / steps
+        K = o["Kf"][0].cpu().numpy()
+        out["noise_%d" % n] = {"evals_per_s": bsz / (ms / 1e3), "ms_per_step": ms,
+                               "drift_rel_err_vs_exact": float(np.abs(K - K0).max() / np.abs(K0).max())}
+    st, _ = plan.get_status()
+    plan.close()
+    if st != B.CL_OK:
+        raise RuntimeError("stochastic drift reported %s" % B.error_string(st))
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1707_08874_gb300 import binding as B
@@ -425,6 +460,7 @@ def run_ours(args, rank, world, local):
                               "sample": lsample}
     if not args.no_compare:
         line["precisions"] = compare_precisions(B, torch, links, bsz, ref)
+        line["stochastic_estimator"] = compare_stochastic(B, torch, links, bsz, out["Kf"])
     print(json.dumps(line), flush=True)
     graph.close()
     plan.close()

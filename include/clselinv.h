@@ -131,6 +131,13 @@ typedef struct cl_langevin_params {
                                 root), removing the drift of det U away from 1; 0: off
                                 (default, as in the paper: Sec. 4.2 keeps the links free
                                 rather than reunitarising, for consistency with mu != 0) */
+  int reunit;                /* 1: after each update (and determinant renormalisation) every
+                                link is projected onto SU(3): first row normalised, second
+                                row orthogonalised to it and normalised, third row the
+                                complex conjugate of their cross product -- the
+                                reunitarisation Sec. 4.2 names as the remedy of the wrong
+                                mu = 0 results (there the evolution should stay in SU(3));
+                                0: off (default, as in the paper's runs)              */
 } cl_langevin_params;
 
 /*
@@ -260,6 +267,44 @@ int cl_fermion_drift(cl_plan* plan, const double* links, const double* Gfwd, con
  */
 int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, double nf,
                   double* Gdiag, double* Gfwd, double* Gbwd, double* Kf, cudaStream_t stream);
+
+/*
+ * Stochastic estimator of the fermion drift (Sec. 3, Eq. 7), the comparison
+ * path the paper contrasts with the exact drift:
+ *   tr[D^{-1} d_{axnu} D] ~ (1/n) sum_i eta_i^dag D^{-1} (d_{axnu} D) eta_i,
+ * for noise vectors with E[eta eta^dag] = 1 (Z2, Z4, U(1) or Gaussian entries).
+ * Site-indexed noise arrays hold every lattice of the plan: eta, w
+ * [n][sites][3] complex, sites = batch x V (single shape, replicas in order) or
+ * the sites of all lattices of a ragged plan (in the plan's order).
+ *
+ * cl_stochastic_workspace -- bytes of device workspace the calls below need
+ *   for n noise vectors (two front-vector sets per noise vector and replica).
+ *
+ * cl_left_solve -- w_i = eta_i^dag D^{-1} (row vectors, w_i[z] the entries of
+ *   eta_i^dag D^{-1} at site z) from the factors of the preceding cl_factor:
+ *   forward over the elimination tree (leaves to root) r_S <- r_S - r_J U-hat,
+ *   backward (root to leaves) w_J = r_J A_JJ^{-1} + w_S (-L-hat), with the
+ *   front blocks A_JJ^{-1}, U-hat = A_JJ^{-1} A_JS, L-hat = A_SJ A_JJ^{-1}
+ *   left by cl_factor.  Must run before cl_selinv_blocks, which overwrites
+ *   the factors.
+ *   eta   device [n][sites][3], read only;  n in 1..65535
+ *   w     device out [n][sites][3]
+ *   work  device scratch of cl_stochastic_workspace bytes (16-byte aligned),
+ *         caller-owned, not used by another call in flight
+ *
+ * cl_stochastic_drift -- cl_factor + cl_left_solve + the estimated selected
+ *   blocks Gfwd_est[x][nu] = (1/n) sum_i eta_i[x] w_i[x+nu]^T, Gbwd_est[x][nu] =
+ *   (1/n) sum_i eta_i[x+nu] w_i[x]^T, Gdiag_est[x] = (1/n) sum_i eta_i[x] w_i[x]^T
+ *   (expectations: the exact blocks G_{x,x+nu}, G_{x+nu,x}, G_{x,x}) + the
+ *   drift of Eq. 8 from them, which is the estimator above link by link.
+ *   links, m, mu, nf, Kf as cl_drift_eval; Gdiag_est may be NULL.
+ */
+int cl_stochastic_workspace(const cl_plan* plan, int n, size_t* bytes);
+int cl_left_solve(cl_plan* plan, const double* eta, int n, double* w, void* work, size_t work_bytes,
+                  cudaStream_t stream);
+int cl_stochastic_drift(cl_plan* plan, const double* links, double m, double mu, double nf, const double* eta, int n,
+                        double* w, double* Gdiag_est, double* Gfwd_est, double* Gbwd_est, double* Kf, void* work,
+                        size_t work_bytes, cudaStream_t stream);
 
 /*
  * cl_gauge_drift -- gauge part of Eq. 5 for the Wilson action:
@@ -451,6 +496,12 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *                        rep_stride, table_base, site_base (replica r of the
  *                        shape has its fronts at pool_base + r rep_stride, its
  *                        tables at table_base, its sites at site_base + r V)
+ *   CL_TABLE_VNODES      fronts of the row-vector solves (cl_left_solve), by
+ *                        level: front, vec, parent_vec, nf, k, r, level,
+ *                        nchild, child_vec[2], child_k[2], ea_map[2], ga_map,
+ *                        site0 (vector offsets in complex elements per noise
+ *                        vector; parent_vec -1 at a root)
+ *   CL_TABLE_VSITES      separator sites of those fronts (front order)
  * Offsets are elements of one replica's arena; a mask [r0, r1, r2, r3]
  * excludes the indices in [r0, r1) and [r2, r3).  Works on symbolic plans.
  */
@@ -466,7 +517,9 @@ enum {
   CL_TABLE_MAPS = 8,
   CL_TABLE_OFF = 9,
   CL_TABLE_LD = 10,
-  CL_TABLE_SEGMENTS = 11
+  CL_TABLE_SEGMENTS = 11,
+  CL_TABLE_VNODES = 12,
+  CL_TABLE_VSITES = 13
 };
 int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count);
 

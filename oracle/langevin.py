@@ -178,6 +178,21 @@ def renorm_det(U):
     return U / c[..., None, None]
 
 
+def reunitarize(U):
+    """Optional projection onto SU(3) after an update (Sec. 4.2 names it as the
+    remedy of the wrong mu = 0 results; off by default, as in the paper's
+    runs): Gram-Schmidt on the first two rows, u = r0/|r0|, v = (r1 - (u^dag
+    r1) u) / |...|, and the third row the complex conjugate of the cross
+    product u x v (which makes det = 1)."""
+    U = np.array(U, dtype=np.complex128)
+    r0, r1 = U[..., 0, :], U[..., 1, :]
+    u = r0 / np.linalg.norm(r0, axis=-1, keepdims=True)
+    v = r1 - np.sum(u.conj() * r1, axis=-1, keepdims=True) * u
+    v = v / np.linalg.norm(v, axis=-1, keepdims=True)
+    w = np.conj(np.cross(u, v))
+    return np.stack([u, v, w], axis=-2)
+
+
 def cooling_gradient(U, Ns, Nt):
     _, dn, _ = shifts(Ns, Nt)
     Uh = np.conj(np.swapaxes(U, -1, -2))
@@ -256,6 +271,8 @@ def langevin_step(U, prm: dict, step: int, Ns: int, Nt: int, replica: int = 0):
     U2 = link_update(U, K, eps, eta)
     if prm.get("renorm_det", 0):
         U2 = renorm_det(U2)
+    if prm.get("reunit", 0):
+        U2 = reunitarize(U2)
     if prm.get("n_cool", 0) > 0:
         U2 = gauge_cool(U2, prm["n_cool"], prm["alpha_cool"], Ns, Nt)
     return U2, obs, eps

@@ -58,7 +58,7 @@ class LangevinParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("m", ctypes.c_double), ("mu", ctypes.c_double), ("nf", ctypes.c_double),
                 ("eps_max", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha_cool", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("n_cool", ctypes.c_int), ("fermions", ctypes.c_int),
-                ("renorm_det", ctypes.c_int)]
+                ("renorm_det", ctypes.c_int), ("reunit", ctypes.c_int)]
 
 
 OBS_FIELDS = ["plaq_s_re", "plaq_s_im", "plaq_t_re", "plaq_t_im", "poly_re", "poly_im", "poly_inv_re",
@@ -82,12 +82,13 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
            "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
            "cl_analyze_symbolic_ex", "cl_plan_export", "cl_plan_set_wait_limit", "cl_analyze_ragged",
-           "cl_analyze_ragged_ex", "cl_analyze_ragged_symbolic"]
+           "cl_analyze_ragged_ex", "cl_analyze_ragged_symbolic", "cl_stochastic_workspace", "cl_left_solve",
+           "cl_stochastic_drift"]
 
 # cl_plan_export tables (include/clselinv.h) and their int64 row widths
 TABLES = {"meta": (0, 10), "factor_ops": (1, 9), "selinv_ops": (2, 9), "gemm": (3, 20), "panel": (4, 5),
           "copy": (5, 14), "extadd": (6, 11), "gather": (7, 7), "maps": (8, 1), "off": (9, 1), "ld": (10, 1),
-          "segments": (11, 8)}
+          "segments": (11, 8), "vnodes": (12, 16), "vsites": (13, 1)}
 
 
 def lib_path() -> str:
@@ -143,6 +144,9 @@ def load(build_if_missing: bool = True):
     L.cl_analyze_ragged.argtypes = [I, IA, IA, IA, I, ctypes.POINTER(P)]
     L.cl_analyze_ragged_ex.argtypes = [I, IA, IA, IA, I, I, ctypes.POINTER(P)]
     L.cl_analyze_ragged_symbolic.argtypes = [I, IA, IA, IA, I, I, ctypes.POINTER(P)]
+    L.cl_stochastic_workspace.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.cl_left_solve.argtypes = [P, P, I, P, P, ctypes.c_size_t, P]
+    L.cl_stochastic_drift.argtypes = [P, P, D, D, D, P, I, P, P, P, P, P, P, ctypes.c_size_t, P]
     L.cl_destroy_plan.argtypes = [P]
     L.cl_destroy_plan.restype = None
     L.cl_error_string.argtypes = [I]
@@ -331,6 +335,31 @@ class Plan:
         _check(load().cl_drift_eval(self._h, _dev(links, "links"), float(m), float(mu), float(nf),
                                     _dev(Gdiag, "Gdiag"), _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"),
                                     _dev(Kf, "Kf"), _stream(stream)), "cl_drift_eval")
+
+    # -- stochastic estimator (Eq. 7) -----------------------------------------
+    def _stoch_work(self, n: int):
+        import torch
+        nbytes = ctypes.c_size_t()
+        _check(load().cl_stochastic_workspace(self._h, int(n), ctypes.byref(nbytes)), "cl_stochastic_workspace")
+        return torch.empty(max(16, nbytes.value), dtype=torch.uint8, device="cuda"), nbytes.value
+
+    def left_solve(self, eta, w, stream=None):
+        """cl_left_solve: w_i = eta_i^dag D^{-1} after factor(); eta, w [n][sites][3]."""
+        work, nb = self._stoch_work(eta.shape[0])
+        _check(load().cl_left_solve(self._h, _dev(eta, "eta"), int(eta.shape[0]), _dev(w, "w"),
+                                    ctypes.c_void_p(work.data_ptr()), nb, _stream(stream)), "cl_left_solve")
+        return work
+
+    def stochastic_drift(self, links, m: float, mu: float, nf: float, eta, w, Gdiag, Gfwd, Gbwd, Kf, stream=None):
+        """cl_stochastic_drift (Eq. 7): factor, left solves, estimated blocks, drift.
+        Returns the workspace tensor (keep it alive until the stream is done)."""
+        work, nb = self._stoch_work(eta.shape[0])
+        _check(load().cl_stochastic_drift(self._h, _dev(links, "links"), float(m), float(mu), float(nf),
+                                          _dev(eta, "eta"), int(eta.shape[0]), _dev(w, "w"), _dev(Gdiag, "Gdiag"),
+                                          _dev(Gfwd, "Gfwd"), _dev(Gbwd, "Gbwd"), _dev(Kf, "Kf"),
+                                          ctypes.c_void_p(work.data_ptr()), nb, _stream(stream)),
+               "cl_stochastic_drift")
+        return work
 
     def set_wait_limit(self, seconds: float):
         """cl_plan_set_wait_limit: limit of the tensor-core GEMM waits (< 0: default 0.5 s)."""

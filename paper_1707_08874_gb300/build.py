@@ -10,7 +10,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libclselinv.so")
-SOURCES = ["api.cu", "kernels.cu", "gemm.cu", "gemm_emu.cu", "peak.cu", "noalloc.cu", "langevin.cu", "group.cu", "analyze.cpp", "schedule_check.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "gemm.cu", "gemm_emu.cu", "peak.cu", "noalloc.cu", "langevin.cu", "group.cu",
+           "stochastic.cu", "analyze.cpp", "schedule_check.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -304,10 +304,14 @@ struct FNode {
   int child[2] = {-1, -1};
   int ea_map[2] = {-1, -1};
   int ga_map = -1;
+  int site0 = 0;  // separator sites at p.vsites[site0 ..]
 };
 
-FNode fnode_of(const SNode& n, int64_t base, int index_base, int maps_base) {
+// appends the separator sites of a node (offset by site_base) to p.vsites
+FNode fnode_of(Plan& p, const SNode& n, int64_t base, int index_base, int maps_base, int64_t site_base) {
   FNode f;
+  f.site0 = (int)p.vsites.size();
+  for (int s : n.sep) p.vsites.push_back((int)(site_base + s));
   f.off = base + n.off;
   f.nf = n.nf;
   f.k = n.k;
@@ -593,6 +597,52 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
   }
   p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, assemble_blocks, -1});
 
+  // row-vector solves (stochastic estimator): nodes by level, front-vector
+  // workspace offsets, CTA offsets of the level launches (128 elements per CTA)
+  {
+    std::vector<int64_t> vec(nn);
+    int64_t v = 0;
+    for (int i = 0; i < nn; ++i) {
+      vec[i] = v;
+      v += F[i].nf;
+    }
+    p.vec_elems = v;
+    p.vnodes.clear();
+    p.vlevel.assign(1, 0);
+    p.vblk_nf.clear();
+    p.vblk_r.clear();
+    for (int h = 0; h < n_levels; ++h) {
+      int bnf = 0, br = 0;
+      for (int i : by_level[h]) {
+        const FNode& n = F[i];
+        VecNode x{};
+        x.front = n.off;
+        x.vec = vec[i];
+        x.parent_vec = parent[i] >= 0 ? vec[parent[i]] : -1;
+        x.nf = n.nf;
+        x.k = n.k;
+        x.r = n.r;
+        x.level = h;
+        x.nchild = n.nchild;
+        for (int q = 0; q < 2; ++q) {
+          x.child_vec[q] = q < n.nchild ? vec[n.child[q]] : -1;
+          x.child_k[q] = q < n.nchild ? F[n.child[q]].k : 0;
+          x.ea_map[q] = n.ea_map[q];
+        }
+        x.ga_map = n.ga_map;
+        x.site0 = n.site0;
+        x.blk_nf = bnf;
+        x.blk_r = br;
+        bnf += (n.nf + 127) / 128;
+        br += (n.r + 127) / 128;
+        p.vnodes.push_back(x);
+      }
+      p.vlevel.push_back((int)p.vnodes.size());
+      p.vblk_nf.push_back(bnf);
+      p.vblk_r.push_back(br);
+    }
+  }
+
   // split-digit workspace of the digit GEMMs: per GEMM launch the problems
   // are laid out one after the other from the start of that launch's stream
   // region (launches of one stream run in order; the factorisation's second
@@ -680,9 +730,10 @@ void analyze_host(Plan& p, int Ns, int Nt, int batch, int precision, int panel) 
   p.ld_all = t.ld;
   p.maps = t.maps;
   p.segs.assign(1, Segment{Ns, Nt, V, batch, 0, 0, 0, 0});
+  p.vsites.clear();
   std::vector<FNode> F;
   F.reserve(t.nodes.size());
-  for (const SNode& n : t.nodes) F.push_back(fnode_of(n, 0, 0, 0));
+  for (const SNode& n : t.nodes) F.push_back(fnode_of(p, n, 0, 0, 0, 0));
   build_schedule(p, F, t.n_levels, precision);
   for (size_t i = 0; i < F.size(); ++i) p.nodes[i].tmp = F[i].tmp;
   p.segs[0].rep_stride = p.arena_elems;  // each replica: its own fronts and workspace (grid.y)
@@ -718,6 +769,7 @@ void analyze_ragged(Plan& p, int nshapes, const int* Ns, const int* Nt, const in
   p.ld_fwd.clear();
   p.ld_bwd.clear();
   p.segs.clear();
+  p.vsites.clear();
   p.factor_flops = p.selinv_flops = 0;
   std::vector<FNode> F;
   int n_levels = 0;
@@ -732,7 +784,8 @@ void analyze_ragged(Plan& p, int nshapes, const int* Ns, const int* Nt, const in
     p.segs.push_back(Segment{Ns[s], Nt[s], t.V, count[s], base, t.pool_elems, table_base, site_base});
     for (int r = 0; r < count[s]; ++r) {
       const int index_base = (int)F.size();
-      for (const SNode& n : t.nodes) F.push_back(fnode_of(n, base, index_base, maps_base));
+      for (const SNode& n : t.nodes)
+        F.push_back(fnode_of(p, n, base, index_base, maps_base, site_base + (int64_t)r * t.V));
       base += t.pool_elems;
     }
     p.nodes.insert(p.nodes.end(), t.nodes.begin(), t.nodes.end());

@@ -1,4 +1,5 @@
 #include <algorithm>
+#include <cstdint>
 #include <cstdlib>
 // C ABI of the library (declared in clselinv.h): plan creation, device memory
 // of the plan, and the stream-ordered compute calls.
@@ -41,6 +42,8 @@ void free_device(Plan& p) {
   cudaFree(p.d_extadd);
   cudaFree(p.d_gather);
   cudaFree(p.d_emu);
+  cudaFree(p.d_vnodes);
+  cudaFree(p.d_vsites);
   cudaFree(p.d_emu_words);
   cudaFree(p.d_emu_ints);
   for (double* q : {p.d_Gdiag, p.d_Gfwd, p.d_Gbwd, p.d_K, p.d_Ui, p.d_F, p.d_Om, p.d_Omi, p.d_part}) cudaFree(q);
@@ -85,7 +88,9 @@ int setup_device(Plan& p) {
       (e = upload(p.d_panels, p.panels.data(), p.panels.size() * sizeof(cl::PanelDesc), total)) != cudaSuccess ||
       (e = upload(p.d_copies, p.copies.data(), p.copies.size() * sizeof(cl::CopyDesc), total)) != cudaSuccess ||
       (e = upload(p.d_extadd, p.extadd.data(), p.extadd.size() * sizeof(cl::ExtAddDesc), total)) != cudaSuccess ||
-      (e = upload(p.d_gather, p.gather.data(), p.gather.size() * sizeof(cl::GatherDesc), total)) != cudaSuccess)
+      (e = upload(p.d_gather, p.gather.data(), p.gather.size() * sizeof(cl::GatherDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_vnodes, p.vnodes.data(), p.vnodes.size() * sizeof(cl::VecNode), total)) != cudaSuccess ||
+      (e = upload(p.d_vsites, p.vsites.data(), p.vsites.size() * sizeof(int), total)) != cudaSuccess)
     return cuda_status(e);
   // Langevin-step buffers (single-shape plans; a ragged plan evaluates drifts only)
   const size_t B = p.ragged ? 0 : p.batch, V = p.V;
@@ -401,6 +406,36 @@ int cl_drift_eval(cl_plan* plan, const double* links, double m, double mu, doubl
   return st;
 }
 
+int cl_stochastic_workspace(const cl_plan* plan, int n, size_t* bytes) {
+  if (!plan || n < 1 || !bytes) return CL_ERR_INVALID_ARG;
+  *bytes = (size_t)cl::stochastic_work_elems(plan->p, n) * sizeof(double2);
+  return CL_OK;
+}
+
+int cl_left_solve(cl_plan* plan, const double* eta, int n, double* w, void* work, size_t work_bytes,
+                  cudaStream_t stream) {
+  if (!compute_ready(plan) || !eta || !w || !work || n < 1 || n > 65535) return CL_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  if (work_bytes < (size_t)cl::stochastic_work_elems(p, n) * sizeof(double2) || ((uintptr_t)work & 15u))
+    return CL_ERR_INVALID_ARG;
+  double2* wk = static_cast<double2*>(work);
+  const cudaError_t e = p.precision == CL_MIXED_FP32 ? cl::launch_left_solve<float2>(p, eta, n, w, wk, stream)
+                                                     : cl::launch_left_solve<double2>(p, eta, n, w, wk, stream);
+  return cuda_status(e);
+}
+
+int cl_stochastic_drift(cl_plan* plan, const double* links, double m, double mu, double nf, const double* eta, int n,
+                        double* w, double* Gdiag_est, double* Gfwd_est, double* Gbwd_est, double* Kf, void* work,
+                        size_t work_bytes, cudaStream_t stream) {
+  if (!Gfwd_est || !Gbwd_est || !Kf) return CL_ERR_INVALID_ARG;
+  int st = cl_factor(plan, links, m, mu, stream);
+  if (st == CL_OK) st = cl_left_solve(plan, eta, n, w, work, work_bytes, stream);
+  if (st == CL_OK)
+    st = cuda_status(cl::launch_stoch_blocks(plan->p, eta, w, n, Gdiag_est, Gfwd_est, Gbwd_est, stream));
+  if (st == CL_OK) st = cl_fermion_drift(plan, links, Gfwd_est, Gbwd_est, mu, nf, Kf, stream);
+  return st;
+}
+
 int cl_gauge_drift(cl_plan* plan, const double* links, double beta, double* Kg, cudaStream_t stream) {
   if (!compute_ready(plan) || !links || !Kg) return CL_ERR_INVALID_ARG;
   if (!langevin_ready(plan)) return CL_ERR_UNSUPPORTED;
@@ -448,6 +483,7 @@ int cl_langevin_step(cl_plan* plan, double* links, const cl_langevin_params* prm
   }
   cl::LangevinArgs a{prm->eps_max, prm->kappa, 0.0, prm->seed, 0};
   a.renorm_det = prm->renorm_det != 0;
+  a.reunit = prm->reunit != 0;
   cudaError_t e = cl::launch_gauge_drift(p, links, p.d_Ui, prm->beta, p.d_K, ferm ? 1 : 0, stream);
   if (e == cudaSuccess) e = cl::launch_kmax(p, p.d_K, p.d_slots, stream);
   if (e == cudaSuccess)
@@ -538,7 +574,7 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
 }
 
 int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count) {
-  if (!plan || !count || table < 0 || table > CL_TABLE_SEGMENTS) return CL_ERR_INVALID_ARG;
+  if (!plan || !count || table < 0 || table > CL_TABLE_VSITES) return CL_ERR_INVALID_ARG;
   const cl::Plan& p = plan->p;
   std::vector<long long> v;
   auto mask = [&v](const cl::Mask2& m) { v.insert(v.end(), {m.r0, m.r1, m.r2, m.r3}); };
@@ -555,6 +591,14 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
     case CL_TABLE_SEGMENTS:
       for (const auto& g : p.segs)
         v.insert(v.end(), {g.Ns, g.Nt, g.V, g.count, g.pool_base, g.rep_stride, g.table_base, g.site_base});
+      break;
+    case CL_TABLE_VNODES:
+      for (const auto& x : p.vnodes)
+        v.insert(v.end(), {x.front, x.vec, x.parent_vec, x.nf, x.k, x.r, x.level, x.nchild, x.child_vec[0],
+                           x.child_vec[1], x.child_k[0], x.child_k[1], x.ea_map[0], x.ea_map[1], x.ga_map, x.site0});
+      break;
+    case CL_TABLE_VSITES:
+      v.assign(p.vsites.begin(), p.vsites.end());
       break;
     case CL_TABLE_GEMM:
       for (const auto& g : p.gemm) {

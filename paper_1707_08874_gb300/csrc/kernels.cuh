@@ -80,6 +80,15 @@ cudaError_t launch_emu(const GemmDesc* gd, const EmuDesc* ed, int d0, int d1, in
                        int* status, bool single_chunk, int max_ctas, int ndig, cudaStream_t st, LaunchOpt lo,
                        unsigned long long wait_ns);
 
+// stochastic estimator (stochastic.cu): row-vector solves w = eta^dag D^{-1}
+// with the factors in the fronts, in a workspace of stochastic_work_elems
+// complex elements, and the estimated selected blocks
+int64_t stochastic_work_elems(const Plan& p, int n);
+template <typename T>
+cudaError_t launch_left_solve(const Plan& p, const double* eta, int n, double* w, double2* work, cudaStream_t st);
+cudaError_t launch_stoch_blocks(const Plan& p, const double* eta, const double* w, int n, double* Gd, double* Gf,
+                                double* Gb, cudaStream_t st);
+
 // fermion drift of every link of every replica
 cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd, const double* Gbwd, double mu,
                          double nf, double* Kf, cudaStream_t st);
@@ -92,6 +101,7 @@ struct LangevinArgs {
   unsigned long long seed;
   long long step;
   int renorm_det = 0;     // 1: U <- U / det(U)^{1/3} after the update
+  int reunit = 0;         // 1: U projected onto SU(3) after the update (Gram-Schmidt rows)
 };
 // observables record per replica (doubles): plaq_s re,im | plaq_t re,im | poly re,im |
 // poly_inv re,im | condensate re,im | unitarity | K_max | eps | t | step | spare |

@@ -263,6 +263,31 @@ __global__ void k_update(double* __restrict__ U, const double* __restrict__ K, i
 #pragma unroll
     for (int i = 0; i < 9; ++i) v.e[i] = cmul(v.e[i], f);
   }
+  if (a.reunit) {
+    // projection onto SU(3) (Sec. 4.2's reunitarisation): the first row
+    // normalised, the second made orthogonal to it (Gram-Schmidt) and
+    // normalised, the third the complex conjugate of their cross product
+    double2* E = v.e;
+    const double n0 = 1.0 / sqrt(E[0].x * E[0].x + E[0].y * E[0].y + E[1].x * E[1].x + E[1].y * E[1].y +
+                                 E[2].x * E[2].x + E[2].y * E[2].y);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E[j] = cscale(E[j], n0);
+    double2 c = make_double2(0, 0);  // u^dagger row1
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c = cadd(c, cmul(make_double2(E[j].x, -E[j].y), E[3 + j]));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E[3 + j] = csub(E[3 + j], cmul(c, E[j]));
+    const double n1 = 1.0 / sqrt(E[3].x * E[3].x + E[3].y * E[3].y + E[4].x * E[4].x + E[4].y * E[4].y +
+                                 E[5].x * E[5].x + E[5].y * E[5].y);
+#pragma unroll
+    for (int j = 3; j < 6; ++j) E[j] = cscale(E[j], n1);
+    const double2 w0 = csub(cmul(E[1], E[5]), cmul(E[2], E[4]));
+    const double2 w1 = csub(cmul(E[2], E[3]), cmul(E[0], E[5]));
+    const double2 w2 = csub(cmul(E[0], E[4]), cmul(E[1], E[3]));
+    E[6] = make_double2(w0.x, -w0.y);
+    E[7] = make_double2(w1.x, -w1.y);
+    E[8] = make_double2(w2.x, -w2.y);
+  }
 #pragma unroll
   for (int i = 0; i < 9; ++i) up[i] = v.e[i];
 }

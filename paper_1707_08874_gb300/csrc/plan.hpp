@@ -131,6 +131,23 @@ struct EmuDesc {
 };
 
 
+// A front of the row-vector solves w = eta^dag D^{-1} (stochastic estimator):
+// per noise vector, the front's vector [J | S] (nf complex) lives at `vec` of
+// the forward (R) and backward (W) vector workspaces; the front's factors at
+// `front` (A_JJ^{-1} | U-hat on the J rows, -L-hat on the S rows).  Sites of
+// the separator (front order) at `site0` of the plan's vsites table (sites
+// of the caller's site-indexed arrays; a single-shape plan adds replica x V).
+struct VecNode {
+  int64_t front, vec, parent_vec;  // parent_vec < 0: root
+  int nf, k, r, level;
+  int nchild;
+  int64_t child_vec[2];
+  int child_k[2];
+  int ea_map[2], ga_map;
+  int site0;
+  int blk_nf, blk_r;  // first CTA of this node in a level launch over nf / r elements (tiles of 128)
+};
+
 enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT };
 
 // One scheduled launch.  The factorisation runs on two streams: the
@@ -188,6 +205,11 @@ struct Plan {
   std::vector<EmuDesc> emu;                         // parallel to gemm (CL_FP64_EMU only)
   int64_t emu_words = 0, emu_ints = 0;              // workspace per replica
   std::vector<Op> factor_ops, selinv_ops;
+  // row-vector solves of the stochastic estimator: nodes sorted by level,
+  // vlevel[h] .. vlevel[h+1] the nodes of level h; CTAs per level launch
+  std::vector<VecNode> vnodes;
+  std::vector<int> vsites, vlevel, vblk_nf, vblk_r;
+  int64_t vec_elems = 0;  // complex elements of one front-vector workspace per noise vector and replica
   // device memory
   void* d_arena = nullptr;       // batch * arena_elems complex (precision-dependent)
   int* d_status = nullptr;       // [4]: code, node, column, spare
@@ -200,6 +222,8 @@ struct Plan {
   ExtAddDesc* d_extadd = nullptr;
   GatherDesc* d_gather = nullptr;
   EmuDesc* d_emu = nullptr;
+  VecNode* d_vnodes = nullptr;
+  int* d_vsites = nullptr;
   unsigned* d_emu_words = nullptr;
   int* d_emu_ints = nullptr;
   // Langevin-step buffers (all replicas): G blocks, drift, link inverses,

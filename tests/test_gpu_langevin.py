@@ -142,6 +142,27 @@ def test_langevin_step_renorm_det(plan, links2):
         assert np.abs(np.linalg.det(got[b]) - 1).max() < 1e-12
 
 
+def test_langevin_step_reunitarize(plan, links2):
+    """The optional SU(3) reunitarisation (Sec. 4.2): after one full step at
+    mu = 0 the links are in SU(3) to rounding and match the oracle step."""
+    B = _B()
+    prm = dict(beta=5.0, m=0.05, mu=0.0, nf=1.0, eps_max=1e-3, kappa=0.0, alpha_cool=0.05, seed=78,
+               n_cool=0, fermions=1, renorm_det=0, reunit=1)
+    U0 = links2
+    U = _dev(U0)
+    state = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    obs = torch.zeros((2, 20), dtype=torch.float64, device="cuda")
+    plan.langevin_step(U, prm, state, obs)
+    torch.cuda.synchronize()
+    assert plan.get_status()[0] == B.CL_OK
+    got = U.cpu().numpy()
+    for b in range(2):
+        ref, _, _ = L.langevin_step(U0[b].copy(), prm, 0, NS, NT, replica=b)
+        assert _rel(got[b], ref) < 1e-11
+        assert np.abs(got[b] @ np.conj(np.swapaxes(got[b], -1, -2)) - np.eye(3)).max() < 1e-13
+        assert np.abs(np.linalg.det(got[b]) - 1).max() < 1e-13
+
+
 def test_pure_gauge_su3_stays_unitary():
     """beta > 0, no fermions, SU(3) start: real drift and real noise keep the
     links in SU(3) (no excursion without a complex action)."""

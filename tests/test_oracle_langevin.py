@@ -203,3 +203,25 @@ def test_observables_closed_form_planes_and_time_order():
     assert abs(pt - 1) > 1e-2
     assert abs(np.trace(rev) - np.trace(line)) > 1e-2
     assert abs(np.trace(np.linalg.inv(line)) - np.conj(np.trace(line))) > 1e-2
+
+
+def test_reunitarize_pins():
+    """SU(3) projection: the result is unitary with det 1 for SL(3,C) input;
+    SU(3) links are left as they are; the first row keeps its direction and
+    the second row stays in the span of the first two input rows (the
+    defining properties of Gram-Schmidt)."""
+    U = inputs.random_links(4, 4, seed=33)
+    R = L.reunitarize(U)
+    eye = np.eye(3)
+    assert np.abs(R @ np.conj(np.swapaxes(R, -1, -2)) - eye).max() < 1e-13
+    assert np.abs(np.linalg.det(R) - 1).max() < 1e-13
+    S = inputs.random_links(4, 4, seed=34, sigma_im=0.0)
+    assert np.abs(L.reunitarize(S) - S).max() < 1e-13
+    r0 = U[..., 0, :]
+    assert np.abs(R[..., 0, :] - r0 / np.linalg.norm(r0, axis=-1, keepdims=True)).max() < 1e-14
+    # R[1] is a combination of U[0], U[1]: orthogonal to the cross product of U[0], U[1]
+    n = np.cross(U[..., 0, :], U[..., 1, :])
+    assert np.abs(np.sum(n * R[..., 1, :], axis=-1)).max() < 1e-12
+    # R[2] is orthogonal to both input rows in the hermitian sense
+    for j in range(2):
+        assert np.abs(np.sum(np.conj(U[..., j, :]) * R[..., 2, :], axis=-1)).max() < 1e-12

@@ -54,7 +54,7 @@ def _grid(base, rows, cols, ld, trans=False):
     return base + (j * ld + i if trans else i * ld + j)
 
 
-def execute(t, D, Ns=None, Nt=None):
+def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_out=None):
     """Run the plan's op lists in order on a host arena.  D: the dense Dirac
     matrix of the one lattice of a single-shape plan, or the list of the dense
     matrices of every lattice of a ragged plan (shape order, replicas in
@@ -71,7 +71,7 @@ def execute(t, D, Ns=None, Nt=None):
         for r in range(count):
             lattices.append((int(sNs), int(sNt), int(V), int(pbase + r * rstride), int(tbase)))
     outs = [dict() for _ in lattices]
-    for ops in (t["factor_ops"], t["selinv_ops"]):
+    for ops in (t[ph] for ph in phases):
         for kind, d0, d1, blocks, *_ in ops:
             if blocks == 0 and kind != OP_ZERO:
                 continue
@@ -133,7 +133,50 @@ def execute(t, D, Ns=None, Nt=None):
                     out["Gbwd"] = np.array([[blk(tb + 5 * V + 4 * s + nu) for nu in range(4)] for s in range(V)])
             for idx, val in writes:
                 A[idx] = val
+    if arena_out is not None:
+        arena_out.append(A)
     return outs if isinstance(D, list) else outs[0]
+
+
+def left_solve(t, A, eta):
+    """The row-vector solves w = eta^dag D^{-1} of cl_left_solve executed from
+    the exported front-vector tables on a factorised host arena A (forward
+    over the levels, then backward), for a plan with one replica per shape
+    segment row; eta [n, sites, 3]."""
+    vn, vs, maps = t["vnodes"], t["vsites"], t["maps"]
+    n, sites = eta.shape[0], eta.shape[1]
+    ne = int((vn[:, 1] + vn[:, 3]).max())
+    R = np.zeros((n, ne), complex)
+    W = np.zeros((n, ne), complex)
+    w = np.zeros_like(eta)
+    levels = sorted(set(vn[:, 6]))
+    front = lambda x: A[x[0]:x[0] + x[3] * x[3]].reshape(x[3], x[3])
+    for h in levels:  # forward
+        for x in vn[vn[:, 6] == h]:
+            fr, vec, pvec, nf, k, r, lv, nch, cv0, cv1, ck0, ck1, em0, em1, gm, s0 = x
+            v = np.zeros((n, nf), complex)
+            e = np.arange(k)
+            v[:, :k] = eta[:, vs[s0 + e // 3], e % 3].conj()
+            for cv, ck, em in ((cv0, ck0, em0), (cv1, ck1, em1))[:nch]:
+                E = np.arange(nf)
+                m = maps[em + E // 3]
+                ok = m >= 0
+                v[:, ok] += R[:, cv + ck + 3 * m[ok] + E[ok] % 3]
+            F = front(x)
+            v[:, k:] -= v[:, :k] @ F[:k, k:]
+            R[:, vec:vec + nf] = v
+    for h in levels[::-1]:  # backward
+        for x in vn[vn[:, 6] == h]:
+            fr, vec, pvec, nf, k, r, lv, nch, cv0, cv1, ck0, ck1, em0, em1, gm, s0 = x
+            F = front(x)
+            S = np.arange(r)
+            wS = W[:, pvec + 3 * maps[gm + S // 3] + S % 3] if r else np.zeros((n, 0), complex)
+            wJ = R[:, vec:vec + k] @ F[:k, :k] + wS @ F[k:, :k]
+            W[:, vec:vec + k] = wJ
+            W[:, vec + k:vec + nf] = wS
+            e = np.arange(k)
+            w[:, vs[s0 + e // 3], e % 3] = wJ
+    return w
 
 
 def _blockwise(a, b):
@@ -207,3 +250,32 @@ def test_ragged_schedule_reproduces_dense_inverses():
     ops = tables["factor_ops"]
     panel_ops = ops[ops[:, 0] == OP_PANEL]
     assert panel_ops[:, 3].max() >= 3 * 4  # >= 4 leaves per 4^4 lattice, three lattices
+
+
+@pytest.mark.parametrize("shapes", [[(4, 4, 1)], [(4, 4, 2), (4, 6, 1)]])
+def test_left_solve_tables(shapes):
+    """The front-vector tables of the row-vector solves (cl_left_solve), run on
+    the host on the factorised fronts, give w = eta^dag D^{-1} for every
+    lattice of a single-shape and of a ragged plan."""
+    if len(shapes) == 1:
+        ns, nt, _ = shapes[0]
+        tables = B.Plan.analyze_symbolic(ns, nt, B.CL_FP64_EMU, 30).export_tables()
+    else:
+        tables = B.Plan.analyze_ragged(shapes, B.CL_FP64_EMU, 0, symbolic=True).export_tables()
+    lat = [(ns, nt) for ns, nt, c in shapes for _ in range(c)]
+    Us = [inputs.random_links(ns, nt, seed=70 + i) for i, (ns, nt) in enumerate(lat)]
+    Ds = [oracle.dirac_dense(ns, nt, U, M, MU) for (ns, nt), U in zip(lat, Us)]
+    arena = []
+    execute(tables, Ds if len(Ds) > 1 else Ds[0], phases=("factor_ops",), arena_out=arena)
+    sites = sum(ns ** 3 * nt for ns, nt in lat)
+    rng = np.random.default_rng(5)
+    eta = rng.normal(size=(3, sites, 3)) + 1j * rng.normal(size=(3, sites, 3))
+    w = left_solve(tables, arena[0], eta)
+    s0 = 0
+    for (ns, nt), D in zip(lat, Ds):
+        V = ns ** 3 * nt
+        e = eta[:, s0:s0 + V].reshape(3, 3 * V)
+        want = (e.conj() @ np.linalg.inv(D)).reshape(3, V, 3)
+        got = w[:, s0:s0 + V]
+        assert np.abs(got - want).max() < 1e-10 * np.abs(want).max()
+        s0 += V
