@@ -41,11 +41,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fermion-drift evals/sec on 8^3x4 (FP64 vs mixed, stated drift error); front TFLOP/s vs peak"
 NS, NT, M, MU = 8, 4, 0.05, 0.25
-# DRAM bytes per launch of the dominant kernel (dram__bytes_read +
-# dram__bytes_write, ncu), keyed by (precision, batch, panel); an entry is
-# valid only for the kernel build it was taken on (None: not captured since
-# the kernel last changed)
-NCU_TRAFFIC = {}
+# DRAM bytes (dram__bytes_read + dram__bytes_write, ncu, caches flushed
+# before each launch) of all digit-GEMM and split launches of one evaluation,
+# the unit of `achieved` (538 launches at 8^3x4, batch 1, 30-unknown panels);
+# keyed by (precision, batch, panel) and valid only for the kernel build it
+# was taken on (profiles/gemm_dram_fp64_emu_8x4.md)
+NCU_TRAFFIC = {("fp64_emu", 1, 30): 17.652e9}
 # BF16 products per FP64-equivalent product of the digit GEMMs: digit pairs
 # p + q <= ND - 1 of ND digits per operand (8 digits: 36)
 DIGIT_PRODUCTS = {"fp64_emu": 36, "mixed": 6}
@@ -442,6 +443,8 @@ def run_ours(args, rank, world, local):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": peak_source,
                      "traffic": NCU_TRAFFIC.get((args.precision, bsz, panel)),
+                     "traffic_unit": "bytes per evaluation (all digit-GEMM and split launches)",
+                     "gemm_algorithmic_bytes": g.get("bytes", 0.0) / args.steps if g else None,
                      "gemm_only_tflops": gemm_only,
                      "gemm_share_of_kernel_time": g.get("total_ms", 0.0) / total_prof_ms if total_prof_ms else None},
         "flops_per_eval": flops_eval,

@@ -5,24 +5,41 @@
 
 namespace cl {
 
+// The per-link kernels take a block of kLinkBlock consecutive links and stage
+// the block's 3x3 link-major records through shared memory: consecutive
+// threads load (and store) consecutive 16-byte words, so every global access
+// is coalesced; each thread then works on its own link's record.
+constexpr int kLinkBlock = 128;
+__device__ __forceinline__ void stage_in(const double2* __restrict__ src, int n, double2* __restrict__ sm) {
+  for (int i = threadIdx.x; i < n; i += kLinkBlock) sm[i] = src[i];
+}
+__device__ __forceinline__ void stage_out(const double2* __restrict__ sm, int n, double2* __restrict__ dst) {
+  for (int i = threadIdx.x; i < n; i += kLinkBlock) dst[i] = sm[i];
+}
+
 // ---------------------------------------------------------------------------
 // D(m;mu) of Eq. 1 scattered into the fronts.  One thread per link (s, nu):
 // D_{s,s+nu} = +1/2 eta s_nu e^{+mu} U,  D_{s+nu,s} = -1/2 eta s_nu e^{-mu} U^{-1}
 // (e^{+-mu} on temporal hops only); the nu = 0 thread also writes D_{s,s} = m.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_assemble(const double* __restrict__ links, T* __restrict__ arena, int64_t stride,
-                           const int64_t* __restrict__ off, const int* __restrict__ ld, LatticeGeo g,
-                           double m, double mu, int* __restrict__ status) {
+__global__ void __launch_bounds__(kLinkBlock) k_assemble(const double* __restrict__ links, T* __restrict__ arena,
+                                                         int64_t stride, const int64_t* __restrict__ off,
+                                                         const int* __restrict__ ld, LatticeGeo g, double m,
+                                                         double mu, int* __restrict__ status) {
   pdl_enter();
-  const int link = blockIdx.x * blockDim.x + threadIdx.x;
-  if (link >= 4 * g.V) return;
-  const int rep = blockIdx.y;
+  __shared__ double2 sm[kLinkBlock * 9];
+  const int V = g.V, rep = blockIdx.y;
+  const int l0 = blockIdx.x * kLinkBlock, nl = min(kLinkBlock, 4 * V - l0);
+  stage_in(reinterpret_cast<const double2*>(links) + ((int64_t)rep * 4 * V + l0) * 9, nl * 9, sm);
+  __syncthreads();
+  const int link = l0 + threadIdx.x;
+  if (threadIdx.x >= nl) return;
   const int s = link >> 2, nu = link & 3;
   T* A = arena + rep * stride;
-  const int V = g.V;
   M3 u;
-  load_m3(links + ((int64_t)rep * 4 * V + link) * 18, u);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) u.e[i] = sm[threadIdx.x * 9 + i];
   bool finite = true;
 #pragma unroll
   for (int i = 0; i < 9; ++i) finite = finite && isfinite(u.e[i].x) && isfinite(u.e[i].y);
@@ -527,47 +544,63 @@ __global__ void k_extract(const T* __restrict__ arena, int64_t stride, const int
 // and Tr(lambda_a M) is read off the entries of M for the eight Gell-Mann
 // matrices.  Non-finite drift records CL_ERR_NONFINITE.
 // ---------------------------------------------------------------------------
-__global__ void k_drift(const double* __restrict__ links, const double* __restrict__ Gfwd,
-                        const double* __restrict__ Gbwd, LatticeGeo g, double mu, double nf,
-                        double* __restrict__ Kf, int* __restrict__ status) {
+__global__ void __launch_bounds__(kLinkBlock) k_drift(const double* __restrict__ links,
+                                                      const double* __restrict__ Gfwd,
+                                                      const double* __restrict__ Gbwd, LatticeGeo g, double mu,
+                                                      double nf, double* __restrict__ Kf,
+                                                      int* __restrict__ status) {
   pdl_enter();
-  const int link = blockIdx.x * blockDim.x + threadIdx.x;
-  if (link >= 4 * g.V) return;
-  const int64_t o = (int64_t)blockIdx.y * 4 * g.V + link;
-  const int s = link >> 2, nu = link & 3;
+  __shared__ double2 sm[kLinkBlock * 9];
+  const int l0 = blockIdx.x * kLinkBlock, nl = min(kLinkBlock, 4 * g.V - l0);
+  const int64_t o0 = (int64_t)blockIdx.y * 4 * g.V + l0;  // first link of the block
+  const int t = threadIdx.x, link = l0 + t;
+  const bool live = t < nl;
   M3 u, P, Q;
-  load_m3(links + o * 18, u);
-  load_m3(Gfwd + o * 18, P);
-  load_m3(Gbwd + o * 18, Q);
-  const M3 ui = inv_m3(u);
-  const M3 a = mul_m3(P, ui), b = mul_m3(u, Q);
-  const double ef = nu == 3 ? exp(mu) : 1.0, eb = nu == 3 ? exp(-mu) : 1.0;
-  const double ph = 0.5 * g.phase(s, nu) * nf;
-  M3 M;
+  const double* src[3] = {links, Gfwd, Gbwd};
+  M3* dst[3] = {&u, &P, &Q};
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    double2 v = cadd(cscale(a.e[i], eb), cscale(b.e[i], ef));
-    M.e[i] = make_double2(-ph * v.y, ph * v.x);  // multiply by i * ph
+  for (int a = 0; a < 3; ++a) {  // the block's U, G_{s,s+nu}, G_{s+nu,s} records in turn
+    stage_in(reinterpret_cast<const double2*>(src[a]) + o0 * 9, nl * 9, sm);
+    __syncthreads();
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) dst[a]->e[i] = sm[t * 9 + i];
+    }
+    __syncthreads();
   }
-  const double2* m = M.e;
-  const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
   double2 K[8];
-  K[0] = cadd(m[3], m[1]);                                      // lambda_1
-  K[1] = make_double2(-(m[1].y - m[3].y), m[1].x - m[3].x);      // lambda_2: i (M01 - M10)
-  K[2] = csub(m[0], m[4]);                                      // lambda_3
-  K[3] = cadd(m[6], m[2]);                                      // lambda_4
-  K[4] = make_double2(-(m[2].y - m[6].y), m[2].x - m[6].x);      // lambda_5: i (M02 - M20)
-  K[5] = cadd(m[7], m[5]);                                      // lambda_6
-  K[6] = make_double2(-(m[5].y - m[7].y), m[5].x - m[7].x);      // lambda_7: i (M12 - M21)
-  K[7] = cscale(csub(cadd(m[0], m[4]), cscale(m[8], 2.0)), r3);  // lambda_8
-  double2* out = reinterpret_cast<double2*>(Kf) + o * 8;
   bool finite = true;
+  if (live) {
+    const int s = link >> 2, nu = link & 3;
+    const M3 ui = inv_m3(u);
+    const M3 a = mul_m3(P, ui), b = mul_m3(u, Q);
+    const double ef = nu == 3 ? exp(mu) : 1.0, eb = nu == 3 ? exp(-mu) : 1.0;
+    const double ph = 0.5 * g.phase(s, nu) * nf;
+    M3 M;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    out[q] = K[q];
-    finite = finite && isfinite(K[q].x) && isfinite(K[q].y);
+    for (int i = 0; i < 9; ++i) {
+      double2 v = cadd(cscale(a.e[i], eb), cscale(b.e[i], ef));
+      M.e[i] = make_double2(-ph * v.y, ph * v.x);  // multiply by i * ph
+    }
+    const double2* m = M.e;
+    const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
+    K[0] = cadd(m[3], m[1]);                                      // lambda_1
+    K[1] = make_double2(-(m[1].y - m[3].y), m[1].x - m[3].x);      // lambda_2: i (M01 - M10)
+    K[2] = csub(m[0], m[4]);                                      // lambda_3
+    K[3] = cadd(m[6], m[2]);                                      // lambda_4
+    K[4] = make_double2(-(m[2].y - m[6].y), m[2].x - m[6].x);      // lambda_5: i (M02 - M20)
+    K[5] = cadd(m[7], m[5]);                                      // lambda_6
+    K[6] = make_double2(-(m[5].y - m[7].y), m[5].x - m[7].x);      // lambda_7: i (M12 - M21)
+    K[7] = cscale(csub(cadd(m[0], m[4]), cscale(m[8], 2.0)), r3);  // lambda_8
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sm[t * 8 + q] = K[q];
+      finite = finite && isfinite(K[q].x) && isfinite(K[q].y);
+    }
+    if (!finite) set_status(status, CL_ERR_NONFINITE, s, nu);
   }
-  if (!finite) set_status(status, CL_ERR_NONFINITE, s, nu);
+  __syncthreads();
+  stage_out(sm, nl * 8, reinterpret_cast<double2*>(Kf) + o0 * 8);
 }
 
 // ---------------------------------------------------------------------------
@@ -587,9 +620,9 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
       // one launch per lattice shape: its replicas on grid.y, its links, fronts and block tables
       for (const Segment& sg : p.segs) {
         const LatticeGeo g{sg.Ns, sg.Nt, sg.V};
-        const dim3 grid((unsigned)((4 * sg.V + 127) / 128), (unsigned)sg.count);
+        const dim3 grid((unsigned)((4 * sg.V + kLinkBlock - 1) / kLinkBlock), (unsigned)sg.count);
         const cudaError_t e =
-            launch_k(k_assemble<T>, grid, dim3(128), 0, st, prio, links + sg.site_base * 72, arena + sg.pool_base,
+            launch_k(k_assemble<T>, grid, dim3(kLinkBlock), 0, st, prio, links + sg.site_base * 72, arena + sg.pool_base,
                      sg.rep_stride, p.d_off + sg.table_base, p.d_ld + sg.table_base, g, m, mu, p.d_status);
         if (e != cudaSuccess) return e;
       }
@@ -633,9 +666,10 @@ cudaError_t launch_drift(const Plan& p, const double* links, const double* Gfwd,
                          double nf, double* Kf, cudaStream_t st) {
   for (const Segment& sg : p.segs) {
     const LatticeGeo g{sg.Ns, sg.Nt, sg.V};
-    const dim3 grid((unsigned)((4 * sg.V + 127) / 128), (unsigned)sg.count);
+    const dim3 grid((unsigned)((4 * sg.V + kLinkBlock - 1) / kLinkBlock), (unsigned)sg.count);
     const int64_t b = sg.site_base;
-    k_drift<<<grid, 128, 0, st>>>(links + b * 72, Gfwd + b * 72, Gbwd + b * 72, g, mu, nf, Kf + b * 64, p.d_status);
+    k_drift<<<grid, kLinkBlock, 0, st>>>(links + b * 72, Gfwd + b * 72, Gbwd + b * 72, g, mu, nf, Kf + b * 64,
+                                         p.d_status);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
