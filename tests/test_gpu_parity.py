@@ -315,6 +315,23 @@ def test_fp64_full_size(prec, full_size):
     plan.close()
 
 
+def test_fp64_full_size_second_configuration():
+    """The 1e-10 bar of the FP64 path at 8^3 x 4 on a second link
+    configuration (seed 1708): every selected block and every drift entry
+    against the oracle's full inverse."""
+    B = _binding()
+    ns, nt = 8, 4
+    U = inputs.random_links(ns, nt, seed=1708)
+    ref = oracle.drift_eval(ns, nt, U, M, MU)
+    plan = B.Plan.analyze(ns, nt, 1, B.CL_FP64_EMU)
+    got, st = _run(plan, U)
+    assert st == B.CL_OK
+    errs = {k: _blockwise(got[k][0], ref[k]) for k in ("Gdiag", "Gfwd", "Gbwd")}
+    kerr = np.abs(got["Kf"][0] - ref["Kf"]).max() / np.abs(ref["Kf"]).max()
+    assert max(errs.values()) < BAR and kerr < BAR, (errs, kerr)
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_singular_panel_reported(prec):
     """m = 0, mu = 0 and one temporal link of -1 on the ring of sites
