@@ -115,6 +115,17 @@ typedef struct cl_profile_entry {
   double bytes;              /* algorithmic DRAM bytes of those launches        */
 } cl_profile_entry;
 
+/* One launch of a profiled call, filled by cl_profile_trace. */
+typedef struct cl_trace_entry {
+  char name[32];             /* kernel family, as in cl_profile_entry           */
+  int phase;                 /* 0 factorisation op, 1 selected-inversion op, -1 other */
+  int op;                    /* index of the op in its phase's list (-1 other)   */
+  int stream;                /* factorisation stream: 0 panel chain, 1 bulk     */
+  int level;                 /* tree level of the op (root = highest; -1 none)  */
+  double t0_us, t1_us;       /* event times around the launch, microseconds from
+                                the first recorded launch                       */
+} cl_trace_entry;
+
 /* Parameters of one complex-Langevin step (cl_langevin_step). */
 typedef struct cl_langevin_params {
   double beta;               /* Wilson coupling: S_g = beta sum_P [1 - (Tr U_P + Tr U_P^{-1})/6] */
@@ -536,6 +547,17 @@ int cl_profile_enable(cl_plan* plan, int enable);
  * per kernel family into out[0..cap-1]; *n receives the number of families.
  */
 int cl_profile_read(cl_plan* plan, cl_profile_entry* out, int cap, int* n);
+
+/*
+ * cl_profile_trace -- the same records as a timeline: synchronises on them and
+ * writes one entry per recorded launch, in issue order, into out[0..cap-1]
+ * (*n receives the number of records, which may exceed cap).  Times come from
+ * the event pairs on each launch's stream, so the two streams of the
+ * factorisation can be compared on one clock; with profiling on, launches do
+ * not overlap their predecessors on the same stream (no programmatic launch).
+ * CL_ERR_INVALID_ARG for a null plan or n, or a null out with cap > 0.
+ */
+int cl_profile_trace(cl_plan* plan, cl_trace_entry* out, int cap, int* n);
 
 /*
  * cl_measure_peak -- measures an arithmetic peak of the current device with a

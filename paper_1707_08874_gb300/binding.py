@@ -54,6 +54,11 @@ class ProfileEntry(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("phase", ctypes.c_int), ("op", ctypes.c_int), ("stream", ctypes.c_int),
+                ("level", ctypes.c_int), ("t0_us", ctypes.c_double), ("t1_us", ctypes.c_double)]
+
+
 class LangevinParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("m", ctypes.c_double), ("mu", ctypes.c_double), ("nf", ctypes.c_double),
                 ("eps_max", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha_cool", ctypes.c_double),
@@ -77,7 +82,7 @@ def obs_dict(row) -> dict:
 
 EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
            "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
-           "cl_profile_read", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
+           "cl_profile_read", "cl_profile_trace", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
            "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
@@ -120,6 +125,7 @@ def load(build_if_missing: bool = True):
                                    ctypes.POINTER(I), P, P]
     L.cl_profile_enable.argtypes = [P, I]
     L.cl_profile_read.argtypes = [P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(I)]
+    L.cl_profile_trace.argtypes = [P, ctypes.POINTER(TraceEntry), I, ctypes.POINTER(I)]
     L.cl_measure_peak.argtypes = [I, ctypes.POINTER(D)]
     L.cl_drift_eval_noalloc.argtypes = [I, I, P, D, D, D, P, P, P, P, P]
     L.cl_gauge_drift.argtypes = [P, P, D, P, P]
@@ -411,6 +417,16 @@ class Plan:
         _check(load().cl_profile_read(self._h, buf, 16, ctypes.byref(n)), "cl_profile_read")
         return {buf[i].name.decode(): dict(launches=buf[i].launches, total_ms=buf[i].total_ms,
                                            flops=buf[i].flops, bytes=buf[i].bytes) for i in range(n.value)}
+
+    def profile_trace(self) -> list:
+        """Per-launch timeline of the profiled calls since profile_enable: one
+        dict per launch (name, phase, op, stream, level, t0_us, t1_us)."""
+        n = ctypes.c_int()
+        _check(load().cl_profile_trace(self._h, None, 0, ctypes.byref(n)), "cl_profile_trace")
+        buf = (TraceEntry * max(1, n.value))()
+        _check(load().cl_profile_trace(self._h, buf, n.value, ctypes.byref(n)), "cl_profile_trace")
+        return [dict(name=b.name.decode(), phase=b.phase, op=b.op, stream=b.stream, level=b.level,
+                     t0_us=b.t0_us, t1_us=b.t1_us) for b in buf[:n.value]]
 
     # -- convenience: allocate outputs and run one evaluation --------------
     def alloc_outputs(self):

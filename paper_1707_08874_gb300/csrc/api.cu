@@ -198,17 +198,18 @@ void prof_begin(Plan& p, cudaStream_t st, cudaEvent_t& e0) {
   cudaEventCreate(&e0);
   cudaEventRecord(e0, st);
 }
-void prof_end(Plan& p, cudaStream_t st, cudaEvent_t e0, int family, double flops, double bytes) {
+void prof_end(Plan& p, cudaStream_t st, cudaEvent_t e0, int family, double flops, double bytes, int phase = -1,
+              int idx = -1, int stream = 0, int level = -1) {
   if (!p.profiling || !e0) return;
   cudaEvent_t e1;
   cudaEventCreate(&e1);
   cudaEventRecord(e1, st);
-  p.prof.push_back(Plan::ProfRec{family, (void*)e0, (void*)e1, flops, bytes});
+  p.prof.push_back(Plan::ProfRec{family, (void*)e0, (void*)e1, flops, bytes, phase, idx, stream, level});
 }
 
 template <typename T, typename R>
 int launch_one(Plan& p, const cl::Op& op, T* arena, const double* links, double m, double mu, double* Gd,
-               double* Gf, double* Gb, cudaStream_t st) {
+               double* Gf, double* Gb, cudaStream_t st, int phase, int idx) {
   if (op.blocks == 0 && op.kind != cl::OP_ZERO) return CL_OK;
   cudaEvent_t e0;
   prof_begin(p, st, e0);
@@ -218,7 +219,7 @@ int launch_one(Plan& p, const cl::Op& op, T* arena, const double* links, double 
     int fam;
     double fl, by;
     op_work(p, op, fam, fl, by);
-    prof_end(p, st, e0, fam, fl, by);
+    prof_end(p, st, e0, fam, fl, by, phase, idx, op.stream, op.level);
   }
   return CL_OK;
 }
@@ -233,7 +234,8 @@ template <typename T, typename R>
 int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double m, double mu, double* Gd,
             double* Gf, double* Gb, cudaStream_t st) {
   T* arena = static_cast<T*>(p.d_arena);
-  const bool two = &ops == &p.factor_ops && p.streams[1] != nullptr;
+  const int phase = &ops == &p.factor_ops ? 0 : 1;
+  const bool two = phase == 0 && p.streams[1] != nullptr;
   // an op's first kernel may launch programmatically (overlapping its
   // predecessor's tail) only when it directly follows a kernel of this op list
   // on its stream, with no event wait in between
@@ -241,10 +243,11 @@ int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double
   auto launches_kernel = [](const cl::Op& op) { return op.kind != cl::OP_ZERO && op.blocks > 0; };
   if (!two) {
     bool fresh = true;
-    for (const auto& op : ops) {
+    for (size_t i = 0; i < ops.size(); ++i) {
+      const cl::Op& op = ops[i];
       cl::Op o = op;
       o.pdl = !fresh && !p.profiling;
-      const int r = launch_one<T, R>(p, o, arena, links, m, mu, Gd, Gf, Gb, st);
+      const int r = launch_one<T, R>(p, o, arena, links, m, mu, Gd, Gf, Gb, st, phase, (int)i);
       if (r != CL_OK) return r;
       fresh = !launches_kernel(op);
     }
@@ -263,7 +266,7 @@ int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double
     cl::Op o = op;
     o.pdl = !fresh[op.stream] && op.wait < 0 && !p.profiling;
     fresh[op.stream] = !launches_kernel(op);
-    const int r = launch_one<T, R>(p, o, arena, links, m, mu, Gd, Gf, Gb, s);
+    const int r = launch_one<T, R>(p, o, arena, links, m, mu, Gd, Gf, Gb, s, phase, (int)i);
     if (r != CL_OK) return r;
     if (op.signal && (e = cudaEventRecord((cudaEvent_t)p.op_events[i], s)) != cudaSuccess) return cuda_status(e);
   }
@@ -697,6 +700,32 @@ int cl_profile_read(cl_plan* plan, cl_profile_entry* out, int cap, int* n) {
     ++k;
   }
   *n = k;
+  return CL_OK;
+}
+
+int cl_profile_trace(cl_plan* plan, cl_trace_entry* out, int cap, int* n) {
+  if (!compute_ready(plan) || !n || (cap > 0 && !out)) return CL_ERR_INVALID_ARG;
+  const auto& recs = plan->p.prof;
+  for (auto& r : recs) {
+    cudaError_t e = cudaEventSynchronize((cudaEvent_t)r.ev1);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  *n = (int)recs.size();
+  for (size_t i = 0; i < recs.size() && (int)i < cap; ++i) {
+    const auto& r = recs[i];
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, (cudaEvent_t)recs[0].ev0, (cudaEvent_t)r.ev0);
+    cudaEventElapsedTime(&b, (cudaEvent_t)recs[0].ev0, (cudaEvent_t)r.ev1);
+    cl_trace_entry& t = out[i];
+    std::memset(&t, 0, sizeof(t));
+    std::strncpy(t.name, kFamilyName[r.family], sizeof(t.name) - 1);
+    t.phase = r.phase;
+    t.op = r.op;
+    t.stream = r.stream;
+    t.level = r.level;
+    t.t0_us = 1e3 * a;
+    t.t1_us = 1e3 * b;
+  }
   return CL_OK;
 }
 

@@ -229,14 +229,13 @@ __device__ __forceinline__ int pivot_row(const T (&v)[H], int c0, int bp, int la
   return (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && key == kmax) ? (unsigned)bi : 0x7fffffffu);
 }
 
-// entry update v - f w of Gauss-Jordan step c, one FMA sequence for every
-// entry (a divergent branch would cost each warp both paths on the FP64
-// pipe): pivot row (i == c): v = scaled pivot row, f = 0; pivot column
-// (j == c): v = 0, w = inv (-> -f inv)
+// v - f w on complex entries, the one FMA sequence of every entry of a
+// Gauss-Jordan step (the special rows and columns enter through their
+// operands, not through a branch that would cost each warp both paths on the
+// FP64 pipe)
 template <typename T>
-__device__ __forceinline__ T gj_entry(T v, T f, T w, bool prow_i, bool pcol_j) {
-  T r = prow_i ? w : (pcol_j ? T{0, 0} : v);
-  if (prow_i) f = T{0, 0};
+__device__ __forceinline__ T gj_fms(T v, T f, T w) {
+  T r = v;
   r.x = fma(-f.x, w.x, r.x);
   r.x = fma(f.y, w.y, r.x);
   r.y = fma(-f.x, w.y, r.y);
@@ -255,34 +254,45 @@ constexpr size_t panel_smem_bytes(int mp) {
 __host__ __device__ constexpr int bit_count(unsigned m) { return m ? (int)(m & 1u) + bit_count(m >> 1) : 0; }
 
 // Update-warp sets: warp w runs on scheduler w % 4.  The pivot chain of warp
-// 0 is a string of dependent FP64 operations, so the update warps stay off
-// scheduler 0 (measured on one 24- / 30-wide FP64 block: 43 / 61 us with
-// twelve update warps on schedulers 1-3, 47 / 67 us with seven warps over all
-// four).
+// 0 is a string of dependent FP64 operations, and the SM's FP64 unit is one
+// unit shared by its four schedulers (measured: ~1.7 lanes per cycle per SM,
+// and one FP64 warp instruction per ~64 cycles per warp, whatever the number
+// of live lanes); a chain instruction waits longer the more schedulers feed
+// the unit (64 cycles alone, 95 with update warps on two schedulers, 133 on
+// three).  So the update warps stay off scheduler 0, and 30-wide FP64 blocks
+// keep them on two schedulers (one block: 55.3 us against 57.3 us on three).
 constexpr unsigned kUpdNoSched0 = 0xEEEEu;
+constexpr unsigned kUpdSched12 = 0x6666u;
 
+// Gauss-Jordan step c in the scaled-multiplier form: with pivot p, column c
+// values f_i and pivot row r_j (logical rows, before the step), every entry
+// becomes v_ij - g_i w_j with g_i = f_i / p (g_c = -1/p), w_j = r_j (w_c = 1)
+// and v = 0 on row c and column c, which yields the scaled pivot row r_j / p,
+// the column -f_i / p and the pivot 1/p in one FMA sequence per entry.  The
+// update warps read r_j from the step's input copy, so the chain only forms g.
+//
 // The block lives in two shared-memory copies: step c reads copy c & 1 and
-// writes the other, so one barrier per column suffices and warp 0 can read
-// the pre-step values of any row while the update warps write the step's
-// results.  Column look-ahead: while the update warps apply step c to every
-// entry outside column c+1, warp 0 applies it to column c+1, every lane forms
-// the reciprocal of its own candidate pivots while the pivot is chosen, warp
-// 0 applies step c to the pivot row and leaves step c+1's row map,
-// multipliers and scaled pivot row for the next column.  The row
-// interchanges are undone at the end by reading the columns through the
-// inverse of the final row map.
+// writes the other, so one barrier per column suffices.  Column look-ahead:
+// while the update warps apply step c to every entry outside column c+1, warp
+// 0 applies it to column c+1, every lane forms the reciprocal of its own
+// candidate pivot while the pivot is chosen, and warp 0 leaves step c+1's row
+// map and multipliers g for the next column (measured against the form that
+// scales the pivot row on the chain: 24 / 30 / 48-wide FP64 blocks 36.9 / 55.3
+// / 168 us against 41.0 / 59.1 / 212 us, FP32 14.3 / 16.4 / 38.9 against
+// 17.4 / 22.4 / 53.3 us).  The row interchanges are undone at the end by
+// reading the columns through the inverse of the final row map.
 template <typename T, typename R, int MP, int NT, unsigned UMASK>
 __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
                                                       int64_t stride, int* __restrict__ status) {
   pdl_enter();
-  constexpr int NU = bit_count(UMASK);                   // update warps
+  constexpr int NU = bit_count(UMASK);                         // update warps
   constexpr int kSlots = (MP * MP + 32 * NU - 1) / (32 * NU);  // update entries per update thread
-  constexpr int H = (MP + 31) / 32;                      // column entries per lane of warp 0
+  constexpr int H = (MP + 31) / 32;                            // column entries per lane of warp 0
   constexpr int NW = NT / 32;
   static_assert((UMASK & 1u) == 0 && (UMASK >> NW) == 0, "update warps: 1 .. NT/32 - 1");
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T(*S)[MP][MP + 1] = reinterpret_cast<T(*)[MP][MP + 1]>(panel_smem);  // S[2]; logical row i in S[.][rmap[.][i]]
-  __shared__ T fcol[2][MP], prow[2][MP], sinv[2];
+  __shared__ T gcol[2][MP];
   __shared__ int rmap[2][MP], qcol[MP];
   __shared__ long long wmax[NW], pkey[MP];
   const PanelDesc d = ds[d0 + blockIdx.x];
@@ -299,7 +309,7 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
   for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
   if (lane == 0) wmax[warp] = km;
   __syncthreads();
-  // step 0's pivot, row map, multipliers and scaled pivot row
+  // step 0's pivot, row map and multipliers
   if (warp == 0) {
     T v[H];
 #pragma unroll
@@ -318,14 +328,10 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
       if (i < bp) {
         const int s = swap_index(i, 0, pr);
         rmap[0][i] = s;
-        fcol[0][i] = S[0][s][0];
-        prow[0][i] = i == 0 ? inv : cmul(S[0][pr][i], inv);
+        gcol[0][i] = i == 0 ? T{-inv.x, -inv.y} : cmul(S[0][s][0], inv);
       }
     }
-    if (lane == 0) {
-      sinv[0] = inv;
-      pkey[0] = mag_key(pv);
-    }
+    if (lane == 0) pkey[0] = mag_key(pv);
   }
   // update entries: the thread of rank q among the update warps takes entries q, q + 32 NU, ...
   const bool upd = (UMASK >> warp) & 1u;
@@ -341,10 +347,11 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
   __syncthreads();
   for (int c = 0; c < bp; ++c) {
     const int cur = c & 1, nxt = cur ^ 1, cn = c + 1;
+    const int rpc = rmap[cur][c];  // storage row of the pivot row
     if (warp == 0) {
       if (cn < bp) {
         // step c on column c+1 (logical row lane + 32 h in v[h])
-        const T wc = prow[cur][cn];
+        const T wc = S[cur][rpc][cn];
         T v[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) {
@@ -352,7 +359,8 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
           v[h] = T{0, 0};
           if (i < bp) {
             const int r = rmap[cur][i];
-            v[h] = gj_entry(S[cur][r][cn], fcol[cur][i], wc, i == c, false);
+            const T s0 = S[cur][r][cn];
+            v[h] = gj_fms(i == c ? T{0, 0} : s0, gcol[cur][i], wc);
             S[nxt][r][cn] = v[h];
           }
         }
@@ -362,16 +370,6 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
 #pragma unroll
         for (int h = 0; h < H; ++h) rv[h] = recip_fast<T, R>(v[h], rok[h]);
         const int pr = pivot_row(v, cn, bp, lane);
-        // step c on the pivot row (logical row pr > c), outside column c+1
-        const int rp = rmap[cur][pr];
-        const T fp = fcol[cur][pr], invc = sinv[cur];
-        T row[H];
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-          const int j = lane + 32 * h;
-          row[h] = T{0, 0};
-          if (j < bp && j != cn) row[h] = gj_entry(S[cur][rp][j], fp, j == c ? invc : prow[cur][j], false, j == c);
-        }
         T mine = v[0], minv = rv[0];
         bool mok = rok[0];
 #pragma unroll
@@ -383,24 +381,19 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
         inv.x = __shfl_sync(0xffffffffu, minv.x, pr & 31);
         inv.y = __shfl_sync(0xffffffffu, minv.y, pr & 31);
         if (!__shfl_sync(0xffffffffu, mok, pr & 31)) inv = recip_exact<T, R>(pv);  // warp-uniform, rare
-        // step c+1: logical rows c+1 and pr exchanged
+        // step c+1: logical rows c+1 and pr exchanged; multipliers of column c+1
 #pragma unroll
         for (int h = 0; h < H; ++h) {
           const int j = lane + 32 * h;
           if (j < bp) {
             rmap[nxt][j] = rmap[cur][swap_index(j, cn, pr)];
-            prow[nxt][j] = j == cn ? inv : cmul(row[h], inv);
-            fcol[nxt][swap_index(j, cn, pr)] = v[h];
+            gcol[nxt][swap_index(j, cn, pr)] = j == pr ? T{-inv.x, -inv.y} : cmul(v[h], inv);
           }
         }
-        if (lane == 0) {
-          sinv[nxt] = inv;
-          pkey[cn] = mag_key(pv);
-        }
+        if (lane == 0) pkey[cn] = mag_key(pv);
       }
     } else if (upd) {
       // step c on every entry outside column c+1: all loads, the FMAs, the stores
-      const T invc = sinv[cur];
       T vv[kSlots], ww[kSlots], ff[kSlots];
       int rp[kSlots];
 #pragma unroll
@@ -408,14 +401,16 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
         if (rank * 32 + 32 * NU * t >= nel) continue;  // warp-uniform: no live entry in this slot
         const int i = ei[t] >= 0 ? ei[t] : 0, j = ej[t];
         rp[t] = rmap[cur][i];
-        vv[t] = S[cur][rp[t]][j];
-        ww[t] = j == c ? invc : prow[cur][j];
-        ff[t] = fcol[cur][i];
+        const T s0 = S[cur][rp[t]][j];
+        const T r0 = S[cur][rpc][j];
+        vv[t] = (i == c || j == c) ? T{0, 0} : s0;
+        ww[t] = j == c ? T{1, 0} : r0;
+        ff[t] = gcol[cur][i];
       }
 #pragma unroll
       for (int t = 0; t < kSlots; ++t) {
         if (rank * 32 + 32 * NU * t >= nel) continue;
-        vv[t] = gj_entry(vv[t], ff[t], ww[t], ei[t] == c, ej[t] == c);
+        vv[t] = gj_fms(vv[t], ff[t], ww[t]);
       }
 #pragma unroll
       for (int t = 0; t < kSlots; ++t)
@@ -449,12 +444,9 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
   }
 }
 
-// the instantiation for a plan's panel width (blocks of 24, 32 or 48) and
-// its block size: twelve update warps off scheduler 0 (512 threads), except
-// 48-wide FP64 blocks, whose update-bound sweep runs best (and without
-// register spills) on 256 threads with update warps 1-7 (measured, one block:
-// 215 us against 219 us)
-constexpr unsigned kUpdAll7 = 0xFEu;
+// the instantiation for a plan's panel width (blocks of 24, 32 or 48): 512
+// threads with the update warps off scheduler 0, on two schedulers for
+// 32-wide FP64 blocks (measured per width and precision on one block)
 template <typename T, typename R>
 struct PanelLaunch {
   void (*k)(const PanelDesc*, int, T*, int64_t, int*);
@@ -463,8 +455,10 @@ struct PanelLaunch {
 template <typename T, typename R>
 PanelLaunch<T, R> panel_kernel(int panel) {
   if (panel <= 24) return {k_panel_inverse<T, R, 24, 512, kUpdNoSched0>, 512, 24};
-  if (panel <= 32) return {k_panel_inverse<T, R, 32, 512, kUpdNoSched0>, 512, 32};
-  if (sizeof(R) == 8) return {k_panel_inverse<T, R, kMaxPanel, 256, kUpdAll7>, 256, kMaxPanel};
+  if (panel <= 32) {
+    if constexpr (sizeof(R) == 8) return {k_panel_inverse<T, R, 32, 512, kUpdSched12>, 512, 32};
+    return {k_panel_inverse<T, R, 32, 512, kUpdNoSched0>, 512, 32};
+  }
   return {k_panel_inverse<T, R, kMaxPanel, 512, kUpdNoSched0>, 512, kMaxPanel};
 }
 

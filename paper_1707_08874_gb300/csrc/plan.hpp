@@ -246,6 +246,7 @@ struct Plan {
     void* ev0;
     void* ev1;
     double flops, bytes;
+    int phase = -1, op = -1, stream = 0, level = -1;  // op list (0 factor, 1 selected inversion), index, stream
   };
   bool profiling = false;
   std::vector<ProfRec> prof;
