@@ -490,7 +490,9 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *                        kind (0 zero, 1 assemble, 2 extend-add, 3 panel,
  *                        4 gemm, 5 copy, 6 gather, 7 extract), d0, d1, blocks,
  *                        level, stream, wait, signal, digits per operand of a
- *                        digit GEMM (0 otherwise)
+ *                        digit GEMM (0 otherwise), x0, x1 (a panel op's copy
+ *                        descriptors [x0, x1), run by extra CTAs of its
+ *                        launch; 0, 0 otherwise)
  *   CL_TABLE_GEMM        a, b, c, lda, ldb, ldc, M, N, K, neg, beta,
  *                        rmask[4], cmask[4], trans (bit 0 A, 1 B, 2 C stored
  *                        transposed)

@@ -435,6 +435,10 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
     int maxk = 0;
     for (int i : lv) maxk = std::max(maxk, F[i].k);
     int last_copy = -1;  // op index of the previous step's stream-1 write-back
+    // copies of the previous step's swept entries that the next panel's
+    // products read: launched with the next panel inverses, which read only
+    // their diagonal blocks (disjoint from the copied entries)
+    int pend_x0 = 0, pend_x1 = 0, pend_blocks = 0;
     for (int c0 = 0, step = 0; c0 < maxk; c0 += b, ++step) {
       const int set = step & 1;
       auto tR_of = [&](const FNode& n) { return n.tmp + (int64_t)set * 2 * b * n.nf; };
@@ -461,6 +465,10 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
       }
       pinv.d1 = (int)p.panels.size();
       pinv.blocks = pinv.d1 - pinv.d0;
+      pinv.x0 = pend_x0;
+      pinv.x1 = pend_x1;
+      pinv.xblocks = pend_blocks;
+      pend_x0 = pend_x1 = pend_blocks = 0;
       p.factor_ops.push_back(pinv);
       g1.d1 = (int)p.gemm.size();
       g1.blocks = blk1;
@@ -504,7 +512,11 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
         st.signal = true;
         strips_idx = (int)p.factor_ops.size();
         p.factor_ops.push_back(st);
-        p.factor_ops.push_back(ec);
+        // the copies overwrite entries the strips read (C_old of panel p+1):
+        // they run with the next panel op, after the strips on stream 0
+        pend_x0 = ec.d0;
+        pend_x1 = ec.d1;
+        pend_blocks = ec.blocks;
       }
       // bulk update and write-back of panel p (stream 1)
       Op g2{OP_GEMM, (int)p.gemm.size(), 0, 0, h};

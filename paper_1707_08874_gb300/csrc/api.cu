@@ -171,6 +171,7 @@ void op_work(const Plan& p, const cl::Op& op, int& family, double& flops, double
         flops += 8.0 * bp * bp * bp * B;
         bytes += 2.0 * es * bp * bp * B;
       }
+      for (int d = op.x0; d < op.x1; ++d) bytes += 2.0 * es * p.copies[d].rows * p.copies[d].cols * B;
       break;
     case cl::OP_GEMM:
       family = cl::F_GEMM;
@@ -589,7 +590,8 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
     case CL_TABLE_SELINV_OPS:
       for (const auto& op : table == CL_TABLE_FACTOR_OPS ? p.factor_ops : p.selinv_ops)
         v.insert(v.end(),
-                 {(long long)op.kind, op.d0, op.d1, op.blocks, op.level, op.stream, op.wait, op.signal, op.ndig});
+                 {(long long)op.kind, op.d0, op.d1, op.blocks, op.level, op.stream, op.wait, op.signal, op.ndig,
+                  op.x0, op.x1});
       break;
     case CL_TABLE_SEGMENTS:
       for (const auto& g : p.segs)

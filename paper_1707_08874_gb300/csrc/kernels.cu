@@ -281,10 +281,27 @@ constexpr unsigned kUpdSched12 = 0x6666u;
 // / 168 us against 41.0 / 59.1 / 212 us, FP32 14.3 / 16.4 / 38.9 against
 // 17.4 / 22.4 / 53.3 us).  The row interchanges are undone at the end by
 // reading the columns through the inverse of the final row map.
+//
+// CTAs np, np+1, ... of a launch run copy descriptors [x0, x1) instead (NT /
+// 256 blocks of 256 entries each, xblocks in all): entries that the next
+// products read and that no panel block of the launch holds.
 template <typename T, typename R, int MP, int NT, unsigned UMASK>
-__global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, T* __restrict__ arena,
-                                                      int64_t stride, int* __restrict__ status) {
+__global__ void __launch_bounds__(NT)
+    k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, int np, const CopyDesc* __restrict__ cds, int x0, int x1,
+                    int xblocks, T* __restrict__ arena, int64_t stride, int* __restrict__ status) {
   pdl_enter();
+  if ((int)blockIdx.x >= np) {  // a copy CTA (CTA-uniform: no barrier on this path)
+    const int cb = (NT / 256) * ((int)blockIdx.x - np) + (int)(threadIdx.x >> 8);
+    if (cb >= xblocks) return;
+    const CopyDesc x = cds[find_desc(cds, x0, x1, cb)];
+    const int64_t e = (int64_t)(cb - x.blk0) * 256 + (threadIdx.x & 255);
+    if (e >= (int64_t)x.rows * x.cols) return;
+    const int i = (int)(e / x.cols), j = (int)(e % x.cols);
+    if (x.rmask.hit(i) || x.cmask.hit(j)) return;
+    T* B = arena + blockIdx.y * stride;
+    B[x.dst + (int64_t)i * x.ldd + j] = B[x.src + (int64_t)i * x.lds + j];
+    return;
+  }
   constexpr int NU = bit_count(UMASK);                         // update warps
   constexpr int kSlots = (MP * MP + 32 * NU - 1) / (32 * NU);  // update entries per update thread
   constexpr int H = (MP + 31) / 32;                            // column entries per lane of warp 0
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(NT) k_panel_inverse(const PanelDesc* __restric
 // 32-wide FP64 blocks (measured per width and precision on one block)
 template <typename T, typename R>
 struct PanelLaunch {
-  void (*k)(const PanelDesc*, int, T*, int64_t, int*);
+  void (*k)(const PanelDesc*, int, int, const CopyDesc*, int, int, int, T*, int64_t, int*);
   int threads, block;
 };
 template <typename T, typename R>
@@ -625,9 +642,12 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
       return launch_k(k_extend_add<T>, grid1, dim3(256), 0, st, prio, p.d_extadd, op.d0, op.d1, p.d_maps, arena,
                       stride);
     case OP_PANEL: {
+      // the panel inverses, then CTAs for the copies launched with them
       const PanelLaunch<T, R> pl = panel_kernel<T, R>(p.panel);
-      return launch_k(pl.k, grid1, dim3(pl.threads), panel_smem_bytes<T>(pl.block), st, prio, p.d_panels, op.d0, arena,
-                      stride, p.d_status);
+      const int per = pl.threads / 256;
+      const dim3 grid((unsigned)(op.blocks + (op.xblocks + per - 1) / per), (unsigned)p.fbatch);
+      return launch_k(pl.k, grid, dim3(pl.threads), panel_smem_bytes<T>(pl.block), st, prio, p.d_panels, op.d0,
+                      op.blocks, p.d_copies, op.x0, op.x1, op.xblocks, arena, stride, p.d_status);
     }
     case OP_GEMM:
       return launch_gemm(p, op, arena, st);

@@ -166,6 +166,9 @@ struct Op {
   bool signal = false;
   bool single_chunk = false;  // digit GEMM with every K <= 32: persistent kernel
   int ndig = 0;               // digit GEMM: base-256 digits per operand (3, 7 or 8)
+  // panel op: copy descriptors [x0, x1) (xblocks blocks of 256 entries) run by
+  // extra CTAs of the panel launch, beside the panel inverses
+  int x0 = 0, x1 = 0, xblocks = 0;
   bool pdl = false;           // set at launch: the op's first kernel follows a kernel of its stream directly
 };
 

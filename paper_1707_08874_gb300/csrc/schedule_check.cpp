@@ -68,6 +68,19 @@ struct Tracker {
 };
 
 template <typename R, typename W>
+void copy_footprint(const Plan& p, int d0, int d1, R& visit_read, W& visit_write) {
+  for (int d = d0; d < d1; ++d) {
+    const CopyDesc& x = p.copies[d];
+    for (int i = 0; i < x.rows; ++i)
+      for (int j = 0; j < x.cols; ++j) {
+        if (x.rmask.hit(i) || x.cmask.hit(j)) continue;
+        visit_read(x.src + (int64_t)i * x.lds + j);
+        visit_write(x.dst + (int64_t)i * x.ldd + j);
+      }
+  }
+}
+
+template <typename R, typename W>
 void footprint(const Plan& p, const Op& op, R&& visit_read, W&& visit_write) {
   switch (op.kind) {
     case OP_ZERO:
@@ -102,6 +115,7 @@ void footprint(const Plan& p, const Op& op, R&& visit_read, W&& visit_write) {
             visit_write(x.a + (int64_t)i * x.ld + j);
           }
       }
+      copy_footprint(p, op.x0, op.x1, visit_read, visit_write);  // the copies launched with the panels
       break;
     case OP_GEMM:
       for (int d = op.d0; d < op.d1; ++d) {
@@ -127,15 +141,7 @@ void footprint(const Plan& p, const Op& op, R&& visit_read, W&& visit_write) {
       }
       break;
     case OP_COPY:
-      for (int d = op.d0; d < op.d1; ++d) {
-        const CopyDesc& x = p.copies[d];
-        for (int i = 0; i < x.rows; ++i)
-          for (int j = 0; j < x.cols; ++j) {
-            if (x.rmask.hit(i) || x.cmask.hit(j)) continue;
-            visit_read(x.src + (int64_t)i * x.lds + j);
-            visit_write(x.dst + (int64_t)i * x.ldd + j);
-          }
-      }
+      copy_footprint(p, op.d0, op.d1, visit_read, visit_write);
       break;
     default:
       break;

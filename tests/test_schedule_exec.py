@@ -54,6 +54,15 @@ def _grid(base, rows, cols, ld, trans=False):
     return base + (j * ld + i if trans else i * ld + j)
 
 
+def _copies(A, descs):
+    """(indices, values) of the copy descriptors' unmasked entries."""
+    out = []
+    for src, dst, lds, ldd, rows, cols, *mk in descs:
+        keep = ~_hit(mk[0:4], np.arange(rows))[:, None] & ~_hit(mk[4:8], np.arange(cols))[None, :]
+        out.append((_grid(dst, rows, cols, ldd)[keep], A[_grid(src, rows, cols, lds)][keep]))
+    return out
+
+
 def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_out=None):
     """Run the plan's op lists in order on a host arena.  D: the dense Dirac
     matrix of the one lattice of a single-shape plan, or the list of the dense
@@ -72,7 +81,9 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
             lattices.append((int(sNs), int(sNt), int(V), int(pbase + r * rstride), int(tbase)))
     outs = [dict() for _ in lattices]
     for ops in (t[ph] for ph in phases):
-        for kind, d0, d1, blocks, *_ in ops:
+        for row in ops:
+            kind, d0, d1, blocks = row[:4]
+            x0, x1 = row[9], row[10]
             if blocks == 0 and kind != OP_ZERO:
                 continue
             writes = []  # (indices, values): every descriptor reads the state before the op
@@ -107,6 +118,9 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
                 for a, l, bp, *_ in t["panel"][d0:d1]:
                     idx = _grid(a, bp, bp, l)
                     writes.append((idx, np.linalg.inv(A[idx])))
+                writes += _copies(A, t["copy"][x0:x1])  # launched with the panels
+            elif kind == OP_COPY:
+                writes += _copies(A, t["copy"][d0:d1])
             elif kind == OP_GEMM:
                 for (a, b, c, lda, ldb, ldc, Mg, Ng, Kg, neg, beta, *mk) in t["gemm"][d0:d1]:
                     rm, cm, tr = mk[0:4], mk[4:8], mk[8]
@@ -115,10 +129,6 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
                     val = (A[idx] if beta else 0) + (-P if neg else P)
                     keep = ~_hit(rm, np.arange(Mg))[:, None] & ~_hit(cm, np.arange(Ng))[None, :]
                     writes.append((idx[keep], val[keep]))
-            elif kind == OP_COPY:
-                for src, dst, lds, ldd, rows, cols, *mk in t["copy"][d0:d1]:
-                    keep = ~_hit(mk[0:4], np.arange(rows))[:, None] & ~_hit(mk[4:8], np.arange(cols))[None, :]
-                    writes.append((_grid(dst, rows, cols, ldd)[keep], A[_grid(src, rows, cols, lds)][keep]))
             elif kind == OP_GATHER:
                 for child, parent, nfc, kc, nfp, rs, mp in t["gather"][d0:d1]:
                     I = np.arange(3 * rs)
