@@ -29,3 +29,14 @@ def test_summary_of_synthetic_timeline():
     assert s["root_median_us"]["gemm/stream1"]["launches"] == 1
     assert s["selinv_span_us"] == 51.0 - 42.0
     assert s["total_us"] == 52.0
+
+
+def test_merge_takes_medians():
+    from paper_1707_08874_gb300.trace import merge
+    sums = [summarise([_rec("panel_inverse", 0, 1, 0, 2, 0.0, x), _rec("gemm", 1, 0, 0, 2, x, x + 1.0)])
+            for x in (3.0, 5.0, 4.0)]
+    m = merge(sums)
+    assert m["reps"] == 3
+    assert m["levels"][2]["span_us"] == 4.0 and m["levels"][2]["chain_launches"] == 1
+    assert m["root_median_us"]["panel_inverse/stream0"] == dict(launches=1, median=4.0)
+    assert m["selinv_span_us"] == 1.0 and m["total_us"] == 5.0
