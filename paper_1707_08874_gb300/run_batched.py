@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 
 
 def parse_shapes(text):
@@ -27,6 +28,30 @@ def parse_shapes(text):
         ns, nt = dims.split("x")
         out.append((int(ns), int(nt), int(cnt)))
     return out
+
+
+# BF16 products per FP64-class product of the digit GEMMs: 8 digits per
+# operand (36 products) on the FP64 path, 3 (6 products) for the mixed form's
+# Schur products; the other front precisions do not run on the BF16 pipe
+DIGIT_PRODUCTS = {"fp64_emu": 36, "mixed": 6}
+
+
+def roofline(precision, achieved_tflops):
+    """Achieved front rate against the digit GEMM's ceiling: the measured
+    sustained BF16 rate (MEASURED_PEAKS.json beside the package, else 1700
+    TFLOP/s) over the BF16 products per FP64-class product."""
+    if precision not in DIGIT_PRODUCTS:
+        return None
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            bf16, src = float(json.load(f)["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1700.0, "fallback"
+    peak = bf16 / DIGIT_PRODUCTS[precision]
+    return {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved_tflops / peak,
+            "peak_source": "bf16 sustained %.0f TFLOP/s (%s) / %d products" % (bf16, src, DIGIT_PRODUCTS[precision])}
 
 
 def main(argv=None):
@@ -98,7 +123,8 @@ def main(argv=None):
            "ms_per_step": ms, "evals_per_s": total / (ms / 1e3), "front_tflops": flops / (ms / 1e3) / 1e12,
            "panels": panels, "launches_per_step": sum(p.info["launches_per_eval"] for p in plans),
            "device_gb": sum(p.info["device_bytes"] for p in plans) / 1e9,
-           "workspace_gb": sum(p.info["workspace_bytes"] for p in plans) / 1e9, "per_shape": []}
+           "workspace_gb": sum(p.info["workspace_bytes"] for p in plans) / 1e9,
+           "roofline": roofline(args.precision, flops / (ms / 1e3) / 1e12), "per_shape": []}
     site0 = 0
     for i, (ns, nt, cnt) in enumerate(shapes):
         V = ns ** 3 * nt
