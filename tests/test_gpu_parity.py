@@ -272,6 +272,31 @@ def test_mixed_bf16x3_bound(ns, nt, full_size):
     plan.close()
 
 
+# All-FP32 fronts (CL_MIXED_FP32, a comparison point): stated bound of the
+# normwise G-block and drift errors on 4^4 (seed 1707), about three times the
+# 6e-4 recorded for the default panel width
+FP32_BOUND = 2e-3
+
+
+@pytest.mark.parametrize("panel", [12, 30, 48])
+def test_fp32_fronts_panel_widths(panel):
+    """Every FP32 width instantiation of the panel inverse (24-, 32- and
+    48-wide blocks, with the copies of the swept entries launched beside it)
+    within the FP32 fronts' stated bound, and not FP64-accurate."""
+    B = _binding()
+    U = inputs.random_links(4, 4, seed=1707)
+    ref = oracle.drift_eval(4, 4, U, M, MU)
+    plan = B.Plan.analyze_ex(4, 4, 1, B.CL_MIXED_FP32, panel)
+    assert plan.info["panel"] == panel
+    got, st = _run(plan, U)
+    assert st == B.CL_OK
+    errs = [_blockwise(got[k][0], ref[k]) for k in ("Gdiag", "Gfwd", "Gbwd")]
+    kerr = np.abs(got["Kf"][0] - ref["Kf"]).max() / np.abs(ref["Kf"]).max()
+    assert max(errs) < FP32_BOUND and kerr < FP32_BOUND, (errs, kerr)
+    assert kerr > 1e-9
+    plan.close()
+
+
 @pytest.fixture(scope="module")
 def full_size():
     """8^3 x 4 with the benchmark's links (seed 1707): the oracle's full
