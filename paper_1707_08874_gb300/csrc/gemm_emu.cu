@@ -188,6 +188,16 @@ __device__ __forceinline__ double f2d_scaled(float f, int ex, bool neg) {
                                           ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
+// Two adjacent complex values (32 bytes, 32-byte aligned) in one 256-bit
+// global access: a whole sector per lane
+__device__ __forceinline__ void ld_c2(const double2* p, double2& a, double2& b) {
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a.x), "=d"(a.y), "=d"(b.x), "=d"(b.y) : "l"(p));
+}
+__device__ __forceinline__ void st_c2(double2* p, double2 a, double2 b) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(a.x), "d"(a.y), "d"(b.x), "d"(b.y)
+               : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // tcgen05 building blocks of the digit GEMMs.  Operands reach shared memory by
 // bulk copies of the pre-tiled digit planes; one thread issues BF16 MMAs into
@@ -494,10 +504,21 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
           fe[4 * q] = x.x, fe[4 * q + 1] = x.y, fe[4 * q + 2] = x.z, fe[4 * q + 3] = x.w;
         }
       }
+      // this group's C row segment; untransposed and 32-byte aligned (every
+      // lane of a warp, when ldc is even), it moves two columns per access
+      double2* cseg = crow + CC * grp * cs;
+      const bool wide = !ctr && (reinterpret_cast<uintptr_t>(cseg) & 31u) == 0;
       double2 cv[CC];
       if (row_ok && g.beta) {
 #pragma unroll
-        for (int jj = 0; jj < CC; ++jj) cv[jj] = c8 + jj < g.N ? crow[(CC * grp + jj) * cs] : make_double2(0, 0);
+        for (int jj = 0; jj < CC; jj += 2) {
+          if (wide && c8 + jj + 1 < g.N) {
+            ld_c2(cseg + jj, cv[jj], cv[jj + 1]);
+          } else {
+            cv[jj] = c8 + jj < g.N ? cseg[jj * cs] : make_double2(0, 0);
+            cv[jj + 1] = c8 + jj + 1 < g.N ? cseg[(jj + 1) * cs] : make_double2(0, 0);
+          }
+        }
       }
       const int s = i & 1, u = i >> 1;
       const bool got = mbar_wait_ab(bar(5 + s), u & 1, abort_flag, wait_ns);
@@ -561,21 +582,31 @@ __global__ void __launch_bounds__(64 + 128 * NG, 1)
         mbar_arrive(bar(7 + s));  // this group is done with accumulator set s
         if (!row_ok) continue;
 #pragma unroll
-        for (int jj = 0; jj < CC; ++jj) {
-          const int cc = c8 + jj;
-          if (cc >= g.N || g.cmask.hit(cc)) continue;
-          const int ex = erow + fe[jj];
-          double vv[2];
+        for (int jj = 0; jj < CC; jj += 2) {
+          double2 vp[2];
+          bool okc[2];
 #pragma unroll
-          for (int part = 0; part < 2; ++part) {
-            const int k = 2 * jj + part;
-            float s1, e1;
-            two_sum(h[k], mi[k], s1, e1);
-            vv[part] = f2d_scaled(s1, ex, neg) + f2d_scaled(e1 + lo[k], ex, neg);
+          for (int q = 0; q < 2; ++q) {
+            const int j2 = jj + q, cc = c8 + j2;
+            okc[q] = cc < g.N && !g.cmask.hit(cc);
+            const int ex = erow + fe[j2];
+            double vv[2];
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+              const int k = 2 * j2 + part;
+              float s1, e1;
+              two_sum(h[k], mi[k], s1, e1);
+              vv[part] = f2d_scaled(s1, ex, neg) + f2d_scaled(e1 + lo[k], ex, neg);
+            }
+            vp[q] = make_double2(vv[0], vv[1]);
+            if (g.beta) vp[q] = cadd(vp[q], cv[j2]);
           }
-          double2 v = make_double2(vv[0], vv[1]);
-          if (g.beta) v = cadd(v, cv[jj]);
-          crow[(CC * hh + jj) * cs] = v;
+          if (wide && okc[0] && okc[1]) {
+            st_c2(cseg + jj, vp[0], vp[1]);
+          } else {
+            if (okc[0]) cseg[jj * cs] = vp[0];
+            if (okc[1]) cseg[(jj + 1) * cs] = vp[1];
+          }
         }
       }
     }
