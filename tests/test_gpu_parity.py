@@ -272,6 +272,26 @@ def test_mixed_bf16x3_bound(ns, nt, full_size):
     plan.close()
 
 
+def test_fp64_emu_seed_sweep():
+    """The 1e-10 bar over twenty 4^4 link configurations (seeds 90-109, kappa
+    up to ~1e4): the FP64 path's error depends on the pivot sequence that the
+    links induce, so a single configuration is not enough evidence."""
+    B = _binding()
+    worst = 0.0
+    for seed in range(90, 110):
+        U = inputs.random_links(4, 4, seed=seed)
+        ref = oracle.drift_eval(4, 4, U, M, MU)
+        plan = B.Plan.analyze(4, 4, 1, B.CL_FP64_EMU)
+        got, st = _run(plan, U)
+        plan.close()
+        assert st == B.CL_OK, seed
+        err = max(_blockwise(got[k][0], ref[k]) for k in ("Gdiag", "Gfwd", "Gbwd"))
+        kerr = np.abs(got["Kf"][0] - ref["Kf"]).max() / np.abs(ref["Kf"]).max()
+        assert err < BAR and kerr < BAR, (seed, err, kerr)
+        worst = max(worst, err, kerr)
+    assert worst > 0.0
+
+
 # All-FP32 fronts (CL_MIXED_FP32, a comparison point): stated bound of the
 # normwise G-block and drift errors on 4^4 (seed 1707), about three times the
 # 6e-4 recorded for the default panel width
