@@ -432,6 +432,21 @@ int cl_zgemm_emu(int M, int N, int K, const double* A, int lda, const double* B,
 int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail);
 
 /*
+ * cl_plan_pivot_growth -- synchronises `stream` and returns in *growth the
+ * largest pivot growth of the latest factorisation's panel blocks:
+ * max |entry| / min |pivot| of each Gauss-Jordan block (magnitudes as
+ * max(|re|, |im|); +inf for a zero pivot; 0 before any factorisation).
+ * Pivoting is partial within each panel of a supernode (static across
+ * panels, Sec. 3), so an ill-conditioned panel block amplifies the rounding
+ * of everything updated through it: on 8^3x4 lattices (m = 0.05, mu = 0.25)
+ * configurations whose growth reaches ~1e3 may miss a 1e-10 relative
+ * accuracy of the FP64 path.  Reset by every factorisation (cl_factor,
+ * cl_drift_eval); not cleared by cl_get_status.  CL_ERR_INVALID_ARG for a
+ * symbolic plan or a null pointer.
+ */
+int cl_plan_pivot_growth(cl_plan* plan, cudaStream_t stream, double* growth);
+
+/*
  * cl_plan_set_wait_limit -- limit of the waits of the tensor-core GEMM roles
  * (producer, MMA issuer, fold warps) for a later launch of this plan's
  * compute calls: seconds in [0, 0.5]; a negative value restores the default

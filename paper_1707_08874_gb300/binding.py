@@ -82,7 +82,7 @@ def obs_dict(row) -> dict:
 
 EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks", "cl_fermion_drift",
            "cl_drift_eval", "cl_get_status", "cl_plan_get_info", "cl_plan_get_node", "cl_profile_enable",
-           "cl_profile_read", "cl_profile_trace", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
+           "cl_profile_read", "cl_profile_trace", "cl_plan_pivot_growth", "cl_measure_peak", "cl_drift_eval_noalloc", "cl_gauge_drift", "cl_link_update", "cl_gauge_cool",
            "cl_observables", "cl_langevin_step", "cl_analyze_ex", "cl_group_create", "cl_group_drift_eval",
            "cl_group_capture", "cl_group_launch", "cl_group_destroy", "cl_destroy_plan", "cl_error_string",
            "cl_zgemm_emu_workspace", "cl_zgemm_emu", "cl_plan_check_schedule",
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True):
     L.cl_profile_enable.argtypes = [P, I]
     L.cl_profile_read.argtypes = [P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(I)]
     L.cl_profile_trace.argtypes = [P, ctypes.POINTER(TraceEntry), I, ctypes.POINTER(I)]
+    L.cl_plan_pivot_growth.argtypes = [P, P, ctypes.POINTER(D)]
     L.cl_measure_peak.argtypes = [I, ctypes.POINTER(D)]
     L.cl_drift_eval_noalloc.argtypes = [I, I, P, D, D, D, P, P, P, P, P]
     L.cl_gauge_drift.argtypes = [P, P, D, P, P]
@@ -417,6 +418,13 @@ class Plan:
         _check(load().cl_profile_read(self._h, buf, 16, ctypes.byref(n)), "cl_profile_read")
         return {buf[i].name.decode(): dict(launches=buf[i].launches, total_ms=buf[i].total_ms,
                                            flops=buf[i].flops, bytes=buf[i].bytes) for i in range(n.value)}
+
+    def pivot_growth(self, stream=None) -> float:
+        """cl_plan_pivot_growth: the largest max|entry| / min|pivot| over the
+        panel blocks of the latest factorisation."""
+        g = ctypes.c_double()
+        _check(load().cl_plan_pivot_growth(self._h, _stream(stream), ctypes.byref(g)), "cl_plan_pivot_growth")
+        return g.value
 
     def profile_trace(self) -> list:
         """Per-launch timeline of the profiled calls since profile_enable: one

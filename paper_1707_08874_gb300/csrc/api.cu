@@ -237,6 +237,10 @@ int run_ops(Plan& p, const std::vector<cl::Op>& ops, const double* links, double
   T* arena = static_cast<T*>(p.d_arena);
   const int phase = &ops == &p.factor_ops ? 0 : 1;
   const bool two = phase == 0 && p.streams[1] != nullptr;
+  if (phase == 0) {  // the pivot growth word describes the latest factorisation
+    const cudaError_t e0 = cudaMemsetAsync(p.d_status + 3, 0, sizeof(int), st);
+    if (e0 != cudaSuccess) return cuda_status(e0);
+  }
   // an op's first kernel may launch programmatically (overlapping its
   // predecessor's tail) only when it directly follows a kernel of this op list
   // on its stream, with no event wait in between
@@ -516,7 +520,7 @@ int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail) {
   int h[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h, plan->p.d_status, sizeof(h), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(plan->p.d_status, 0, sizeof(h), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->p.d_status, 0, 3 * sizeof(int), stream);  // not the growth word
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_status(e);
   *info = h[0];
@@ -524,6 +528,18 @@ int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail) {
     detail[0] = h[0] ? h[1] : -1;
     detail[1] = h[0] ? h[2] : -1;
   }
+  return CL_OK;
+}
+
+int cl_plan_pivot_growth(cl_plan* plan, cudaStream_t stream, double* growth) {
+  if (!compute_ready(plan) || !growth) return CL_ERR_INVALID_ARG;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, plan->p.d_status + 3, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  float f;
+  std::memcpy(&f, &h, sizeof(f));
+  *growth = (double)f;
   return CL_OK;
 }
 

@@ -135,7 +135,8 @@ __device__ __forceinline__ int find_desc(const D* __restrict__ ds, int d0, int d
   return lo;
 }
 
-// status word: [0] code, [1] supernode, [2] column
+// status word: [0] code, [1] supernode, [2] column; [3] the largest pivot
+// growth of the factorisation's panel blocks (float bits, see k_panel_inverse)
 __device__ __forceinline__ void set_status(int* st, int code, int a, int b) {
   if (atomicCAS(st, 0, code) == 0) {
     st[1] = a;

@@ -452,11 +452,24 @@ __global__ void __launch_bounds__(NT)
     // infinity's) is reported as non-finite, not as a tiny pivot
     const long long inf_key = sizeof(R) == 8 ? 0x7FF0000000000000ll : 0x7F800000ll;
     int bad = 0x7fffffff;
-    for (int c = lane; c < bp; c += 32)
+    long long pmin = 0x7FFFFFFFFFFFFFFFll;
+    for (int c = lane; c < bp; c += 32) {
       if (pkey[c] < thr || pkey[c] == 0) bad = min(bad, c);
+      pmin = min(pmin, pkey[c]);
+    }
     bad = __reduce_min_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
     if (lane == 0 && m >= inf_key) set_status(status, CL_ERR_NONFINITE, d.node, d.col0);
     else if (lane == 0 && bad != 0x7fffffff) set_status(status, CL_ERR_SINGULAR, d.node, d.col0 + bad);
+    // pivot growth of the block: max |entry| / min |pivot| (magnitudes as
+    // max(|re|, |im|)), kept as the largest over the factorisation in status[3]
+    // (non-negative float bits order like the floats; a zero pivot gives +inf)
+    if (lane == 0 && m < inf_key) {
+      const double mv = key_value(m, R(0)), pv = key_value(pmin, R(0));
+      const float ratio = pv > 0.0 ? (float)(mv / pv) : __int_as_float(0x7F800000);
+      atomicMax(status + 3, __float_as_int(ratio));
+    }
   }
   __syncthreads();
   for (int e = tid; e < nel; e += NT) {

@@ -215,7 +215,7 @@ struct Plan {
   int64_t vec_elems = 0;  // complex elements of one front-vector workspace per noise vector and replica
   // device memory
   void* d_arena = nullptr;       // batch * arena_elems complex (precision-dependent)
-  int* d_status = nullptr;       // [4]: code, node, column, spare
+  int* d_status = nullptr;       // [4]: code, node, column, pivot growth (float bits)
   int64_t* d_off = nullptr;      // off_diag | off_fwd | off_bwd
   int* d_ld = nullptr;           // ld_diag | ld_fwd | ld_bwd
   int* d_maps = nullptr;
