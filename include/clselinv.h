@@ -436,13 +436,15 @@ int cl_get_status(cl_plan* plan, cudaStream_t stream, int* info, int* detail);
  * largest pivot growth of the latest factorisation's panel blocks:
  * max |entry| / min |pivot| of each Gauss-Jordan block (magnitudes as
  * max(|re|, |im|); +inf for a zero pivot; 0 before any factorisation).
- * Pivoting is partial within each panel of a supernode (static across
- * panels, Sec. 3), so an ill-conditioned panel block amplifies the rounding
- * of everything updated through it: on 8^3x4 lattices (m = 0.05, mu = 0.25)
- * configurations whose growth reaches ~1e3 may miss a 1e-10 relative
- * accuracy of the FP64 path.  Reset by every factorisation (cl_factor,
- * cl_drift_eval); not cleared by cl_get_status.  CL_ERR_INVALID_ARG for a
- * symbolic plan or a null pointer.
+ * Pivots are chosen among the rows of a panel and of the next panel of its
+ * supernode (static across supernodes, Sec. 3); a large growth means an
+ * ill-conditioned pivot block that amplifies the rounding of everything
+ * updated through it (on 8^3x4 lattices, m = 0.05, mu = 0.25: growths of
+ * 11-62 over twenty configurations, errors of the FP64 path <= 2e-11; with
+ * pivots restricted to each panel the growth reached ~1e3 and the error
+ * 1.6e-9).  Reset by every factorisation (cl_factor, cl_drift_eval); not
+ * cleared by cl_get_status.  CL_ERR_INVALID_ARG for a symbolic plan or a
+ * null pointer.
  */
 int cl_plan_pivot_growth(cl_plan* plan, cudaStream_t stream, double* growth);
 
@@ -500,10 +502,13 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  * NULL only *count (the number of int64 values) is set; otherwise out must
  * hold cap >= *count values.  Row layouts:
  *   CL_TABLE_META        Ns, Nt, V, N, precision, panel, pool_elems,
- *                        tmp_elems, arena_elems, n_levels
+ *                        tmp_elems, arena_elems, n_levels, perm_ints (the
+ *                        permutation workspace per replica, ints)
  *   CL_TABLE_FACTOR_OPS, CL_TABLE_SELINV_OPS
  *                        kind (0 zero, 1 assemble, 2 extend-add, 3 panel,
- *                        4 gemm, 5 copy, 6 gather, 7 extract), d0, d1, blocks,
+ *                        4 gemm, 5 copy, 6 gather, 7 extract, 8 row swap of
+ *                        the panels [d0, d1), 9 column un-permutation),
+ *                        d0, d1, blocks,
  *                        level, stream, wait, signal, digits per operand of a
  *                        digit GEMM (0 otherwise), x0, x1 (a panel op's copy
  *                        descriptors [x0, x1), run by extra CTAs of its
@@ -511,7 +516,11 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *   CL_TABLE_GEMM        a, b, c, lda, ldb, ldc, M, N, K, neg, beta,
  *                        rmask[4], cmask[4], trans (bit 0 A, 1 B, 2 C stored
  *                        transposed)
- *   CL_TABLE_PANEL       a, ld, bp, node, col0
+ *   CL_TABLE_PANEL       a, ld, bp, node, col0, nc (candidate pivot rows: this
+ *                        panel's and the next panel's of the supernode),
+ *                        lperm, pi (offsets in the permutation workspace of
+ *                        the panel's row permutation and of the supernode's
+ *                        running one), swap_blk0
  *   CL_TABLE_COPY        src, dst, lds, ldd, rows, cols, rmask[4], cmask[4]
  *   CL_TABLE_EXTADD      parent, nfp, nchild, child[2], nfc[2], kc[2], map[2]
  *   CL_TABLE_GATHER      child, parent, nfc, kc, nfp, rs, map
@@ -527,9 +536,12 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *   CL_TABLE_VNODES      fronts of the row-vector solves (cl_left_solve), by
  *                        level: front, vec, parent_vec, nf, k, r, level,
  *                        nchild, child_vec[2], child_k[2], ea_map[2], ga_map,
- *                        site0 (vector offsets in complex elements per noise
- *                        vector; parent_vec -1 at a root)
+ *                        site0, pan0, npan (vector offsets in complex
+ *                        elements per noise vector; parent_vec -1 at a root)
  *   CL_TABLE_VSITES      separator sites of those fronts (front order)
+ *   CL_TABLE_UNPERM      per supernode of an un-permutation op: front, nf, k,
+ *                        pan0, npan (its panels in CL_TABLE_NODE_PANELS), blk0
+ *   CL_TABLE_NODE_PANELS panel indices grouped by supernode, in step order
  * Offsets are elements of one replica's arena; a mask [r0, r1, r2, r3]
  * excludes the indices in [r0, r1) and [r2, r3).  Works on symbolic plans.
  */
@@ -547,7 +559,9 @@ enum {
   CL_TABLE_LD = 10,
   CL_TABLE_SEGMENTS = 11,
   CL_TABLE_VNODES = 12,
-  CL_TABLE_VSITES = 13
+  CL_TABLE_VSITES = 13,
+  CL_TABLE_UNPERM = 14,
+  CL_TABLE_NODE_PANELS = 15
 };
 int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count);
 

@@ -91,9 +91,10 @@ EXPORTS = ["cl_analyze", "cl_analyze_symbolic", "cl_factor", "cl_selinv_blocks",
            "cl_stochastic_drift"]
 
 # cl_plan_export tables (include/clselinv.h) and their int64 row widths
-TABLES = {"meta": (0, 10), "factor_ops": (1, 11), "selinv_ops": (2, 11), "gemm": (3, 20), "panel": (4, 5),
+TABLES = {"meta": (0, 11), "factor_ops": (1, 11), "selinv_ops": (2, 11), "gemm": (3, 20), "panel": (4, 9),
           "copy": (5, 14), "extadd": (6, 11), "gather": (7, 7), "maps": (8, 1), "off": (9, 1), "ld": (10, 1),
-          "segments": (11, 8), "vnodes": (12, 16), "vsites": (13, 1)}
+          "segments": (11, 8), "vnodes": (12, 18), "vsites": (13, 1), "unperm": (14, 6),
+          "node_panels": (15, 1)}
 
 
 def lib_path() -> str:

@@ -393,6 +393,16 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
     return (int)(((int64_t)rows * cols + 255) / 256);
   };
 
+  // permutation workspace: per node its running row permutation (k ints),
+  // then per panel its local permutation of the candidate rows (nc ints)
+  p.unperm.clear();
+  int64_t perm_ints = 0;
+  std::vector<int> pi_off(nn);
+  for (int i = 0; i < nn; ++i) {
+    pi_off[i] = (int)perm_ints;
+    perm_ints += F[i].k;
+  }
+
   p.factor_ops.push_back(Op{OP_ZERO, 0, 0, 0, -1});
   int assemble_blocks = 0;
   for (const Segment& sg : p.segs) assemble_blocks = std::max(assemble_blocks, (4 * sg.V + 127) / 128);
@@ -446,12 +456,17 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
       Op pinv{OP_PANEL, (int)p.panels.size(), 0, 0, h};
       Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
       g1.ndig = nd_panel;
-      int blk1 = 0;
+      int blk1 = 0, blk_sw = 0;
       for (int i : lv) {
         const FNode& n = F[i];
         if (c0 >= n.k) continue;
         const int bp = std::min(b, n.k - c0);
-        p.panels.push_back(PanelDesc{n.off + (int64_t)c0 * n.nf + c0, n.nf, bp, i, c0});
+        // pivots among the rows of this panel and of the next one in the supernode
+        const int nc = std::min(bp + b, n.k - c0);
+        PanelDesc pd{n.off + (int64_t)c0 * n.nf + c0, n.nf, bp, i, c0, nc, (int)perm_ints, pi_off[i], blk_sw};
+        perm_ints += nc;
+        if (nc > bp) blk_sw += (n.nf + kSwapCols - 1) / kSwapCols;  // rows from the next panel may come in
+        p.panels.push_back(pd);
         if (n.nf == bp) continue;  // nothing outside the panel
         // TR = Y * R_old (bp x nf), TC = -C_old * Y (nf x bp)
         if (tr_short)  // TR^T = R_old^T Y^T
@@ -470,6 +485,14 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
       pinv.xblocks = pend_blocks;
       pend_x0 = pend_x1 = pend_blocks = 0;
       p.factor_ops.push_back(pinv);
+      // the panel's row permutation applied to the columns outside the panel
+      // (the rows of the next panel still receive the previous step's bulk
+      // update and write-back on stream 1: wait for them)
+      if (blk_sw > 0) {
+        Op sw{OP_SWAP, pinv.d0, pinv.d1, blk_sw, h};
+        sw.wait = last_copy;
+        p.factor_ops.push_back(sw);
+      }
       g1.d1 = (int)p.gemm.size();
       g1.blocks = blk1;
       if (g1.d1 == g1.d0) continue;
@@ -556,8 +579,36 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
   std::vector<int> parent(nn, -1);
   for (int i = 0; i < nn; ++i)
     for (int q = 0; q < F[i].nchild; ++q) parent[F[i].child[q]] = i;
+  // columns of the level's pivot rows back in the supernodes' original order,
+  // once the level's G is complete (before the level below gathers from it)
+  // each supernode's panels in step order
+  std::vector<int> pan0(nn, 0), npan(nn, 0);
+  {
+    std::vector<std::vector<int>> by_node(nn);
+    for (int d = 0; d < (int)p.panels.size(); ++d) by_node[p.panels[d].node].push_back(d);
+    p.node_panels.clear();
+    for (int i = 0; i < nn; ++i) {
+      pan0[i] = (int)p.node_panels.size();
+      npan[i] = (int)by_node[i].size();
+      p.node_panels.insert(p.node_panels.end(), by_node[i].begin(), by_node[i].end());
+    }
+  }
+  auto push_unperm = [&](int h) {
+    Op up{OP_UNPERM, (int)p.unperm.size(), 0, 0, h};
+    int blk = 0;
+    for (int i : by_level[h]) {
+      const FNode& n = F[i];
+      if (n.k == 0) continue;
+      p.unperm.push_back(UnpermDesc{n.off, n.nf, n.k, pan0[i], npan[i], blk});
+      blk += (n.nf + kUnpermRows - 1) / kUnpermRows;
+    }
+    up.d1 = (int)p.unperm.size();
+    up.blocks = blk;
+    if (blk > 0) p.selinv_ops.push_back(up);
+  };
   for (int h = n_levels - 1; h >= 0; --h) {
     const auto& lv = by_level[h];
+    if (h == n_levels - 1) push_unperm(h);  // the root level's G is the factorisation's inverse
     Op ga{OP_GATHER, (int)p.gather.size(), 0, 0, h};
     int blk = 0;
     for (int i : lv) {
@@ -570,7 +621,10 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
     }
     ga.d1 = (int)p.gather.size();
     ga.blocks = blk;
-    if (ga.d1 == ga.d0) continue;
+    if (ga.d1 == ga.d0) {  // only roots on this level (their G is the factorisation's inverse)
+      if (h != n_levels - 1) push_unperm(h);
+      continue;
+    }
     p.selinv_ops.push_back(ga);
     Op g1{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
     g1.ndig = nd_offdiag;
@@ -606,8 +660,10 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
     cp.blocks = blk3;
     p.selinv_ops.push_back(g2);
     p.selinv_ops.push_back(cp);
+    push_unperm(h);
   }
   p.selinv_ops.push_back(Op{OP_EXTRACT, 0, 0, assemble_blocks, -1});
+  p.perm_ints = perm_ints;
 
   // row-vector solves (stochastic estimator): nodes by level, front-vector
   // workspace offsets, CTA offsets of the level launches (128 elements per CTA)
@@ -636,6 +692,8 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
         x.r = n.r;
         x.level = h;
         x.nchild = n.nchild;
+        x.pan0 = pan0[i];
+        x.npan = npan[i];
         for (int q = 0; q < 2; ++q) {
           x.child_vec[q] = q < n.nchild ? vec[n.child[q]] : -1;
           x.child_k[q] = q < n.nchild ? F[n.child[q]].k : 0;

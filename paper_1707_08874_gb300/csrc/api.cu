@@ -38,6 +38,9 @@ void free_device(Plan& p) {
   cudaFree(p.d_maps);
   cudaFree(p.d_gemm);
   cudaFree(p.d_panels);
+  cudaFree(p.d_unperm);
+  cudaFree(p.d_node_panels);
+  cudaFree(p.d_perm);
   cudaFree(p.d_copies);
   cudaFree(p.d_extadd);
   cudaFree(p.d_gather);
@@ -86,6 +89,10 @@ int setup_device(Plan& p) {
       (e = upload(p.d_maps, p.maps.data(), p.maps.size() * sizeof(int), total)) != cudaSuccess ||
       (e = upload(p.d_gemm, p.gemm.data(), p.gemm.size() * sizeof(cl::GemmDesc), total)) != cudaSuccess ||
       (e = upload(p.d_panels, p.panels.data(), p.panels.size() * sizeof(cl::PanelDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_unperm, p.unperm.data(), p.unperm.size() * sizeof(cl::UnpermDesc), total)) != cudaSuccess ||
+      (e = upload(p.d_node_panels, p.node_panels.data(), p.node_panels.size() * sizeof(int), total)) !=
+          cudaSuccess ||
+      (e = upload(p.d_perm, nullptr, (size_t)p.perm_ints * p.fbatch * sizeof(int), total)) != cudaSuccess ||
       (e = upload(p.d_copies, p.copies.data(), p.copies.size() * sizeof(cl::CopyDesc), total)) != cudaSuccess ||
       (e = upload(p.d_extadd, p.extadd.data(), p.extadd.size() * sizeof(cl::ExtAddDesc), total)) != cudaSuccess ||
       (e = upload(p.d_gather, p.gather.data(), p.gather.size() * sizeof(cl::GatherDesc), total)) != cudaSuccess ||
@@ -190,6 +197,15 @@ void op_work(const Plan& p, const cl::Op& op, int& family, double& flops, double
       for (int d = op.d0; d < op.d1; ++d) bytes += 2.0 * es * 9.0 * p.gather[d].rs * p.gather[d].rs * B;
       break;
     case cl::OP_EXTRACT: family = cl::F_EXTRACT; bytes = sites * 9 * 9 * (es + 16.0); break;
+    case cl::OP_SWAP:  // row exchanges of the cross-panel pivoting (counted with the copies)
+      family = cl::F_COPY;
+      for (int d = op.d0; d < op.d1; ++d)
+        if (p.panels[d].nc > p.panels[d].bp) bytes += 2.0 * es * p.panels[d].nc * p.panels[d].ld * B;
+      break;
+    case cl::OP_UNPERM:
+      family = cl::F_COPY;
+      for (int d = op.d0; d < op.d1; ++d) bytes += 2.0 * es * p.unperm[d].nf * p.unperm[d].k * B;
+      break;
   }
 }
 
@@ -594,13 +610,14 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
 }
 
 int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap, long long* count) {
-  if (!plan || !count || table < 0 || table > CL_TABLE_VSITES) return CL_ERR_INVALID_ARG;
+  if (!plan || !count || table < 0 || table > CL_TABLE_NODE_PANELS) return CL_ERR_INVALID_ARG;
   const cl::Plan& p = plan->p;
   std::vector<long long> v;
   auto mask = [&v](const cl::Mask2& m) { v.insert(v.end(), {m.r0, m.r1, m.r2, m.r3}); };
   switch (table) {
     case CL_TABLE_META:
-      v = {p.Ns, p.Nt, p.V, p.N, p.precision, p.panel, p.pool_elems, p.tmp_elems, p.arena_elems, p.n_levels};
+      v = {p.Ns, p.Nt, p.V, p.N, p.precision, p.panel, p.pool_elems, p.tmp_elems, p.arena_elems, p.n_levels,
+           p.perm_ints};
       break;
     case CL_TABLE_FACTOR_OPS:
     case CL_TABLE_SELINV_OPS:
@@ -616,7 +633,8 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
     case CL_TABLE_VNODES:
       for (const auto& x : p.vnodes)
         v.insert(v.end(), {x.front, x.vec, x.parent_vec, x.nf, x.k, x.r, x.level, x.nchild, x.child_vec[0],
-                           x.child_vec[1], x.child_k[0], x.child_k[1], x.ea_map[0], x.ea_map[1], x.ga_map, x.site0});
+                           x.child_vec[1], x.child_k[0], x.child_k[1], x.ea_map[0], x.ea_map[1], x.ga_map, x.site0,
+                           x.pan0, x.npan});
       break;
     case CL_TABLE_VSITES:
       v.assign(p.vsites.begin(), p.vsites.end());
@@ -630,7 +648,14 @@ int cl_plan_export(const cl_plan* plan, int table, long long* out, long long cap
       }
       break;
     case CL_TABLE_PANEL:
-      for (const auto& d : p.panels) v.insert(v.end(), {d.a, d.ld, d.bp, d.node, d.col0});
+      for (const auto& d : p.panels)
+        v.insert(v.end(), {d.a, d.ld, d.bp, d.node, d.col0, d.nc, d.lperm, d.pi, d.swap_blk0});
+      break;
+    case CL_TABLE_UNPERM:
+      for (const auto& d : p.unperm) v.insert(v.end(), {d.front, d.nf, d.k, d.pan0, d.npan, d.blk0});
+      break;
+    case CL_TABLE_NODE_PANELS:
+      v.assign(p.node_panels.begin(), p.node_panels.end());
       break;
     case CL_TABLE_COPY:
       for (const auto& d : p.copies) {

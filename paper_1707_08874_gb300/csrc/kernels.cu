@@ -116,9 +116,13 @@ __global__ void k_gather(const GatherDesc* __restrict__ ds, int d0, int d1, cons
 }
 
 // ---------------------------------------------------------------------------
-// In-place inverse of one diagonal panel block (bp <= kMaxPanel) by
-// Gauss-Jordan elimination with partial (row) pivoting inside the panel; the
-// row interchanges are undone on the columns at the end.  Pivots are chosen by
+// Pivot panel of a supernode (bp <= kMaxPanel): its bp pivot rows are chosen
+// among the rows of the panel and of the next panel of the supernode (partial
+// pivoting on their panel columns), and the block of the chosen rows is
+// inverted in place by Gauss-Jordan elimination with partial (row) pivoting
+// inside it; those inner row interchanges are undone on the columns at the
+// end, the exchange of rows between the two panels is kept (the row swap and
+// the un-permutation after the selected inversion apply it).  Pivots are chosen by
 // max(|re|, |im|), compared through the leading 32 bits of the ordered bit
 // pattern of the absolute value (ties: the lowest row); a pivot below
 // 1e-13 * max|block| (1e-6 for FP32 fronts) records CL_ERR_SINGULAR
@@ -252,7 +256,9 @@ __device__ __forceinline__ int swap_index(int i, int a, int b) { return i == a ?
 
 template <typename T>
 constexpr size_t panel_smem_bytes(int mp) {
-  return 2 * (size_t)mp * (mp + 1) * sizeof(T);
+  // the block's two copies, then the candidate rows' panel columns (up to
+  // 2 mp rows) in the front's precision and as float2 for the pivot choice
+  return 2 * (size_t)mp * (mp + 1) * sizeof(T) + 2 * (size_t)mp * mp * (sizeof(T) + sizeof(float2));
 }
 
 __host__ __device__ constexpr int bit_count(unsigned m) { return m ? (int)(m & 1u) + bit_count(m >> 1) : 0; }
@@ -292,7 +298,8 @@ constexpr unsigned kUpdSched12 = 0x6666u;
 template <typename T, typename R, int MP, int NT, unsigned UMASK>
 __global__ void __launch_bounds__(NT)
     k_panel_inverse(const PanelDesc* __restrict__ ds, int d0, int np, const CopyDesc* __restrict__ cds, int x0, int x1,
-                    int xblocks, T* __restrict__ arena, int64_t stride, int* __restrict__ status) {
+                    int xblocks, T* __restrict__ arena, int64_t stride, int* __restrict__ perm, int64_t perm_stride,
+                    int* __restrict__ status) {
   pdl_enter();
   if ((int)blockIdx.x >= np) {  // a copy CTA (CTA-uniform: no barrier on this path)
     const int cb = (NT / 256) * ((int)blockIdx.x - np) + (int)(threadIdx.x >> 8);
@@ -316,13 +323,91 @@ __global__ void __launch_bounds__(NT)
   __shared__ T gcol[2][MP];
   __shared__ int rmap[2][MP], qcol[MP];
   __shared__ long long wmax[NW], pkey[MP];
+  T(*Tc)[MP] = reinterpret_cast<T(*)[MP]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1));  // candidate rows
+  float2(*Tf)[MP] = reinterpret_cast<float2(*)[MP]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1) +
+                                                    2 * sizeof(T) * MP * MP);
+  __shared__ int lpl[2 * MP], chosen[MP];   // nc <= 2 MP candidate rows
+  __shared__ float cmul_f[4 * MP];          // (re, im) multiplier per candidate row
+  __shared__ unsigned char alive[2 * MP];
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
   const int bp = d.bp, nel = bp * bp, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nc = d.nc;  // candidate rows: this panel's and the next panel's
+  // Pivot rows.  Partial pivoting over the nc candidate rows of the panel's
+  // columns chooses bp of them (in FP32: only the choice is taken from it);
+  // the chosen rows of the panel keep their positions, the chosen rows of the
+  // next panel take the positions of the panel rows left out, which move to
+  // theirs (position i then holds candidate row lpl[i]).  The block inverted
+  // below is that of the chosen rows.
+  for (int e = tid; e < nc * bp; e += NT) {
+    const int i = e / bp, j = e - i * bp;
+    const T v = A[(int64_t)i * d.ld + j];
+    Tc[i][j] = v;
+    Tf[i][j] = make_float2((float)v.x, (float)v.y);
+  }
+  for (int i = tid; i < nc; i += NT) {
+    lpl[i] = i;
+    alive[i] = 1;
+  }
+  __syncthreads();
+  if (nc > bp) {
+    for (int c = 0; c < bp; ++c) {
+      if (warp == 0) {  // the largest remaining entry of column c (max(|re|, |im|); ties: the lowest row)
+        unsigned key = 0;
+        int bi = 0x7fffffff;
+        for (int r = lane; r < nc; r += 32) {
+          if (!alive[r]) continue;
+          const unsigned k2 = max(__float_as_uint(fabsf(Tf[r][c].x)), __float_as_uint(fabsf(Tf[r][c].y)));
+          if (bi == 0x7fffffff || k2 > key) key = k2, bi = r;
+        }
+        const unsigned kmx = __reduce_max_sync(0xffffffffu, bi != 0x7fffffff ? key : 0u);
+        const int pr = (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && key == kmx) ? (unsigned)bi : 0x7fffffffu);
+        if (lane == 0) {
+          chosen[c] = pr;
+          alive[pr] = 0;
+        }
+      }
+      __syncthreads();
+      const int pr = chosen[c];
+      const float2 pv = Tf[pr][c];
+      const float n2 = pv.x * pv.x + pv.y * pv.y;
+      for (int r = tid; r < nc; r += NT) {  // multipliers f_r = T[r][c] / T[pr][c] (0 for a zero pivot)
+        const float2 v = Tf[r][c];
+        const float re = n2 > 0.f ? (v.x * pv.x + v.y * pv.y) / n2 : 0.f;
+        const float im = n2 > 0.f ? (v.y * pv.x - v.x * pv.y) / n2 : 0.f;
+        cmul_f[2 * r] = alive[r] ? re : 0.f;
+        cmul_f[2 * r + 1] = alive[r] ? im : 0.f;
+      }
+      __syncthreads();
+      for (int e = tid; e < nc * (bp - c - 1); e += NT) {
+        const int r = e / (bp - c - 1), j = c + 1 + e % (bp - c - 1);
+        if (!alive[r]) continue;
+        const float fr = cmul_f[2 * r], fi = cmul_f[2 * r + 1];
+        const float2 w = Tf[pr][j];
+        Tf[r][j].x -= fr * w.x - fi * w.y;
+        Tf[r][j].y -= fr * w.y + fi * w.x;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {  // pair the panel positions left out with the incoming rows
+      int v = 0;
+      for (int c = 0; c < bp; ++c) {
+        const int j = chosen[c];
+        if (j < bp) continue;
+        while (v < bp && !alive[v]) ++v;  // alive[v] here: panel row v was not chosen
+        lpl[v] = j;
+        lpl[j] = v;
+        ++v;
+      }
+    }
+    __syncthreads();
+    int* lp = perm + blockIdx.y * perm_stride + d.lperm;
+    for (int i = tid; i < nc; i += NT) lp[i] = lpl[i];
+  }
   long long km = 0;
   for (int e = tid; e < nel; e += NT) {
     const int i = e / bp, j = e - i * bp;
-    const T v = A[(int64_t)i * d.ld + j];
+    const T v = Tc[lpl[i]][j];
     S[0][i][j] = v;
     km = max(km, mag_key(v));
   }
@@ -476,6 +561,12 @@ __global__ void __launch_bounds__(NT)
     const int i = e / bp, j = e - i * bp;
     A[(int64_t)i * d.ld + j] = S[fin][rmap[fmap][i]][qcol[j]];
   }
+  // the panel rows left out, now at the positions of the incoming rows (their
+  // columns outside the panel are exchanged by the row swap after this launch)
+  for (int e = bp * bp + tid; e < nc * bp; e += NT) {
+    const int i = e / bp, j = e - i * bp;
+    A[(int64_t)i * d.ld + j] = Tc[lpl[i]][j];
+  }
 }
 
 // the instantiation for a plan's panel width (blocks of 24, 32 or 48): 512
@@ -483,7 +574,7 @@ __global__ void __launch_bounds__(NT)
 // 32-wide FP64 blocks (measured per width and precision on one block)
 template <typename T, typename R>
 struct PanelLaunch {
-  void (*k)(const PanelDesc*, int, int, const CopyDesc*, int, int, int, T*, int64_t, int*);
+  void (*k)(const PanelDesc*, int, int, const CopyDesc*, int, int, int, T*, int64_t, int*, int64_t, int*);
   int threads, block;
 };
 template <typename T, typename R>
@@ -509,6 +600,73 @@ cudaError_t panel_prepare() {
       e = cudaFuncSetAttribute(pf.k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem_bytes<float2>(w));
   }
   return e;
+}
+
+// ---------------------------------------------------------------------------
+// Row exchanges of the cross-panel pivoting on the columns outside a panel:
+// thread = column of the front, the panel's exchanges (disjoint pairs i <->
+// lperm[i] of its candidate rows) swapped in place.  Runs after the previous
+// step's bulk update and write-back, which still write those rows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_swap_desc(const PanelDesc* __restrict__ ds, int d0, int d1, int blk) {
+  int lo = d0, hi = d1 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ds[mid].swap_blk0 <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+template <typename T>
+__global__ void __launch_bounds__(kSwapCols) k_row_swap(const PanelDesc* __restrict__ ds, int d0, int d1,
+                                                        const int* __restrict__ perm, int64_t perm_stride,
+                                                        T* __restrict__ arena, int64_t stride) {
+  pdl_enter();
+  const PanelDesc d = ds[find_swap_desc(ds, d0, d1, blockIdx.x)];
+  if (d.nc <= d.bp) return;
+  const int col = (blockIdx.x - d.swap_blk0) * kSwapCols + threadIdx.x;
+  if (col >= d.ld || (col >= d.col0 && col < d.col0 + d.bp)) return;
+  const int* lp = perm + blockIdx.y * perm_stride + d.lperm;
+  T* row0 = arena + blockIdx.y * stride + (d.a - d.col0) + col;  // column col of the first candidate row
+  for (int i = 0; i < d.nc; ++i) {
+    const int j = lp[i];
+    if (j <= i) continue;
+    const T a = row0[(int64_t)i * d.ld], b = row0[(int64_t)j * d.ld];
+    row0[(int64_t)i * d.ld] = b;
+    row0[(int64_t)j * d.ld] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// After a supernode's selected-inversion step: its pivot-row columns back in
+// the supernode's original order, by undoing its panels' row exchanges as
+// column exchanges in reverse order (warp = front row).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(32 * kUnpermRows)
+    k_unperm(const UnpermDesc* __restrict__ ds, int d0, int d1, const PanelDesc* __restrict__ pan,
+             const int* __restrict__ node_panels, const int* __restrict__ perm, int64_t perm_stride,
+             T* __restrict__ arena, int64_t stride) {
+  pdl_enter();
+  const UnpermDesc d = ds[find_desc(ds, d0, d1, blockIdx.x)];
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x - d.blk0) * kUnpermRows + (threadIdx.x >> 5);
+  if (row >= d.nf) return;
+  T* F = arena + blockIdx.y * stride + d.front + (int64_t)row * d.nf;
+  const int* pm = perm + blockIdx.y * perm_stride;
+  for (int q = d.npan - 1; q >= 0; --q) {
+    const PanelDesc pd = pan[node_panels[d.pan0 + q]];
+    if (pd.nc <= pd.bp) continue;  // no exchange
+    const int* lp = pm + pd.lperm;
+    for (int i = lane; i < pd.nc; i += 32) {
+      const int j = lp[i];
+      if (j <= i) continue;
+      const T a = F[pd.col0 + i], b = F[pd.col0 + j];
+      F[pd.col0 + i] = b;
+      F[pd.col0 + j] = a;
+    }
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -664,8 +822,15 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
       const int per = pl.threads / 256;
       const dim3 grid((unsigned)(op.blocks + (op.xblocks + per - 1) / per), (unsigned)p.fbatch);
       return launch_k(pl.k, grid, dim3(pl.threads), panel_smem_bytes<T>(pl.block), st, prio, p.d_panels, op.d0,
-                      op.blocks, p.d_copies, op.x0, op.x1, op.xblocks, arena, stride, p.d_status);
+                      op.blocks, p.d_copies, op.x0, op.x1, op.xblocks, arena, stride, p.d_perm,
+                      (int64_t)p.perm_ints, p.d_status);
     }
+    case OP_SWAP:
+      return launch_k(k_row_swap<T>, grid1, dim3(kSwapCols), 0, st, prio, p.d_panels, op.d0, op.d1, p.d_perm,
+                      (int64_t)p.perm_ints, arena, stride);
+    case OP_UNPERM:
+      return launch_k(k_unperm<T>, grid1, dim3(32 * kUnpermRows), 0, st, prio, p.d_unperm, op.d0, op.d1,
+                      p.d_panels, p.d_node_panels, p.d_perm, (int64_t)p.perm_ints, arena, stride);
     case OP_GEMM:
       return launch_gemm(p, op, arena, st);
     case OP_COPY:

@@ -100,7 +100,8 @@ int make_resident(int dev, int Ns, int Nt, unsigned char* base, cudaStream_t str
   const size_t table_bytes[] = {off.size() * sizeof(int64_t), ld.size() * sizeof(int), p.maps.size() * sizeof(int),
                                 p.gemm.size() * sizeof(cl::GemmDesc), p.panels.size() * sizeof(cl::PanelDesc),
                                 p.copies.size() * sizeof(cl::CopyDesc), p.extadd.size() * sizeof(cl::ExtAddDesc),
-                                p.gather.size() * sizeof(cl::GatherDesc)};
+                                p.gather.size() * sizeof(cl::GatherDesc), p.unperm.size() * sizeof(cl::UnpermDesc),
+                                p.node_panels.size() * sizeof(int), (size_t)p.perm_ints * sizeof(int)};
   for (size_t b : table_bytes) need += align256(b ? b : 16);
   if (need > kNoAllocBytes) {
     delete r;
@@ -120,6 +121,11 @@ int make_resident(int dev, int Ns, int Nt, unsigned char* base, cudaStream_t str
   if (e == cudaSuccess) e = place(base, o, p.d_copies, p.copies.data(), table_bytes[5], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_extadd, p.extadd.data(), table_bytes[6], stream);
   if (e == cudaSuccess) e = place(base, o, p.d_gather, p.gather.data(), table_bytes[7], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_unperm, p.unperm.data(), table_bytes[8], stream);
+  if (e == cudaSuccess) e = place(base, o, p.d_node_panels, p.node_panels.data(), table_bytes[9], stream);
+  // the panels' row permutations (written by the panel kernels before they are read)
+  p.d_perm = reinterpret_cast<int*>(base + o);
+  o = align256(o + (table_bytes[10] ? table_bytes[10] : 16));
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     delete r;

@@ -13,6 +13,12 @@ namespace cl {
 // GEMM tile in complex elements (rows x cols); shared by host schedule and kernels.
 constexpr int kTileM = 64;
 constexpr int kTileN = 32;
+// row swap of the cross-panel pivoting: columns per CTA (one thread per
+// column; a panel's row exchanges are disjoint pairs, swapped in place)
+constexpr int kSwapCols = 256;
+// column un-permutation after a supernode's selected-inversion step: front
+// rows per CTA (one warp per row)
+constexpr int kUnpermRows = 8;
 constexpr int kEmuTileM = 128;
 // Sites per leaf of the nested dissection and pivoting panel (unknowns) by
 // precision.  30 unknowns (10 sites) is the widest panel whose products stay
@@ -81,11 +87,34 @@ struct GemmDesc {
   int trans = 0;
 };
 
-// In-place inverse of the diagonal panel block A[pp] (bp x bp, leading dim ld).
+// Pivot panel of a supernode: its pivots are chosen among the nc rows col0 ..
+// col0 + nc - 1 of the front (the rows of this panel and of the next one in
+// the supernode), the chosen rows' block A[pp] (bp x bp, leading dim ld) is
+// inverted in place, and the panel's row permutation of those nc rows (lperm:
+// position i holds candidate row lperm[i]) is left in the permutation
+// workspace, where the row swap applies it to the other columns and to the
+// supernode's running permutation pi (position i of the front holds the
+// supernode's original row pi[i]); swap_blk0: first CTA of the panel in the
+// row-swap launch.
 struct PanelDesc {
   int64_t a;
   int ld, bp;
   int node, col0;
+  int nc;
+  int lperm, pi;  // offsets (ints) in the permutation workspace
+  int swap_blk0;
+};
+
+// After a supernode's step of the selected inversion: the columns of its
+// pivot rows are put back in the supernode's original order, G[:, pi[i]] =
+// front[:, i] for i < k, on every row of the front, by undoing the panels'
+// row exchanges (node_panels[pan0 .. pan0 + npan): its panels in step order)
+// in reverse order; one warp per front row.
+struct UnpermDesc {
+  int64_t front;
+  int nf, k;
+  int pan0, npan;
+  int blk0;
 };
 
 // dst[i][j] = src[i][j] for i < rows, j < cols, skipping rows in `rmask` and
@@ -146,9 +175,10 @@ struct VecNode {
   int ea_map[2], ga_map;
   int site0;
   int blk_nf, blk_r;  // first CTA of this node in a level launch over nf / r elements (tiles of 128)
+  int pan0, npan;     // the supernode's panels (node_panels), whose row exchanges the solve undoes
 };
 
-enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT };
+enum OpKind { OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT, OP_SWAP, OP_UNPERM };
 
 // One scheduled launch.  The factorisation runs on two streams: the
 // critical chain (panel inverses, panel products, next-panel strips) on the
@@ -202,6 +232,9 @@ struct Plan {
   std::vector<int> maps;                            // int maps of extend-add and gather
   std::vector<GemmDesc> gemm;
   std::vector<PanelDesc> panels;
+  std::vector<UnpermDesc> unperm;
+  std::vector<int> node_panels;  // panel indices grouped by supernode, in step order
+  int64_t perm_ints = 0;         // permutation workspace per replica (ints)
   std::vector<CopyDesc> copies;
   std::vector<ExtAddDesc> extadd;
   std::vector<GatherDesc> gather;
@@ -221,6 +254,9 @@ struct Plan {
   int* d_maps = nullptr;
   GemmDesc* d_gemm = nullptr;
   PanelDesc* d_panels = nullptr;
+  UnpermDesc* d_unperm = nullptr;
+  int* d_node_panels = nullptr;
+  int* d_perm = nullptr;  // fbatch x perm_ints
   CopyDesc* d_copies = nullptr;
   ExtAddDesc* d_extadd = nullptr;
   GatherDesc* d_gather = nullptr;

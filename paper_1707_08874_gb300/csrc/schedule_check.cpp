@@ -106,16 +106,29 @@ void footprint(const Plan& p, const Op& op, R&& visit_read, W&& visit_write) {
           }
       }
       break;
-    case OP_PANEL:
+    case OP_PANEL:  // the candidate rows in the panel's columns (inverse of the chosen block, displaced rows)
       for (int d = op.d0; d < op.d1; ++d) {
         const PanelDesc& x = p.panels[d];
-        for (int i = 0; i < x.bp; ++i)
+        for (int i = 0; i < x.nc; ++i)
           for (int j = 0; j < x.bp; ++j) {
             visit_read(x.a + (int64_t)i * x.ld + j);
             visit_write(x.a + (int64_t)i * x.ld + j);
           }
       }
       copy_footprint(p, op.x0, op.x1, visit_read, visit_write);  // the copies launched with the panels
+      break;
+    case OP_SWAP:  // the candidate rows in every column outside the panel
+      for (int d = op.d0; d < op.d1; ++d) {
+        const PanelDesc& x = p.panels[d];
+        if (x.nc <= x.bp) continue;
+        const int64_t row0 = x.a - x.col0;  // column 0 of the panel's first row
+        for (int i = 0; i < x.nc; ++i)
+          for (int j = 0; j < x.ld; ++j) {
+            if (j >= x.col0 && j < x.col0 + x.bp) continue;
+            visit_read(row0 + (int64_t)i * x.ld + j);
+            visit_write(row0 + (int64_t)i * x.ld + j);
+          }
+      }
       break;
     case OP_GEMM:
       for (int d = op.d0; d < op.d1; ++d) {

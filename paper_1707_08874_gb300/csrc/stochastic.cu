@@ -85,7 +85,9 @@ template <typename T>
 __global__ void k_vec_backward(const VecNode* __restrict__ vn, int v0, int v1, const int* __restrict__ maps,
                                const int* __restrict__ vsites, const T* __restrict__ arena, int64_t stride,
                                const double2* __restrict__ R, double2* __restrict__ W, int64_t vec_elems,
-                               double2* __restrict__ w, int64_t sites, int vrep) {
+                               double2* __restrict__ w, int64_t sites, int vrep, const PanelDesc* __restrict__ pan,
+                               const int* __restrict__ node_panels, const int* __restrict__ perm,
+                               int64_t perm_stride) {
   const int ni = find_vnode<false>(vn, v0, v1, blockIdx.x);
   const VecNode d = vn[ni];
   const int e = (blockIdx.x - d.blk_nf) * 128 + threadIdx.x;
@@ -104,9 +106,17 @@ __global__ void k_vec_backward(const VecNode* __restrict__ vn, int v0, int v1, c
   double2 acc = make_double2(0, 0);
   for (int j = 0; j < d.k; ++j) cfma(acc, Ri[j], to_d2(F[(int64_t)j * d.nf]));
   for (int s = 0; s < d.r; ++s) cfma(acc, wpar(s), to_d2(F[(int64_t)(d.k + s) * d.nf]));
-  Wi[d.vec + e] = acc;
-  const int64_t site = (int64_t)rep * vrep + vsites[d.site0 + e / 3];
-  w[((int64_t)i * sites + site) * 3 + e % 3] = acc;
+  // the factors are those of the row-permuted supernode: entry e belongs to
+  // its unknown pi(e), the panels' row exchanges composed (the last first)
+  int x = e;
+  const int* pm = perm + rep * perm_stride;
+  for (int q = d.npan - 1; q >= 0; --q) {
+    const PanelDesc pd = pan[node_panels[d.pan0 + q]];
+    if (pd.nc > pd.bp && x >= pd.col0 && x < pd.col0 + pd.nc) x = pd.col0 + pm[pd.lperm + x - pd.col0];
+  }
+  Wi[d.vec + x] = acc;
+  const int64_t site = (int64_t)rep * vrep + vsites[d.site0 + x / 3];
+  w[((int64_t)i * sites + site) * 3 + x % 3] = acc;
 }
 
 // estimated selected blocks of one lattice shape: thread = link (s, nu)
@@ -179,7 +189,8 @@ cudaError_t launch_left_solve(const Plan& p, const double* eta, int n, double* w
     const int v0 = p.vlevel[h], v1 = p.vlevel[h + 1];
     if (v1 == v0) continue;
     k_vec_backward<T><<<dim3((unsigned)p.vblk_nf[h], (unsigned)n, (unsigned)p.fbatch), 128, 0, st>>>(
-        p.d_vnodes, v0, v1, p.d_maps, p.d_vsites, arena, stride, R, W, p.vec_elems, w2, sites, vrep);
+        p.d_vnodes, v0, v1, p.d_maps, p.d_vsites, arena, stride, R, W, p.vec_elems, w2, sites, vrep, p.d_panels,
+        p.d_node_panels, p.d_perm, (int64_t)p.perm_ints);
   }
   return cudaGetLastError();
 }

@@ -19,7 +19,7 @@ from paper_1707_08874_gb300 import binding as B
 from paper_1707_08874_gb300 import build as libbuild
 from paper_1707_08874_gb300 import inputs
 
-OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT = range(8)
+OP_ZERO, OP_ASSEMBLE, OP_EXTADD, OP_PANEL, OP_GEMM, OP_COPY, OP_GATHER, OP_EXTRACT, OP_SWAP, OP_UNPERM = range(10)
 M, MU = 0.05, 0.25
 
 
@@ -63,7 +63,32 @@ def _copies(A, descs):
     return out
 
 
-def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_out=None):
+def _pivot_rows(T, bp):
+    """Local permutation of the nc candidate rows of a panel (rows of T): the
+    bp rows that partial pivoting on T (magnitude max(|re|, |im|), ties to the
+    lowest row) makes pivots take the panel positions, the chosen rows of the
+    panel keeping theirs and the displaced rows taking the places of the
+    incoming ones; position i then holds candidate row lperm[i]."""
+    T = T.copy()
+    nc = T.shape[0]
+    live = list(range(nc))
+    chosen = []
+    for c in range(bp):
+        mags = np.maximum(np.abs(T[live, c].real), np.abs(T[live, c].imag))
+        j = live[int(np.argmax(mags))]
+        chosen.append(j)
+        live.remove(j)
+        for r in live:
+            T[r, c:] -= T[r, c] / T[j, c] * T[j, c:]
+    incoming = [j for j in chosen if j >= bp]
+    vacated = [i for i in range(bp) if i not in chosen]
+    lperm = np.arange(nc)
+    for i, j in zip(vacated, incoming):
+        lperm[i], lperm[j] = j, i
+    return lperm
+
+
+def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_out=None, perm_out=None):
     """Run the plan's op lists in order on a host arena.  D: the dense Dirac
     matrix of the one lattice of a single-shape plan, or the list of the dense
     matrices of every lattice of a ragged plan (shape order, replicas in
@@ -74,6 +99,10 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
     meta = t["meta"][0]
     pool, n_arena = int(meta[6]), int(meta[8])
     A = np.full(n_arena, np.nan + 0j)  # the workspace is never read before it is written
+    perm = np.zeros(int(meta[10]), dtype=np.int64)  # the permutation workspace (pi per supernode)
+    node_k = {}
+    for _, _, bp, node, c0, *_ in t["panel"]:
+        node_k[node] = max(node_k.get(node, 0), int(c0 + bp))
     off, ld, maps = t["off"], t["ld"], t["maps"]
     lattices = []  # (Ns, Nt, V, arena base, table base) per lattice
     for sNs, sNt, V, count, pbase, rstride, tbase, _ in segs:
@@ -115,10 +144,30 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
                     idx = _grid(parent, nfp, nfp, nfp)
                     writes.append((idx[hit], A[idx][hit] + acc[hit]))
             elif kind == OP_PANEL:
-                for a, l, bp, *_ in t["panel"][d0:d1]:
+                for idx, val in _copies(A, t["copy"][x0:x1]):  # launched with the panels, before them
+                    A[idx] = val
+                for a, l, bp, node, c0, nc, lp, pi, _ in t["panel"][d0:d1]:
+                    if c0 == 0:  # a supernode's first panel: its rows in their original order
+                        perm[pi:pi + node_k[node]] = np.arange(node_k[node])
+                    # pivots among the nc candidate rows; the rows are exchanged on
+                    # every column at once (the device swaps the panel's columns in
+                    # the panel launch and the others in the swap op after it)
+                    first = a - c0  # column 0 of the candidate rows
+                    R = A[first + np.arange(nc)[:, None] * l + np.arange(l)[None, :]]
+                    lperm = _pivot_rows(R[:, c0:c0 + bp], bp)
+                    A[first + np.arange(nc)[:, None] * l + np.arange(l)[None, :]] = R[lperm]
+                    perm[pi + c0:pi + c0 + nc] = perm[pi + c0 + lperm]
                     idx = _grid(a, bp, bp, l)
                     writes.append((idx, np.linalg.inv(A[idx])))
-                writes += _copies(A, t["copy"][x0:x1])  # launched with the panels
+            elif kind == OP_SWAP:
+                pass  # applied with the panel op above
+            elif kind == OP_UNPERM:
+                for front, nf, k, p0, npn, _ in t["unperm"][d0:d1]:
+                    pi = t["panel"][t["node_panels"][p0]][7]  # the supernode's running permutation
+                    F = A[front:front + nf * nf].reshape(nf, nf).copy()
+                    G = F.copy()
+                    G[:, perm[pi:pi + k]] = F[:, :k]
+                    writes.append((np.arange(front, front + nf * nf), G.reshape(-1)))
             elif kind == OP_COPY:
                 writes += _copies(A, t["copy"][d0:d1])
             elif kind == OP_GEMM:
@@ -145,10 +194,12 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
                 A[idx] = val
     if arena_out is not None:
         arena_out.append(A)
+    if perm_out is not None:
+        perm_out.append(perm)
     return outs if isinstance(D, list) else outs[0]
 
 
-def left_solve(t, A, eta):
+def left_solve(t, A, eta, perm):
     """The row-vector solves w = eta^dag D^{-1} of cl_left_solve executed from
     the exported front-vector tables on a factorised host arena A (forward
     over the levels, then backward), for a plan with one replica per shape
@@ -163,7 +214,7 @@ def left_solve(t, A, eta):
     front = lambda x: A[x[0]:x[0] + x[3] * x[3]].reshape(x[3], x[3])
     for h in levels:  # forward
         for x in vn[vn[:, 6] == h]:
-            fr, vec, pvec, nf, k, r, lv, nch, cv0, cv1, ck0, ck1, em0, em1, gm, s0 = x
+            fr, vec, pvec, nf, k, r, lv, nch, cv0, cv1, ck0, ck1, em0, em1, gm, s0, p0, npn = x
             v = np.zeros((n, nf), complex)
             e = np.arange(k)
             v[:, :k] = eta[:, vs[s0 + e // 3], e % 3].conj()
@@ -177,14 +228,17 @@ def left_solve(t, A, eta):
             R[:, vec:vec + nf] = v
     for h in levels[::-1]:  # backward
         for x in vn[vn[:, 6] == h]:
-            fr, vec, pvec, nf, k, r, lv, nch, cv0, cv1, ck0, ck1, em0, em1, gm, s0 = x
+            fr, vec, pvec, nf, k, r, lv, nch, cv0, cv1, ck0, ck1, em0, em1, gm, s0, p0, npn = x
+            pi = t["panel"][t["node_panels"][p0]][7] if npn else 0
             F = front(x)
             S = np.arange(r)
             wS = W[:, pvec + 3 * maps[gm + S // 3] + S % 3] if r else np.zeros((n, 0), complex)
             wJ = R[:, vec:vec + k] @ F[:k, :k] + wS @ F[k:, :k]
-            W[:, vec:vec + k] = wJ
+            # the factors are those of the row-permuted supernode: entry i of wJ
+            # belongs to the supernode's unknown pi[i]
+            e = perm[pi:pi + k] if k else np.zeros(0, dtype=np.int64)
+            W[:, vec + e] = wJ
             W[:, vec + k:vec + nf] = wS
-            e = np.arange(k)
             w[:, vs[s0 + e // 3], e % 3] = wJ
     return w
 
@@ -275,12 +329,12 @@ def test_left_solve_tables(shapes):
     lat = [(ns, nt) for ns, nt, c in shapes for _ in range(c)]
     Us = [inputs.random_links(ns, nt, seed=70 + i) for i, (ns, nt) in enumerate(lat)]
     Ds = [oracle.dirac_dense(ns, nt, U, M, MU) for (ns, nt), U in zip(lat, Us)]
-    arena = []
-    execute(tables, Ds if len(Ds) > 1 else Ds[0], phases=("factor_ops",), arena_out=arena)
+    arena, perm = [], []
+    execute(tables, Ds if len(Ds) > 1 else Ds[0], phases=("factor_ops",), arena_out=arena, perm_out=perm)
     sites = sum(ns ** 3 * nt for ns, nt in lat)
     rng = np.random.default_rng(5)
     eta = rng.normal(size=(3, sites, 3)) + 1j * rng.normal(size=(3, sites, 3))
-    w = left_solve(tables, arena[0], eta)
+    w = left_solve(tables, arena[0], eta, perm[0])
     s0 = 0
     for (ns, nt), D in zip(lat, Ds):
         V = ns ** 3 * nt
