@@ -326,13 +326,16 @@ __global__ void __launch_bounds__(NT)
   T(*Tc)[MP] = reinterpret_cast<T(*)[MP]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1));  // candidate rows
   float2(*Tf)[MP] = reinterpret_cast<float2(*)[MP]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1) +
                                                     2 * sizeof(T) * MP * MP);
-  __shared__ int lpl[2 * MP], chosen[MP];   // nc <= 2 MP candidate rows
-  __shared__ float cmul_f[4 * MP];          // (re, im) multiplier per candidate row
+  __shared__ int lpl[2 * MP], chosen[MP];  // nc <= 2 MP candidate rows
   __shared__ unsigned char alive[2 * MP];
+  // threads per candidate row in the pivot choice (a power of two, TPR 2 MP <= NT)
+  constexpr int TPR = NT / (2 * MP) >= 8 ? 8 : (NT / (2 * MP) >= 4 ? 4 : (NT / (2 * MP) >= 2 ? 2 : 1));
+  static_assert(TPR * 2 * MP <= NT, "one thread group per candidate row");
   const PanelDesc d = ds[d0 + blockIdx.x];
   T* A = arena + blockIdx.y * stride + d.a;
   const int bp = d.bp, nel = bp * bp, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nc = d.nc;  // candidate rows: this panel's and the next panel's
+  const int srow = tid / TPR, ssub = tid % TPR;
   // Pivot rows.  Partial pivoting over the nc candidate rows of the panel's
   // columns chooses bp of them (in FP32: only the choice is taken from it);
   // the chosen rows of the panel keep their positions, the chosen rows of the
@@ -368,24 +371,20 @@ __global__ void __launch_bounds__(NT)
         }
       }
       __syncthreads();
+      // elimination of column c from the remaining rows: TPR threads per
+      // candidate row (row srow, columns c+1+ssub, c+1+ssub+TPR, ...), each
+      // forming its row's multiplier T[r][c] / T[pr][c] (0 for a zero pivot)
       const int pr = chosen[c];
-      const float2 pv = Tf[pr][c];
-      const float n2 = pv.x * pv.x + pv.y * pv.y;
-      for (int r = tid; r < nc; r += NT) {  // multipliers f_r = T[r][c] / T[pr][c] (0 for a zero pivot)
-        const float2 v = Tf[r][c];
-        const float re = n2 > 0.f ? (v.x * pv.x + v.y * pv.y) / n2 : 0.f;
-        const float im = n2 > 0.f ? (v.y * pv.x - v.x * pv.y) / n2 : 0.f;
-        cmul_f[2 * r] = alive[r] ? re : 0.f;
-        cmul_f[2 * r + 1] = alive[r] ? im : 0.f;
-      }
-      __syncthreads();
-      for (int e = tid; e < nc * (bp - c - 1); e += NT) {
-        const int r = e / (bp - c - 1), j = c + 1 + e % (bp - c - 1);
-        if (!alive[r]) continue;
-        const float fr = cmul_f[2 * r], fi = cmul_f[2 * r + 1];
-        const float2 w = Tf[pr][j];
-        Tf[r][j].x -= fr * w.x - fi * w.y;
-        Tf[r][j].y -= fr * w.y + fi * w.x;
+      if (srow < nc && alive[srow]) {
+        const float2 pv = Tf[pr][c], v = Tf[srow][c];
+        const float n2 = pv.x * pv.x + pv.y * pv.y;
+        const float fr = n2 > 0.f ? (v.x * pv.x + v.y * pv.y) / n2 : 0.f;
+        const float fi = n2 > 0.f ? (v.y * pv.x - v.x * pv.y) / n2 : 0.f;
+        for (int j = c + 1 + ssub; j < bp; j += TPR) {
+          const float2 w = Tf[pr][j];
+          Tf[srow][j].x -= fr * w.x - fi * w.y;
+          Tf[srow][j].y -= fr * w.y + fi * w.x;
+        }
       }
       __syncthreads();
     }
@@ -623,17 +622,35 @@ __global__ void __launch_bounds__(kSwapCols) k_row_swap(const PanelDesc* __restr
                                                         T* __restrict__ arena, int64_t stride) {
   pdl_enter();
   const PanelDesc d = ds[find_swap_desc(ds, d0, d1, blockIdx.x)];
-  if (d.nc <= d.bp) return;
+  if (d.nc <= d.bp) return;  // CTA-uniform
   const int col = (blockIdx.x - d.swap_blk0) * kSwapCols + threadIdx.x;
-  if (col >= d.ld || (col >= d.col0 && col < d.col0 + d.bp)) return;
+  // the panel's exchanged pairs (i < lperm[i]), listed once per CTA
+  __shared__ int pair_i[2 * kMaxPanel], pair_j[2 * kMaxPanel], npairs;
   const int* lp = perm + blockIdx.y * perm_stride + d.lperm;
+  if (threadIdx.x < 32) {
+    int base = 0;
+    for (int i0 = 0; i0 < d.nc; i0 += 32) {
+      const int i = i0 + (int)threadIdx.x;
+      const int j = i < d.nc ? lp[i] : -1;
+      const bool take = j > i;
+      const unsigned m = __ballot_sync(0xffffffffu, take);
+      if (take) {
+        const int q = base + __popc(m & ((1u << threadIdx.x) - 1u));
+        pair_i[q] = i;
+        pair_j[q] = j;
+      }
+      base += __popc(m);
+    }
+    if (threadIdx.x == 0) npairs = base;
+  }
+  __syncthreads();
+  if (col >= d.ld || (col >= d.col0 && col < d.col0 + d.bp)) return;
   T* row0 = arena + blockIdx.y * stride + (d.a - d.col0) + col;  // column col of the first candidate row
-  for (int i = 0; i < d.nc; ++i) {
-    const int j = lp[i];
-    if (j <= i) continue;
-    const T a = row0[(int64_t)i * d.ld], b = row0[(int64_t)j * d.ld];
-    row0[(int64_t)i * d.ld] = b;
-    row0[(int64_t)j * d.ld] = a;
+  for (int q = 0; q < npairs; ++q) {
+    const int64_t oi = (int64_t)pair_i[q] * d.ld, oj = (int64_t)pair_j[q] * d.ld;
+    const T a = row0[oi], b = row0[oj];
+    row0[oi] = b;
+    row0[oj] = a;
   }
 }
 
