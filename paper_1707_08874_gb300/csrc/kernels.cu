@@ -258,7 +258,8 @@ template <typename T>
 constexpr size_t panel_smem_bytes(int mp) {
   // the block's two copies, then the candidate rows' panel columns (up to
   // 2 mp rows) in the front's precision and as float2 for the pivot choice
-  return 2 * (size_t)mp * (mp + 1) * sizeof(T) + 2 * (size_t)mp * mp * (sizeof(T) + sizeof(float2));
+  return 2 * (size_t)mp * (mp + 1) * sizeof(T) + 2 * (size_t)mp * mp * sizeof(T) +
+         2 * (size_t)mp * (mp + 1) * sizeof(float2);
 }
 
 __host__ __device__ constexpr int bit_count(unsigned m) { return m ? (int)(m & 1u) + bit_count(m >> 1) : 0; }
@@ -324,10 +325,11 @@ __global__ void __launch_bounds__(NT)
   __shared__ int rmap[2][MP], qcol[MP];
   __shared__ long long wmax[NW], pkey[MP];
   T(*Tc)[MP] = reinterpret_cast<T(*)[MP]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1));  // candidate rows
-  float2(*Tf)[MP] = reinterpret_cast<float2(*)[MP]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1) +
-                                                    2 * sizeof(T) * MP * MP);
-  __shared__ int lpl[2 * MP], chosen[MP];  // nc <= 2 MP candidate rows
-  __shared__ unsigned char alive[2 * MP];
+  float2(*Tf)[MP + 1] = reinterpret_cast<float2(*)[MP + 1]>(panel_smem + 2 * sizeof(T) * MP * (MP + 1) +
+                                                            2 * sizeof(T) * MP * MP);  // rows padded: no bank conflicts
+  __shared__ int lpl[2 * MP], chosen[MP], vlist[MP], ilist[MP];  // nc <= 2 MP candidate rows
+  __shared__ unsigned char picked[2 * MP];
+  __shared__ unsigned long long best[3];  // per column (mod 3): (magnitude bits << 32) | ~row
   // threads per candidate row in the pivot choice (a power of two, TPR 2 MP <= NT)
   constexpr int TPR = NT / (2 * MP) >= 8 ? 8 : (NT / (2 * MP) >= 4 ? 4 : (NT / (2 * MP) >= 2 ? 2 : 1));
   static_assert(TPR * 2 * MP <= NT, "one thread group per candidate row");
@@ -350,53 +352,64 @@ __global__ void __launch_bounds__(NT)
   }
   for (int i = tid; i < nc; i += NT) {
     lpl[i] = i;
-    alive[i] = 1;
+    picked[i] = 0;
   }
+  if (tid < 3) best[tid] = 0ull;
   __syncthreads();
   if (nc > bp) {
+    // one barrier per column: each remaining row's group updates its row and
+    // posts the row's magnitude in the next column through a shared atomic
+    // maximum (ties: the lowest row), read after the barrier
+    auto post = [&](int slot, int r, int col) {
+      const float2 v = Tf[r][col];
+      const unsigned m = max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y)));
+      atomicMax(&best[slot], ((unsigned long long)m << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)r));
+    };
+    bool mine = srow < nc;  // this thread's row is still a candidate
+    if (mine && ssub == 0) post(0, srow, 0);
+    __syncthreads();
     for (int c = 0; c < bp; ++c) {
-      if (warp == 0) {  // the largest remaining entry of column c (max(|re|, |im|); ties: the lowest row)
-        unsigned key = 0;
-        int bi = 0x7fffffff;
-        for (int r = lane; r < nc; r += 32) {
-          if (!alive[r]) continue;
-          const unsigned k2 = max(__float_as_uint(fabsf(Tf[r][c].x)), __float_as_uint(fabsf(Tf[r][c].y)));
-          if (bi == 0x7fffffff || k2 > key) key = k2, bi = r;
-        }
-        const unsigned kmx = __reduce_max_sync(0xffffffffu, bi != 0x7fffffff ? key : 0u);
-        const int pr = (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && key == kmx) ? (unsigned)bi : 0x7fffffffu);
-        if (lane == 0) {
-          chosen[c] = pr;
-          alive[pr] = 0;
-        }
+      const int pr = (int)(0xFFFFFFFFu - (unsigned)(best[c % 3] & 0xFFFFFFFFull));
+      if (tid == 0) {
+        chosen[c] = pr;
+        best[(c + 2) % 3] = 0ull;  // read last at column c - 1, posted to from column c + 1 on
       }
-      __syncthreads();
-      // elimination of column c from the remaining rows: TPR threads per
-      // candidate row (row srow, columns c+1+ssub, c+1+ssub+TPR, ...), each
-      // forming its row's multiplier T[r][c] / T[pr][c] (0 for a zero pivot)
-      const int pr = chosen[c];
-      if (srow < nc && alive[srow]) {
+      if (srow == pr) mine = false;
+      if (mine && c + 1 < bp) {
+        // eliminate column c from the row (fast reciprocal: only the choice is kept)
         const float2 pv = Tf[pr][c], v = Tf[srow][c];
         const float n2 = pv.x * pv.x + pv.y * pv.y;
-        const float fr = n2 > 0.f ? (v.x * pv.x + v.y * pv.y) / n2 : 0.f;
-        const float fi = n2 > 0.f ? (v.y * pv.x - v.x * pv.y) / n2 : 0.f;
+        const float rn = n2 > 0.f ? __frcp_rn(n2) : 0.f;
+        const float fr = (v.x * pv.x + v.y * pv.y) * rn, fi = (v.y * pv.x - v.x * pv.y) * rn;
         for (int j = c + 1 + ssub; j < bp; j += TPR) {
           const float2 w = Tf[pr][j];
           Tf[srow][j].x -= fr * w.x - fi * w.y;
           Tf[srow][j].y -= fr * w.y + fi * w.x;
         }
+        if (ssub == 0) post((c + 1) % 3, srow, c + 1);  // its own update of column c + 1 is done
       }
       __syncthreads();
     }
-    if (tid == 0) {  // pair the panel positions left out with the incoming rows
-      int v = 0;
-      for (int c = 0; c < bp; ++c) {
-        const int j = chosen[c];
-        if (j < bp) continue;
-        while (v < bp && !alive[v]) ++v;  // alive[v] here: panel row v was not chosen
-        lpl[v] = j;
-        lpl[j] = v;
-        ++v;
+    // pair the panel positions left out with the incoming rows (in pivot order)
+    for (int c = tid; c < bp; c += NT) picked[chosen[c]] = 1;
+    __syncthreads();
+    if (warp == 0) {
+      int nv = 0, ni = 0;
+      for (int i0 = 0; i0 < bp; i0 += 32) {
+        const int v = i0 + lane;
+        const bool vac = v < bp && !picked[v];
+        const bool inc = v < bp && chosen[v] >= bp;
+        const unsigned mv = __ballot_sync(0xffffffffu, vac), mi = __ballot_sync(0xffffffffu, inc);
+        const unsigned below = (1u << lane) - 1u;
+        if (vac) vlist[nv + __popc(mv & below)] = v;
+        if (inc) ilist[ni + __popc(mi & below)] = chosen[v];
+        nv += __popc(mv);
+        ni += __popc(mi);
+      }
+      __syncwarp();
+      for (int q = lane; q < nv; q += 32) {  // nv == ni
+        lpl[vlist[q]] = ilist[q];
+        lpl[ilist[q]] = vlist[q];
       }
     }
     __syncthreads();
