@@ -438,9 +438,10 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": world * bsz / (e2e_ms / 1e3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": info["launches_per_eval"] * args.steps,
-        # largest max|entry| / min|pivot| of the panel blocks of the timed links
-        # (cl_plan_pivot_growth): ill-conditioned configurations, which may
-        # miss a 1e-10 accuracy of the FP64 path, show growths of ~700 or more
+        # largest max|entry| / min|pivot| of the pivot blocks of the timed links
+        # (cl_plan_pivot_growth): 11-62 over twenty 8^3x4 configurations with
+        # pivots chosen among two panels' rows (~1e3 on the ill-conditioned
+        # ones when pivots were restricted to a panel)
         "pivot_growth": growth,
         "roofline": {"bound": "tensor" if prec != B.CL_MIXED_FP32 else "alu",
                      "kernel": "front GEMMs (factorisation + selected inversion); achieved = flops_per_eval x "
