@@ -615,10 +615,13 @@ cudaError_t panel_prepare() {
 }
 
 // ---------------------------------------------------------------------------
-// Row exchanges of the cross-panel pivoting on the columns outside a panel:
-// thread = column of the front, the panel's exchanges (disjoint pairs i <->
-// lperm[i] of its candidate rows) swapped in place.  Runs after the previous
-// step's bulk update and write-back, which still write those rows.
+// Row exchanges of the cross-panel pivoting on the columns outside a panel.
+// The panel's exchanges are disjoint pairs i <-> lperm[i] of its candidate
+// rows.  A CTA takes kSwapCols columns of the front, and its kSwapGroups
+// thread groups share out the pairs.  Each thread loads the entries of up to
+// kSwapBatch pairs of its column before it stores any of them, so that those
+// loads are in flight together.  Runs after the previous step's bulk update
+// and write-back, which still write those rows.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_swap_desc(const PanelDesc* __restrict__ ds, int d0, int d1, int blk) {
   int lo = d0, hi = d1 - 1;
@@ -629,14 +632,17 @@ __device__ __forceinline__ int find_swap_desc(const PanelDesc* __restrict__ ds, 
   }
   return lo;
 }
+constexpr int kSwapGroups = 4;  // thread groups of a row-swap CTA, one pair in kSwapGroups each
+constexpr int kSwapBatch = 8;   // pairs a thread loads before it stores them
 template <typename T>
-__global__ void __launch_bounds__(kSwapCols) k_row_swap(const PanelDesc* __restrict__ ds, int d0, int d1,
-                                                        const int* __restrict__ perm, int64_t perm_stride,
-                                                        T* __restrict__ arena, int64_t stride) {
+__global__ void __launch_bounds__(kSwapCols* kSwapGroups)
+    k_row_swap(const PanelDesc* __restrict__ ds, int d0, int d1, const int* __restrict__ perm, int64_t perm_stride,
+               T* __restrict__ arena, int64_t stride) {
   pdl_enter();
   const PanelDesc d = ds[find_swap_desc(ds, d0, d1, blockIdx.x)];
   if (d.nc <= d.bp) return;  // CTA-uniform
-  const int col = (blockIdx.x - d.swap_blk0) * kSwapCols + threadIdx.x;
+  const int col = (blockIdx.x - d.swap_blk0) * kSwapCols + (int)(threadIdx.x % kSwapCols);
+  const int grp = (int)(threadIdx.x / kSwapCols);
   // the panel's exchanged pairs (i < lperm[i]), listed once per CTA
   __shared__ int pair_i[2 * kMaxPanel], pair_j[2 * kMaxPanel], npairs;
   const int* lp = perm + blockIdx.y * perm_stride + d.lperm;
@@ -659,11 +665,28 @@ __global__ void __launch_bounds__(kSwapCols) k_row_swap(const PanelDesc* __restr
   __syncthreads();
   if (col >= d.ld || (col >= d.col0 && col < d.col0 + d.bp)) return;
   T* row0 = arena + blockIdx.y * stride + (d.a - d.col0) + col;  // column col of the first candidate row
-  for (int q = 0; q < npairs; ++q) {
-    const int64_t oi = (int64_t)pair_i[q] * d.ld, oj = (int64_t)pair_j[q] * d.ld;
-    const T a = row0[oi], b = row0[oj];
-    row0[oi] = b;
-    row0[oj] = a;
+  const int np = npairs;
+  // the pairs are disjoint: no load of a batch reads an entry another pair stores
+  for (int q0 = grp; q0 < np; q0 += kSwapGroups * kSwapBatch) {
+    T a[kSwapBatch], b[kSwapBatch];
+#pragma unroll
+    for (int u = 0; u < kSwapBatch; ++u) {
+      const int q = q0 + u * kSwapGroups;
+      if (q < np) {
+        a[u] = row0[(int64_t)pair_i[q] * d.ld];
+        b[u] = row0[(int64_t)pair_j[q] * d.ld];
+      } else {
+        a[u] = b[u] = T{};
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSwapBatch; ++u) {
+      const int q = q0 + u * kSwapGroups;
+      if (q < np) {
+        row0[(int64_t)pair_i[q] * d.ld] = b[u];
+        row0[(int64_t)pair_j[q] * d.ld] = a[u];
+      }
+    }
   }
 }
 
@@ -856,7 +879,7 @@ cudaError_t launch_op(const Plan& p, const Op& op, T* arena, const double* links
                       (int64_t)p.perm_ints, p.d_status);
     }
     case OP_SWAP:
-      return launch_k(k_row_swap<T>, grid1, dim3(kSwapCols), 0, st, prio, p.d_panels, op.d0, op.d1, p.d_perm,
+      return launch_k(k_row_swap<T>, grid1, dim3(kSwapCols * kSwapGroups), 0, st, prio, p.d_panels, op.d0, op.d1, p.d_perm,
                       (int64_t)p.perm_ints, arena, stride);
     case OP_UNPERM:
       return launch_k(k_unperm<T>, grid1, dim3(32 * kUnpermRows), 0, st, prio, p.d_unperm, op.d0, op.d1,

@@ -13,9 +13,10 @@ namespace cl {
 // GEMM tile in complex elements (rows x cols); shared by host schedule and kernels.
 constexpr int kTileM = 64;
 constexpr int kTileN = 32;
-// row swap of the cross-panel pivoting: columns per CTA (one thread per
-// column; a panel's row exchanges are disjoint pairs, swapped in place)
-constexpr int kSwapCols = 256;
+// row swap of the cross-panel pivoting: front columns per CTA (a panel's row
+// exchanges are disjoint pairs, swapped in place by several thread groups per
+// column)
+constexpr int kSwapCols = 64;
 // column un-permutation after a supernode's selected-inversion step: front
 // rows per CTA (one warp per row)
 constexpr int kUnpermRows = 8;
