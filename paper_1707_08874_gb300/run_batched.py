@@ -141,7 +141,7 @@ def main(argv=None):
                            r["Gbwd"], r["Kf"])
             torch.cuda.synchronize()
             want = r["Kf"][0].cpu().numpy()
-            entry["drift_rel_err_vs_fp64"] = float(np.abs(K - want).max() / np.abs(want).max())
+            entry["drift_rel_err_vs_single_plan"] = float(np.abs(K - want).max() / np.abs(want).max())
             ref.close()
         rec["per_shape"].append(entry)
         site0 += cnt * V
