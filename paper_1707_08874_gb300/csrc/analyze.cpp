@@ -437,10 +437,11 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
       if (op.d1 > op.d0) p.factor_ops.push_back(op);
     }
     // Blocked sweep of the pivot panels with a one-panel look-ahead.  Stream 0
-    // (critical): panel inverse, panel products TR/TC, the update of the
-    // next panel's row and column strips and the entries the next panel
-    // reads from the current one.  Stream 1: the bulk rank-b update of the
-    // rest of the front and the write-back of the panel.  TR/TC alternate
+    // (critical): panel inverse, row swap, panel products TR/TC, the update
+    // of the next two panels' rows and of the next panel's column strip, and
+    // the entries the next step reads from the current one.  Stream 1: the
+    // bulk rank-b update of the rest of the front and the write-back of the
+    // panel.  TR/TC alternate
     // between two workspace sets by panel parity.
     int maxk = 0;
     for (int i : lv) maxk = std::max(maxk, F[i].k);
@@ -485,21 +486,22 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
       pinv.xblocks = pend_blocks;
       pend_x0 = pend_x1 = pend_blocks = 0;
       p.factor_ops.push_back(pinv);
-      // the panel's row permutation applied to the columns outside the panel
-      // (the rows of the next panel still receive the previous step's bulk
-      // update and write-back on stream 1: wait for them)
-      if (blk_sw > 0) {
-        Op sw{OP_SWAP, pinv.d0, pinv.d1, blk_sw, h};
-        sw.wait = last_copy;
-        p.factor_ops.push_back(sw);
-      }
+      // the panel's row permutation applied to the columns outside the panel.
+      // The candidate rows (panels p and p+1) took their updates of step p-1
+      // from its strips on this stream, and those of the steps before from
+      // bulk updates that the strips of step p-1 waited for: no wait here
+      if (blk_sw > 0) p.factor_ops.push_back(Op{OP_SWAP, pinv.d0, pinv.d1, blk_sw, h});
       g1.d1 = (int)p.gemm.size();
       g1.blocks = blk1;
       if (g1.d1 == g1.d0) continue;
       g1.signal = true;
       const int g1_idx = (int)p.factor_ops.size();
       p.factor_ops.push_back(g1);
-      // next-panel strips and the entries the next panel reads (stream 0)
+      // strips and the entries the next panel reads (stream 0).  The row strip
+      // covers the rows of panels p+1 and p+2, the candidate pivot rows of
+      // step p+1: their update of step p is then ordered before the row swap
+      // of step p+1 on this stream, and that swap need not wait for the bulk
+      // update of step p
       Op st{OP_GEMM, (int)p.gemm.size(), 0, 0, h};
       st.ndig = nd_factor;
       Op ec{OP_COPY, (int)p.copies.size(), 0, 0, h};
@@ -509,20 +511,21 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
         if (c0 >= n.k) continue;
         const int bp = std::min(b, n.k - c0), c1 = c0 + b;
         if (n.nf == bp || c1 >= n.k) continue;
-        const int b1 = std::min(b, n.k - c1);
+        const int b1 = std::min(b, n.k - c1), r2 = std::min(2 * b, n.k - c1);
         const int64_t tR = tR_of(n), tC = tC_of(n);
-        // row strip: A[c1.., j] -= C_old[c1.., :] TR[:, j], j outside panel p
+        // row strip: A[c1 .. c1+r2, j] -= C_old[c1 .., :] TR[:, j], j outside panel p
         if (tr_short)  // (A[c1.., :])^T -= TR^T C_old[c1.., :]^T
           blks += add_gemm(blks, tR, n.nf, n.off + (int64_t)c1 * n.nf + c0, n.nf, n.off + (int64_t)c1 * n.nf, n.nf,
-                           n.nf, b1, bp, 1, 1, Mask2{c0, c0 + bp, 0, 0}, none, 7);
+                           n.nf, r2, bp, 1, 1, Mask2{c0, c0 + bp, 0, 0}, none, 7);
         else
           blks += add_gemm(blks, n.off + (int64_t)c1 * n.nf + c0, n.nf, tR, n.nf, n.off + (int64_t)c1 * n.nf, n.nf,
-                           b1, n.nf, bp, 1, 1, none, Mask2{c0, c0 + bp, 0, 0});
-        // column strip: A[r, c1..] -= C_old[r, :] TR[:, c1..], r outside panels p and p+1
+                           r2, n.nf, bp, 1, 1, none, Mask2{c0, c0 + bp, 0, 0});
+        // column strip: A[r, c1..] -= C_old[r, :] TR[:, c1..], r outside panels p .. p+2
         blks += add_gemm(blks, n.off + c0, n.nf, tR + c1, n.nf, n.off + c1, n.nf, n.nf, b1, bp, 1, 1,
-                         Mask2{c0, c0 + bp, c1, c1 + b1}, none);
-        // swept entries of panel p that panel p+1 reads: A[c1.., c0..] = TC, A[c0.., c1..] = TR
-        blke += add_copy(blke, tC + (int64_t)c1 * bp, bp, n.off + (int64_t)c1 * n.nf + c0, n.nf, b1, bp, none, none);
+                         Mask2{c0, c0 + bp, c1, c1 + r2}, none);
+        // swept entries of panel p that the next step reads or swaps:
+        // A[c1 .. c1+r2, c0..] = TC, A[c0.., c1..] = TR
+        blke += add_copy(blke, tC + (int64_t)c1 * bp, bp, n.off + (int64_t)c1 * n.nf + c0, n.nf, r2, bp, none, none);
         blke += add_copy(blke, tR + c1, n.nf, n.off + (int64_t)c0 * n.nf + c1, n.nf, bp, b1, none, none);
       }
       st.d1 = (int)p.gemm.size();
@@ -552,11 +555,13 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
         const int bp = std::min(b, n.k - c0), c1 = c0 + b;
         if (n.nf == bp) continue;
         const int b1 = c1 < n.k ? std::min(b, n.k - c1) : 0;
-        const Mask2 pp{c0, c0 + bp, c1, c1 + b1};  // panels p and p+1
+        const int r2 = c1 < n.k ? std::min(2 * b, n.k - c1) : 0;
+        const Mask2 rows{c0, c0 + bp, c1, c1 + r2};  // panels p .. p+2 (row strip)
+        const Mask2 cols{c0, c0 + bp, c1, c1 + b1};  // panels p and p+1 (column strip)
         const int64_t tR = tR_of(n), tC = tC_of(n);
-        blk2 += add_gemm(blk2, n.off + c0, n.nf, tR, n.nf, n.off, n.nf, n.nf, n.nf, bp, 1, 1, pp, pp);
-        blk3 += add_copy(blk3, tC, bp, n.off + c0, n.nf, n.nf, bp, pp, none);
-        blk3 += add_copy(blk3, tR, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, bp, n.nf, none, pp);
+        blk2 += add_gemm(blk2, n.off + c0, n.nf, tR, n.nf, n.off, n.nf, n.nf, n.nf, bp, 1, 1, rows, cols);
+        blk3 += add_copy(blk3, tC, bp, n.off + c0, n.nf, n.nf, bp, rows, none);
+        blk3 += add_copy(blk3, tR, n.nf, n.off + (int64_t)c0 * n.nf, n.nf, bp, n.nf, none, cols);
       }
       g2.d1 = (int)p.gemm.size();
       g2.blocks = blk2;

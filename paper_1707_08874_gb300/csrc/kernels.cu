@@ -620,8 +620,9 @@ cudaError_t panel_prepare() {
 // rows.  A CTA takes kSwapCols columns of the front, and its kSwapGroups
 // thread groups share out the pairs.  Each thread loads the entries of up to
 // kSwapBatch pairs of its column before it stores any of them, so that those
-// loads are in flight together.  Runs after the previous step's bulk update
-// and write-back, which still write those rows.
+// loads are in flight together.  Runs on the chain stream right after the
+// panel inverse: the previous step's strips updated those rows on that stream,
+// and its bulk update and write-back leave them out.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_swap_desc(const PanelDesc* __restrict__ ds, int d0, int d1, int blk) {
   int lo = d0, hi = d1 - 1;

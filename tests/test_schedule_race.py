@@ -52,3 +52,28 @@ def test_ragged_schedule_race_free(prec):
     conflicts, first = p.check_schedule(ignore_waits=True)
     assert conflicts > 0
     p.close()
+
+
+@pytest.mark.parametrize("ns,nt,prec,panel", [(6, 4, B.CL_FP64_EMU, 30), (4, 4, B.CL_FP64, 12),
+                                              (8, 4, B.CL_FP64_EMU, 30)])
+def test_row_swaps_wait_for_no_bulk_update(ns, nt, prec, panel):
+    """The row swap of a step exchanges rows of its panel and of the next one,
+    which the previous step updated in its strips on the chain stream: every
+    swap runs on that stream with no cross-stream wait, the bulk updates leave
+    out the rows of the next two panels, and the schedule stays race-free."""
+    p = B.Plan.analyze_symbolic(ns, nt, prec, panel)
+    t = p.export_tables()
+    ops, gemm = t["factor_ops"], t["gemm"]
+    swaps = [op for op in ops if op[0] == 8]
+    assert swaps and all(op[5] == 0 and op[6] < 0 for op in swaps)
+    b = p.info["panel"]
+    bulk = [g for op in ops if op[0] == 4 and op[5] == 1 for g in gemm[op[1]:op[2]]]
+    assert bulk
+    for g in bulk:
+        rm, cm = g[11:15], g[15:19]
+        # rows left out: panel p, then panels p+1 and p+2; columns: panels p and p+1
+        assert tuple(rm[:3]) == tuple(cm[:3]) and rm[3] - rm[2] <= 2 * b and cm[3] - cm[2] <= b
+    assert any(g[14] - g[13] > b for g in bulk)
+    conflicts, first = p.check_schedule()
+    assert conflicts == 0, first
+    p.close()
