@@ -519,8 +519,9 @@ int cl_plan_check_schedule(const cl_plan* plan, int ignore_waits, long long* con
  *   CL_TABLE_PANEL       a, ld, bp, node, col0, nc (candidate pivot rows: this
  *                        panel's and the next panel's of the supernode),
  *                        lperm, pi (offsets in the permutation workspace of
- *                        the panel's row permutation and of the supernode's
- *                        running one), swap_blk0
+ *                        the panel's row permutation, which the device
+ *                        writes, and of a slot for the supernode's running
+ *                        one, which it leaves to host executors), swap_blk0
  *   CL_TABLE_COPY        src, dst, lds, ldd, rows, cols, rmask[4], cmask[4]
  *   CL_TABLE_EXTADD      parent, nfp, nchild, child[2], nfc[2], kc[2], map[2]
  *   CL_TABLE_GATHER      child, parent, nfc, kc, nfp, rs, map

@@ -393,8 +393,9 @@ void build_schedule(Plan& p, std::vector<FNode>& F, int n_levels, int precision)
     return (int)(((int64_t)rows * cols + 255) / 256);
   };
 
-  // permutation workspace: per node its running row permutation (k ints),
-  // then per panel its local permutation of the candidate rows (nc ints)
+  // permutation workspace: per node a slot for its running row permutation
+  // (k ints, kept by host executors of the exported schedule only), then per
+  // panel its local permutation of the candidate rows (nc ints)
   p.unperm.clear();
   int64_t perm_ints = 0;
   std::vector<int> pi_off(nn);

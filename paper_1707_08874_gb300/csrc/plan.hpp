@@ -93,10 +93,12 @@ struct GemmDesc {
 // the supernode), the chosen rows' block A[pp] (bp x bp, leading dim ld) is
 // inverted in place, and the panel's row permutation of those nc rows (lperm:
 // position i holds candidate row lperm[i]) is left in the permutation
-// workspace, where the row swap applies it to the other columns and to the
-// supernode's running permutation pi (position i of the front holds the
-// supernode's original row pi[i]); swap_blk0: first CTA of the panel in the
-// row-swap launch.
+// workspace, where the row swap applies it to the other columns.  pi: a slot
+// of k ints per supernode for its running permutation (position i of the
+// front holds the supernode's original row pi[i]), which host executors of
+// the exported schedule keep; the device kernels leave it untouched and undo
+// the panels' exchanges one by one instead.  swap_blk0: first CTA of the
+// panel in the row-swap launch.
 struct PanelDesc {
   int64_t a;
   int ld, bp;
