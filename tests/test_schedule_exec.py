@@ -9,7 +9,9 @@ GEMM = C <- beta C -/+ A B on the unmasked entries, ...), with the dense D of
 the oracle assembled into the fronts.  The extracted blocks must equal the
 oracle's blocks of D^{-1} to the FP64 parity bar: this checks the
 arithmetic of the schedule itself, independently of the CUDA kernels (the
-race check covers the ordering of its two streams).
+race check covers the ordering of its two streams).  The factorisation is
+also executed in other orders its two streams may run in, which must leave
+the same arena bit for bit, while dropping any group of its waits must not.
 """
 import numpy as np
 import pytest
@@ -88,11 +90,39 @@ def _pivot_rows(T, bp):
     return lperm
 
 
-def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_out=None, perm_out=None):
+def legal_order(ops, mode, rng=None, waits=True):
+    """An order of a factor op list that the device could run it in: each
+    stream's ops in list order, every op after the op it waits for (the
+    op lists' waits point backwards, so the walk never gets stuck).  mode:
+    0 / 1 runs that stream as far ahead as it can go, "random" switches
+    streams after bursts of random length.  waits=False drops the
+    cross-stream waits (an order the device must not run)."""
+    per = [[i for i in range(len(ops)) if ops[i][5] == s] for s in (0, 1)]
+    pos, done, out, cur = [0, 0], set(), [], 0
+    while len(out) < len(ops):
+        ready = [s for s in (0, 1) if pos[s] < len(per[s]) and
+                 (not waits or ops[per[s][pos[s]]][6] < 0 or ops[per[s][pos[s]]][6] in done)]
+        assert ready
+        if mode == "random":
+            if cur not in ready or rng.random() < 0.3:
+                cur = ready[int(rng.integers(len(ready)))]
+        else:
+            cur = mode if mode in ready else ready[0]
+        i = per[cur][pos[cur]]
+        pos[cur] += 1
+        done.add(i)
+        out.append(i)
+    return out
+
+
+def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_out=None, perm_out=None,
+            factor_order=None):
     """Run the plan's op lists in order on a host arena.  D: the dense Dirac
     matrix of the one lattice of a single-shape plan, or the list of the dense
     matrices of every lattice of a ragged plan (shape order, replicas in
-    order).  Returns the extracted blocks, one dict per lattice for a list."""
+    order).  factor_order: the factorisation's ops in this order of their
+    indices instead of list order.  Returns the extracted blocks, one dict
+    per lattice for a list."""
     segs = t["segments"]
     Ds = D if isinstance(D, list) else [D]
     assert len(Ds) == int(segs[:, 3].sum())
@@ -109,7 +139,11 @@ def execute(t, D, Ns=None, Nt=None, phases=("factor_ops", "selinv_ops"), arena_o
         for r in range(count):
             lattices.append((int(sNs), int(sNt), int(V), int(pbase + r * rstride), int(tbase)))
     outs = [dict() for _ in lattices]
-    for ops in (t[ph] for ph in phases):
+    for ph in phases:
+        ops = t[ph]
+        if ph == "factor_ops" and factor_order is not None:
+            assert sorted(factor_order) == list(range(len(ops)))
+            ops = ops[factor_order]
         for row in ops:
             kind, d0, d1, blocks = row[:4]
             x0, x1 = row[9], row[10]
@@ -287,6 +321,65 @@ def test_schedule_executor_sees_a_broken_table():
     tables["gemm"][bulk[0], 8] = 0  # K = 0: the product adds nothing
     got = execute(tables, D, 4, 4)
     assert _blockwise(got["Gfwd"], ref["Gfwd"]) > 1e3 * tol
+
+
+@pytest.mark.parametrize("ns,nt,prec,panel", [(4, 4, B.CL_FP64_EMU, 12), (4, 4, B.CL_FP64, 24),
+                                              (4, 6, B.CL_FP64_EMU, 30)])
+def test_schedule_same_in_every_legal_order(ns, nt, prec, panel):
+    """The factorisation's two streams may interleave in any way that keeps
+    each stream's order and the cross-stream waits.  Executed in such orders
+    (each stream as far ahead as it can go, and random bursts), the schedule
+    leaves the same arena, bit for bit, as in list order: a check of the
+    race check by execution.  The same walk with the waits dropped changes
+    the result."""
+    D, _, _ = _reference(ns, nt)
+    t = B.Plan.analyze_symbolic(ns, nt, prec, panel).export_tables()
+    ops = t["factor_ops"]
+    assert (ops[:, 5] == 1).any() and (ops[:, 6] >= 0).any()
+
+    def run(order):
+        arena = []
+        got = execute(t, D, ns, nt, arena_out=arena, factor_order=order)
+        return arena[0], got
+
+    A0, g0 = run(None)
+    rng = np.random.default_rng(1707)
+    orders = [legal_order(ops, m, rng) for m in (0, 1, "random", "random")]
+    assert len({tuple(o) for o in orders}) == len(orders)
+    for order in orders:
+        A, g = run(order)
+        assert np.array_equal(A, A0, equal_nan=True)
+        for key in g0:
+            assert np.array_equal(g[key], g0[key]), key
+    with np.errstate(invalid="ignore", divide="ignore"):  # reads of unwritten (NaN) entries
+        A, _ = run(legal_order(ops, 1, waits=False))
+    assert not np.array_equal(A, A0, equal_nan=True)
+
+
+def test_each_dropped_wait_changes_some_order():
+    """Every group of cross-stream waits is needed: with the waits of one
+    (op kind, stream) group dropped, one of the two extreme interleavings
+    (either stream as far ahead as it can go) leaves another arena than
+    list order."""
+    D, _, _ = _reference(4, 4)
+    t = B.Plan.analyze_symbolic(4, 4, B.CL_FP64_EMU, 12).export_tables()
+    ops = t["factor_ops"]
+    arena = []
+    execute(t, D, 4, 4, arena_out=arena)
+    A0 = arena[0]
+    groups = sorted({(int(o[0]), int(o[5])) for o in ops if o[6] >= 0})
+    assert len(groups) >= 3
+    for kind, stream in groups:
+        o2 = ops.copy()
+        o2[(o2[:, 0] == kind) & (o2[:, 5] == stream), 6] = -1
+        t2 = dict(t, factor_ops=o2)
+        changed = []
+        for mode in (0, 1):
+            arena = []
+            with np.errstate(invalid="ignore", divide="ignore"):  # reads of unwritten (NaN) entries
+                execute(t2, D, 4, 4, arena_out=arena, factor_order=legal_order(o2, mode))
+            changed.append(not np.array_equal(arena[0], A0, equal_nan=True))
+        assert any(changed), (kind, stream)
 
 
 def test_ragged_schedule_reproduces_dense_inverses():
