@@ -131,6 +131,37 @@ def test_cooling_invariants(links):
     assert abs(a.real - b.real) < 1e-10 * abs(a.real)
 
 
+def test_cooling_gradient_is_the_norm_gradient(links):
+    """The cooling direction (Sec. 4.1, gauge cooling) is the gradient of the
+    unitarity norm under gauge transformations.  A transformation exp(h X) at
+    one site x (X traceless) changes N_U at the rate (2 / 4V) Re Tr(X f_x);
+    checked by central differences at several sites and directions, which
+    fixes the sign and both neighbour terms of f.  f is also Hermitian and
+    traceless, and the norm, which is 0 on SU(3) links, has f = 0 there."""
+    U = links
+    V = U.shape[0]
+    f = L.cooling_gradient(U, NS, NT)
+    np.testing.assert_allclose(f, np.conj(np.swapaxes(f, -1, -2)), atol=1e-12)
+    assert np.abs(np.trace(f, axis1=1, axis2=2)).max() < 1e-12
+    rng = np.random.default_rng(17)
+    h = 1e-5
+    for x in (0, 37, V - 1):
+        for _ in range(2):
+            X = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+            X -= np.trace(X) / 3 * np.eye(3)
+            n = []
+            for sgn in (1, -1):
+                om = np.broadcast_to(np.eye(3, dtype=complex), (V, 3, 3)).copy()
+                om[x] = scipy.linalg.expm(sgn * h * X)
+                n.append(L.unitarity_norm(inputs.gauge_transform(U, om, NS, NT)))
+            fd = (n[0] - n[1]) / (2 * h)
+            want = 2.0 / (4 * V) * np.trace(X @ f[x]).real
+            assert abs(fd - want) < 1e-6 * abs(want) + 1e-12, (x, fd, want)
+    su3 = inputs.unit_links(NS, NT)
+    assert abs(L.unitarity_norm(su3)) < 1e-15
+    assert np.abs(L.cooling_gradient(su3, NS, NT)).max() < 1e-15
+
+
 def test_observables_unit_and_gauge_invariant(links):
     o = L.observables(inputs.unit_links(NS, NT), NS, NT)
     for k in ("plaq_s", "plaq_t", "poly", "poly_inv"):
