@@ -356,6 +356,26 @@ def test_schedule_same_in_every_legal_order(ns, nt, prec, panel):
     assert not np.array_equal(A, A0, equal_nan=True)
 
 
+def test_ragged_schedule_same_in_every_legal_order():
+    """The merged schedule of a ragged plan (two 4^4 lattices and one 4^3 x 6
+    lattice, fronts of different pivot counts in every launch) leaves the same
+    arena in the extreme and random interleavings of its two streams."""
+    shapes = [(4, 4, 2), (4, 6, 1)]
+    t = B.Plan.analyze_ragged(shapes, B.CL_FP64_EMU, 0, symbolic=True).export_tables()
+    Us = [inputs.random_links(4, 4, seed=1707 + r) for r in range(2)] + [inputs.random_links(4, 6, seed=3)]
+    Ds = [oracle.dirac_dense(4, 4, Us[0], M, MU), oracle.dirac_dense(4, 4, Us[1], M, MU),
+          oracle.dirac_dense(4, 6, Us[2], M, MU)]
+    ops = t["factor_ops"]
+    arena = []
+    execute(t, Ds, phases=("factor_ops",), arena_out=arena)
+    A0 = arena[0]
+    rng = np.random.default_rng(11)
+    for mode in (0, 1, "random"):
+        arena = []
+        execute(t, Ds, phases=("factor_ops",), arena_out=arena, factor_order=legal_order(ops, mode, rng))
+        assert np.array_equal(arena[0], A0, equal_nan=True), mode
+
+
 def test_each_dropped_wait_changes_some_order():
     """Every group of cross-stream waits is needed: with the waits of one
     (op kind, stream) group dropped, one of the two extreme interleavings
